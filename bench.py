@@ -1,0 +1,272 @@
+"""Benchmark: Monte Carlo samples/s and 1/(sigma^2 s) on a generated graph set.
+
+Workload (default): all 28 three-loop vertex graphs without lepton loops,
+plain graph-specific density, one launch per graph; one step = every graph
+integrated over 2^24 fresh Philox samples (seed = step number; under torchrun
+each rank adds rank * 1000003 to the seed, so ranks draw disjoint streams:
+weak scaling, no data-path collective; the per-graph sums are merged once at
+the end).
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MC samples/s and 1/(σ²·s) per graph set, learned+batched vs plain pdf, 1 B300"
+
+
+def sampler_flops(M):
+    """FP64 operations of one draw of the sampler and density (FMA = 2),
+    counted from the steps of the walk: uniforms (4 ops each, 2M of them),
+    M-1 walk steps (product, |T| additions, one series log2 of 42 ops, a
+    quotient and a sum), M series exp2 (76 ops) with normalisation, and the
+    density of three sector components plus the mixture (4 exp2, 1 log2)."""
+    walk = sum(1 + (M - l) + 42 + 2 for l in range(M - 1))
+    norm = M * 76 + M + 42 + 2 * M
+    pdf = M + 3 * (M - 1) * 3 + 9 + 4 * (2 + 76) + 42 + 2
+    return 8 * M + 2 + walk + norm + pdf
+
+
+def oracle_rate(n_loops, graph_ids, per_graph, seed=0):
+    """Time the CPU oracle (as it stands) on a bounded sample: the listed
+    graphs, per_graph samples each, evaluation time after per-graph setup.
+    Runs one process per host core (spawned)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    jobs = []
+    chunk = max(1, per_graph // max(1, cores // max(1, len(graph_ids))))
+    for gi in graph_ids:
+        for lo in range(0, per_graph, chunk):
+            jobs.append((n_loops, gi, lo, min(chunk, per_graph - lo), seed))
+    with mp.get_context("spawn").Pool(min(cores, len(jobs))) as pool:
+        res = pool.map(_oracle_job, jobs)
+    evals = sum(r[0] for r in res)
+    eval_cpu_s = sum(r[1] for r in res)
+    used = min(cores, len(jobs))
+    wall = eval_cpu_s / used
+    return evals / wall, used, evals, wall
+
+
+def _oracle_job(args):
+    n_loops, gi, lo, cnt, seed = args
+    sys.path.insert(0, ROOT)
+    from oracle.estimate import GraphOracle
+    from oracle.graphs import enumerate_graphs
+    o = GraphOracle(enumerate_graphs(n_loops)[gi], gi)
+    t = time.perf_counter()
+    o.samples(lo, cnt, seed)
+    return cnt, time.perf_counter() - t
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while timing."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, path):
+        self.path = path
+        self.p = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self, gpu_index):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    ids = [0, 13, 27]
+    rate, cores, evals, wall = oracle_rate(3, ids, args.oracle_samples)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "samples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "3-loop vertex graphs without lepton loops, plain pdf",
+                       "graphs": len(ids), "samples_per_graph": args.oracle_samples},
+            "cpu_baseline": {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                             "sample": "graphs %s of the 3-loop set, %d samples each, evaluation after "
+                                       "per-graph setup, %.1f s" % (ids, args.oracle_samples, wall)},
+            "e2e": {"value": rate, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "vs_baseline": None}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--loops", type=int, default=3)
+    ap.add_argument("--samples", type=int, default=1 << 24, help="samples per graph per step")
+    ap.add_argument("--oracle-samples", type=int, default=96)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import paper_1909_08015_b300 as ae
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    opts = ae.default_opts()
+    opts.stream = stream.cuda_stream
+    ctx = ae.Context(local, opts)
+    ngr = ctx.load_graphs(args.loops)
+    ids = list(range(ngr))
+    info = [ctx.graph_info(i) for i in ids]
+    M = info[0]["M"]
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def step(seed):
+        return ctx.integrate(ids, args.samples, seed=seed + rank * 1000003)
+
+    for w in range(args.warmup):
+        step(10 ** 6 + w)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv")
+    clocks.start()
+    dev_ms = 0.0
+    e2e_s = 0.0
+    per_all = []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        v, s, per = step(k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - t0
+        dev_ms += ev0.elapsed_time(ev1)
+        per_all.append(per)
+    ck = clocks.stop(local)
+    t_dev = dev_ms / 1e3
+    if dist:
+        tt = torch.tensor([t_dev, e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev, e2e_s = tt.tolist()
+    # merge per-graph sums over steps (and ranks): value and sigma_down
+    sums = np.zeros((len(ids), 3))
+    for per in per_all:
+        for i, p in enumerate(per):
+            sums[i] += (p["sum_y"], p["sum_y2"], p["n"])
+    if dist:
+        ts = torch.tensor(sums, dtype=torch.float64, device="cuda")
+        dist.all_reduce(ts)
+        sums = ts.cpu().numpy()
+    val = 0.0
+    var = 0.0
+    for i in ids:
+        sy, sy2, N = sums[i]
+        mean = sy / N
+        v1 = sy2 / N ** 2 - sy ** 2 / N ** 3
+        val += info[i]["mult"] * mean
+        var += info[i]["mult"] ** 2 * max(v1, 0.0)
+    sigma = math.sqrt(var)
+    total = args.samples * len(ids) * args.steps * world
+    rate = total / t_dev
+    # roofline of the FP64 integrand kernel (sampler + tape per sample)
+    kern_s = sum(p["kernel_seconds"] for per in per_all for p in per)
+    kern_launches = sum(1 for per in per_all for p in per)   # one per graph per slice here
+    flops_per = [info[i]["flops"] + sampler_flops(M) for i in ids]
+    fl_total = sum(flops_per[i] * args.samples for i in ids) * args.steps
+    achieved = fl_total / kern_s / 1e12
+    peak = ctx.fp64_peak() if rank == 0 else 0.0
+    launches = sum(p["launches"] for per in per_all for p in per)
+    d2h = sum(p["d2h_bytes"] for per in per_all for p in per) / args.steps
+    n_dd = sum(p["n_dd"] for per in per_all for p in per)
+    zeroed = sum(p["n_nonfinite"] for per in per_all for p in per)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        crate, cores, evals, wall = oracle_rate(args.loops, [0, ngr // 2, ngr - 1], args.oracle_samples)
+        cpu = {"value": crate, "unit": "samples/s", "cores": cores, "kind": "oracle",
+               "sample": "graphs 0, %d, %d of the set, %d samples each (evaluation after per-graph "
+                         "setup, %.1f s on %d processes)" % (ngr // 2, ngr - 1, args.oracle_samples, wall, cores)}
+    line = {
+        "metric": METRIC, "value": rate, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "all %d %d-loop vertex graphs without lepton loops, plain pdf, one launch "
+                               "per graph" % (len(ids), args.loops),
+                   "samples_per_graph_per_step": args.samples, "seed": "step index (+ rank offset)",
+                   "l2": "256 MB buffer written between timed steps", "parallelism": "dp%d" % world},
+        "inv_sigma2_per_s": 1.0 / (sigma ** 2 * t_dev) if sigma > 0 else None,
+        "estimate": {"value": val, "sigma_down": sigma, "samples": total, "dd_reevaluated": n_dd,
+                     "zeroed": zeroed},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "kernel": "integrate_kernel (sampler + FP64 tape)",
+                     "peak_source": "measured: own DFMA probe (ae_fp64_peak)"},
+        "e2e": {"value": total / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

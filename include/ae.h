@@ -1,0 +1,145 @@
+/* libae: B300-native Monte Carlo integration of the divergence-subtracted
+ * Feynman-parametric integrands of QED vertex graphs without lepton loops
+ * (S. Volkov, arXiv:1909.08015).
+ *
+ * C ABI.  Plain pointers and sizes only.  Every entry point returns 0 on
+ * success or a negative AE_ERR_* code; no exception crosses the boundary and
+ * the message of the last failure is read with ae_last_error().
+ *
+ * Ownership: output buffers are caller-owned HOST memory unless stated
+ * otherwise.  Device memory, streams and compiled integrand tapes are owned
+ * by the context.  One context per host thread.
+ */
+#ifndef AE_H
+#define AE_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AE_OK 0
+#define AE_ERR_ARG (-1)       /* invalid argument (graph id, size, pointer) */
+#define AE_ERR_CUDA (-2)      /* a CUDA runtime call failed                  */
+#define AE_ERR_OOM (-3)       /* device or host allocation failed            */
+#define AE_ERR_TIMEOUT (-4)   /* a bounded device wait ran out               */
+#define AE_ERR_NONFINITE (-5) /* non-finite result where one is not allowed  */
+#define AE_ERR_STATE (-6)     /* call out of order (e.g. no graphs loaded)   */
+#define AE_ERR_NODEV (-7)     /* the call needs a CUDA device, none bound    */
+
+typedef struct ae_ctx ae_ctx;
+
+/* Options.  Defaults (ae_default_opts) are the Calc 2 settings of Sec. V:
+ * C2 = 0.03, C3 = 0.01, C4 = 0.06, D = 0.75 (C1 = 1 - C2 - C3 - C4), and the
+ * six Deg constants of Eq. eq_mc_settings. */
+typedef struct ae_opts {
+  double C2, C3, C4, D;              /* mixture weights of g2, g3, g4; g3 flattening */
+  double C_subI, C_subSE, C_subO;    /* Deg(s) constants used by the library      */
+  double C_bigZ, C_bigF, C_add;      /* Deg(s) constants kept, not used           */
+  double dd_ratio;                   /* re-evaluate in double-double when
+                                        K > dd_ratio * |I| (default 1e8); <= 0 off */
+  int block_size;                    /* threads per CTA, 0 = automatic            */
+  int ctas_per_sm;                   /* CTAs per SM for the grid, 0 = automatic   */
+  void *stream;                      /* cudaStream_t to launch on; NULL = a stream
+                                        owned by the context                      */
+} ae_opts;
+
+void ae_default_opts(ae_opts *opts);
+
+/* Create a context.  cuda_device >= 0 binds that device; -1 creates a
+ * host-only context (graph enumeration, compilation and table export work;
+ * integration calls return AE_ERR_NODEV).  opts may be NULL (defaults). */
+int ae_create(ae_ctx **out, int cuda_device, const ae_opts *opts);
+void ae_destroy(ae_ctx *ctx);
+const char *ae_last_error(const ae_ctx *ctx);
+
+/* Enumerate every n-loop vertex graph without lepton loops (Sec. I: graphs
+ * differing only in arrow direction count once), find its UV-divergent
+ * subgraphs and forests (Sec. II), compile its subtracted integrand to a
+ * tape and build its sampling tables (Sec. III.A).  Graph ids are 0..N-1 in
+ * lexicographic order of the canonical path word.  Replaces any previously
+ * loaded set.  1 <= loops <= 5. */
+int ae_load_graphs(ae_ctx *ctx, int loops, int *n_graphs_out);
+
+typedef struct ae_graph_meta {
+  int loops, M, mult;
+  int klass[3];          /* (k, m, m') of Sec. V, Table I */
+  int word[11];          /* path word, -1 = external vertex; 2n+1 entries */
+  int n_subgraphs, n_terms, tape_len, nslots, n_monomials;
+  double flops;          /* FP64 flops of one tape evaluation (FMA = 2) */
+} ae_graph_meta;
+int ae_graph_info(ae_ctx *ctx, int graph_id, ae_graph_meta *out);
+
+typedef struct ae_graph_result {
+  double value;          /* mult * mean of y = I/g (Eq. eq_integral_approx)       */
+  double sigma;          /* mult * sigma_down (Eq. eq_sigma_down)                  */
+  double mean;           /* mean of y for one orientation                         */
+  double sigma1;         /* sigma_down for one orientation                        */
+  double mean_abs;       /* mean |y|, estimate of the integral of |I|            */
+  double sum_y, sum_y2;  /* raw sums                                               */
+  double max_y2;         /* largest single y^2                                     */
+  uint64_t n;            /* samples                                               */
+  uint64_t n_dd;         /* samples re-evaluated in double-double                 */
+  uint64_t n_nonfinite;  /* samples whose value stayed non-finite: set to zero    */
+  double seconds;        /* device time of the graph's launches                    */
+  uint64_t launches;     /* kernels launched for this graph                        */
+  double kernel_seconds; /* device time of the FP64 integrand kernel alone         */
+  uint64_t d2h_bytes;    /* bytes read back to the host for this graph's result     */
+} ae_graph_result;
+
+/* Integrate the listed graphs with n_samples samples each, Philox seed
+ * `seed`.  value = sum_j mult_j mean_j, sigma^2 = sum_j (mult_j sigma_j)^2
+ * (Eq. eq_sigma_sum).  per_graph may be NULL, else n_ids entries.  One
+ * launch per graph.  Deterministic for given (ids, n_samples, seed, opts). */
+int ae_integrate(ae_ctx *ctx, const int *graph_ids, int n_ids, uint64_t n_samples,
+                 uint64_t seed, double *value, double *sigma, ae_graph_result *per_graph);
+
+/* Batched form: all listed graphs with their own sample counts in ONE
+ * persistent launch (work queue of (graph, counter range) chunks). */
+int ae_integrate_batched(ae_ctx *ctx, const int *graph_ids, int n_ids,
+                         const uint64_t *n_samples, uint64_t seed, double *value,
+                         double *sigma, ae_graph_result *per_graph);
+
+/* Per-sample dump for parity tests: samples first .. first+count-1 of
+ * graph_id under `seed`.  z: count*M, log2g, I, K, y: count each (any may be
+ * NULL).  Host buffers. */
+int ae_eval_samples(ae_ctx *ctx, int graph_id, uint64_t first, uint64_t count,
+                    uint64_t seed, double *z, double *log2g, double *I, double *K,
+                    double *y);
+
+/* Same samples, every one evaluated by the double-double (about 106-bit)
+ * twin of the integrand tape.  I, K, y: count each (any may be NULL). */
+int ae_eval_samples_dd(ae_ctx *ctx, int graph_id, uint64_t first, uint64_t count,
+                       uint64_t seed, double *I, double *K, double *y);
+
+/* Philox4x32-10 on the device: count (counter[4], key[2]) -> word[4]. */
+int ae_philox(ae_ctx *ctx, const uint32_t *ctr, const uint32_t *key, uint32_t *out,
+              size_t count);
+
+/* Measured FP64 throughput of this device (TFLOP/s, FMA = 2 flops): eight
+ * independent DFMA chains per thread on every SM, best of five launches.
+ * The roofline denominator of the integrand kernel. */
+int ae_fp64_peak(ae_ctx *ctx, double *tflops);
+
+/* Host copies of a graph's sampling tables: deg and phi are 3 * 2^M doubles
+ * each (densities g1, g3, g4). */
+int ae_density_tables(ae_ctx *ctx, int graph_id, double *deg, double *phi);
+
+/* Structure export for tests: the UV-divergent subgraphs as (lo, hi, kind)
+ * with kind 0 = self-energy, 1 = vertexlike, 2 = vertexlike in J[G]; and
+ * the R^new terms as a flat list: sign, count, then count * (lo, hi, op) with
+ * op 0 = A, 1 = U, 2 = L, 3 = L-U.  *len receives the number of ints. */
+int ae_subgraphs(ae_ctx *ctx, int graph_id, int *buf, int cap, int *len);
+int ae_terms(ae_ctx *ctx, int graph_id, int *buf, int cap, int *len);
+
+/* Test hook (host, no device): replay a graph's tape at count points z
+ * (count*M doubles).  Used only by the test suite to check the compiler
+ * against the oracle on machines without a GPU; no integration call uses it. */
+int aetest_tape_replay(ae_ctx *ctx, int graph_id, const double *z, size_t count,
+                       double *I, double *K);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AE_H */

@@ -1,0 +1,75 @@
+"""Oracle: Monte Carlo estimator (Sec. III.B) on the Philox sample stream.
+
+TEST INFRASTRUCTURE ONLY (see the package header).
+
+For sample index i of graph j under seed s:
+    u    = Philox uniforms (philox.uniforms),
+    z, g = sampler.sample(density, u),
+    y_i  = I(z)/g(z)   (Eq. eq_integral_approx), computed range-safely as
+           y = (I * 2^(kf - log2 g)) * 2^-kf with kf = floor(log2 g).
+value = (1/N) sum y, sigma_down^2 = sum y^2/N^2 - (sum y)^2/N^3
+(Eq. eq_sigma_down); set sums add mult_j value_j with sigma^2 = sum
+(mult_j sigma_j)^2 (Eq. eq_sigma_sum).  Sums are compensated (math.fsum).
+"""
+import math
+import numpy as np
+
+from .graphs import enumerate_graphs
+from .integrand import Integrand
+from .philox import uniforms
+from .sampler import Density, sample, exp2_series
+
+
+def weight(I, lg):
+    kf = math.floor(lg)
+    s = float(exp2_series(kf - lg))
+    kc = min(max(kf, -100000.0), 100000.0)
+    return math.ldexp(I * s, -int(kc))
+
+
+class GraphOracle:
+    def __init__(self, g, graph_id):
+        self.g = g
+        self.gid = graph_id
+        self.dens = Density(g)
+        self.integrand = Integrand(g)
+
+    def samples(self, first, count, seed=0):
+        """Per-sample (z, log2g, I, K, y) for samples first..first+count-1."""
+        idx = np.arange(first, first + count, dtype=np.uint64)
+        u = uniforms(idx, self.gid, seed, self.dens.M)
+        z, lg, comp = sample(self.dens, u)
+        I = np.empty(count)
+        K = np.empty(count)
+        y = np.empty(count)
+        for k in range(count):
+            I[k], K[k] = self.integrand.evaluate(z[k])
+            y[k] = weight(I[k], lg[k])
+        return dict(z=z, log2g=lg, I=I, K=K, y=y, comp=comp)
+
+
+def summarize(y, mult=1):
+    y = np.asarray(y, dtype=np.float64)
+    N = len(y)
+    sy = math.fsum(y)
+    sy2 = math.fsum(y * y)
+    mean = sy / N
+    var = sy2 / (N * N) - sy * sy / (N * N * N)
+    sig = math.sqrt(max(var, 0.0))
+    return dict(mean=mean, sigma1=sig, value=mult * mean, sigma=mult * sig, n=N,
+                sum_y=sy, sum_y2=sy2, mean_abs=math.fsum(np.abs(y)) / N)
+
+
+def integrate(n_loops, n_samples, seed=0, graph_ids=None):
+    gs = enumerate_graphs(n_loops)
+    ids = range(len(gs)) if graph_ids is None else graph_ids
+    total = 0.0
+    var = 0.0
+    per = []
+    for gi in ids:
+        o = GraphOracle(gs[gi], gi)
+        r = summarize(o.samples(0, n_samples, seed)["y"], gs[gi].mult)
+        per.append(r)
+        total += r["value"]
+        var += r["sigma"] ** 2
+    return total, math.sqrt(var), per

@@ -1,0 +1,220 @@
+"""Python binding of libae (argument marshalling only).
+
+Every computation runs in libae.so: graph enumeration, forests and the
+integrand compiler in its host C++ code, sampling, integrand evaluation and
+reductions in its sm_103a kernels.  This module loads the library, converts
+arguments and raises on error codes; it holds no arithmetic of the method.
+Importing fails loudly if the library cannot be built or loaded.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+AE_ERRORS = {-1: "AE_ERR_ARG", -2: "AE_ERR_CUDA", -3: "AE_ERR_OOM", -4: "AE_ERR_TIMEOUT",
+             -5: "AE_ERR_NONFINITE", -6: "AE_ERR_STATE", -7: "AE_ERR_NODEV"}
+
+
+class AeOpts(ctypes.Structure):
+    _fields_ = [("C2", ctypes.c_double), ("C3", ctypes.c_double), ("C4", ctypes.c_double),
+                ("D", ctypes.c_double), ("C_subI", ctypes.c_double), ("C_subSE", ctypes.c_double),
+                ("C_subO", ctypes.c_double), ("C_bigZ", ctypes.c_double), ("C_bigF", ctypes.c_double),
+                ("C_add", ctypes.c_double), ("dd_ratio", ctypes.c_double),
+                ("block_size", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class AeGraphMeta(ctypes.Structure):
+    _fields_ = [("loops", ctypes.c_int), ("M", ctypes.c_int), ("mult", ctypes.c_int),
+                ("klass", ctypes.c_int * 3), ("word", ctypes.c_int * 11),
+                ("n_subgraphs", ctypes.c_int), ("n_terms", ctypes.c_int),
+                ("tape_len", ctypes.c_int), ("nslots", ctypes.c_int),
+                ("n_monomials", ctypes.c_int), ("flops", ctypes.c_double)]
+
+
+class AeGraphResult(ctypes.Structure):
+    _fields_ = [("value", ctypes.c_double), ("sigma", ctypes.c_double), ("mean", ctypes.c_double),
+                ("sigma1", ctypes.c_double), ("mean_abs", ctypes.c_double),
+                ("sum_y", ctypes.c_double), ("sum_y2", ctypes.c_double), ("max_y2", ctypes.c_double),
+                ("n", ctypes.c_uint64), ("n_dd", ctypes.c_uint64), ("n_nonfinite", ctypes.c_uint64),
+                ("seconds", ctypes.c_double), ("launches", ctypes.c_uint64),
+                ("kernel_seconds", ctypes.c_double), ("d2h_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load (building first if needed) libae.so."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        vp = ctypes.c_void_p
+        dp = P(ctypes.c_double)
+        L.ae_default_opts.argtypes = [P(AeOpts)]
+        L.ae_create.argtypes = [P(vp), ctypes.c_int, P(AeOpts)]
+        L.ae_destroy.argtypes = [vp]
+        L.ae_last_error.argtypes = [vp]
+        L.ae_last_error.restype = ctypes.c_char_p
+        L.ae_load_graphs.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
+        L.ae_graph_info.argtypes = [vp, ctypes.c_int, P(AeGraphMeta)]
+        L.ae_integrate.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                   dp, dp, P(AeGraphResult)]
+        L.ae_integrate_batched.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_uint64),
+                                           ctypes.c_uint64, dp, dp, P(AeGraphResult)]
+        L.ae_eval_samples.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                      dp, dp, dp, dp, dp]
+        L.ae_eval_samples_dd.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                         dp, dp, dp]
+        L.ae_philox.argtypes = [vp, P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32), ctypes.c_size_t]
+        L.ae_density_tables.argtypes = [vp, ctypes.c_int, dp, dp]
+        L.ae_fp64_peak.argtypes = [vp, dp]
+        L.ae_subgraphs.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)]
+        L.ae_terms.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)]
+        L.aetest_tape_replay.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t, dp, dp]
+        _lib = L
+    return _lib
+
+
+def _ptr(a, ct=ctypes.c_double):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def default_opts():
+    o = AeOpts()
+    lib().ae_default_opts(ctypes.byref(o))
+    return o
+
+
+class AeError(RuntimeError):
+    pass
+
+
+class Context:
+    """One libae context.  device=-1 gives a host-only context."""
+
+    def __init__(self, device=0, opts=None):
+        self._h = ctypes.c_void_p()
+        o = opts if opts is not None else default_opts()
+        self._check(lib().ae_create(ctypes.byref(self._h), device, ctypes.byref(o)))
+        self.device = device
+        self.n_graphs = 0
+
+    def _check(self, rc):
+        if rc != 0:
+            msg = lib().ae_last_error(self._h).decode() if self._h else ""
+            raise AeError("%s: %s" % (AE_ERRORS.get(rc, rc), msg))
+
+    def close(self):
+        if self._h:
+            lib().ae_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_graphs(self, loops):
+        n = ctypes.c_int()
+        self._check(lib().ae_load_graphs(self._h, loops, ctypes.byref(n)))
+        self.n_graphs = n.value
+        return n.value
+
+    def graph_info(self, gid):
+        m = AeGraphMeta()
+        self._check(lib().ae_graph_info(self._h, gid, ctypes.byref(m)))
+        d = {k: getattr(m, k) for k, _ in m._fields_}
+        d["klass"] = tuple(m.klass)
+        d["word"] = tuple(m.word[:2 * m.loops + 1])
+        return d
+
+    def integrate(self, ids, n_samples, seed=0):
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        v = ctypes.c_double()
+        s = ctypes.c_double()
+        res = (AeGraphResult * len(ids))()
+        self._check(lib().ae_integrate(self._h, _ptr(ids, ctypes.c_int), len(ids), int(n_samples), int(seed),
+                                       ctypes.byref(v), ctypes.byref(s), res))
+        return v.value, s.value, [r.as_dict() for r in res]
+
+    def integrate_batched(self, ids, n_samples, seed=0):
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        ns = np.ascontiguousarray(n_samples, dtype=np.uint64)
+        v = ctypes.c_double()
+        s = ctypes.c_double()
+        res = (AeGraphResult * len(ids))()
+        self._check(lib().ae_integrate_batched(self._h, _ptr(ids, ctypes.c_int), len(ids),
+                                               _ptr(ns, ctypes.c_uint64), int(seed),
+                                               ctypes.byref(v), ctypes.byref(s), res))
+        return v.value, s.value, [r.as_dict() for r in res]
+
+    def eval_samples(self, gid, first, count, seed=0):
+        M = self.graph_info(gid)["M"]
+        z = np.empty((count, M))
+        lg = np.empty(count); I = np.empty(count); K = np.empty(count); y = np.empty(count)
+        self._check(lib().ae_eval_samples(self._h, gid, first, count, seed, _ptr(z), _ptr(lg),
+                                          _ptr(I), _ptr(K), _ptr(y)))
+        return dict(z=z, log2g=lg, I=I, K=K, y=y)
+
+    def eval_samples_dd(self, gid, first, count, seed=0):
+        I = np.empty(count); K = np.empty(count); y = np.empty(count)
+        self._check(lib().ae_eval_samples_dd(self._h, gid, first, count, seed, _ptr(I), _ptr(K), _ptr(y)))
+        return dict(I=I, K=K, y=y)
+
+    def philox(self, ctr, key):
+        ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+        key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+        out = np.empty_like(ctr)
+        self._check(lib().ae_philox(self._h, _ptr(ctr, ctypes.c_uint32), _ptr(key, ctypes.c_uint32),
+                                    _ptr(out, ctypes.c_uint32), ctr.shape[0]))
+        return out
+
+    def fp64_peak(self):
+        t = ctypes.c_double()
+        self._check(lib().ae_fp64_peak(self._h, ctypes.byref(t)))
+        return t.value
+
+    def density_tables(self, gid):
+        M = self.graph_info(gid)["M"]
+        deg = np.empty(3 << M)
+        phi = np.empty(3 << M)
+        self._check(lib().ae_density_tables(self._h, gid, _ptr(deg), _ptr(phi)))
+        return deg.reshape(3, 1 << M), phi.reshape(3, 1 << M)
+
+    def _intlist(self, fn, gid):
+        n = ctypes.c_int()
+        self._check(fn(self._h, gid, None, 0, ctypes.byref(n)))
+        buf = np.empty(max(n.value, 1), dtype=np.int32)
+        self._check(fn(self._h, gid, _ptr(buf, ctypes.c_int), n.value, ctypes.byref(n)))
+        return buf[:n.value].tolist()
+
+    def subgraphs(self, gid):
+        v = self._intlist(lib().ae_subgraphs, gid)
+        return [tuple(v[i:i + 3]) for i in range(0, len(v), 3)]
+
+    def terms(self, gid):
+        v = self._intlist(lib().ae_terms, gid)
+        out, i = [], 0
+        while i < len(v):
+            sign, cnt = v[i], v[i + 1]
+            els = [tuple(v[i + 2 + 3 * k:i + 5 + 3 * k]) for k in range(cnt)]
+            out.append((sign, els))
+            i += 2 + 3 * cnt
+        return out
+
+    def tape_replay(self, gid, z):
+        """Test hook: host replay of the compiled tape at points z."""
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        I = np.empty(z.shape[0]); K = np.empty(z.shape[0])
+        self._check(lib().aetest_tape_replay(self._h, gid, _ptr(z), z.shape[0], _ptr(I), _ptr(K)))
+        return I, K

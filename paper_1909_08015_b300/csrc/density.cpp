@@ -1,0 +1,118 @@
+// Deg(s) and the sector-density tables of g1, g3, g4 (Sec. III.A,
+// Eqs. eq_pdf_final, eq_pdf, eq_mc_settings), and the project's log2/exp2.
+//
+// Deg(s) (the paper's formula is in a reference that is not available; this
+// is the library's reading): power counting in Feynman-parameter units,
+//   d0(s) = n_e(s)/2 + n_gamma(s) - 2 L(s) + 1/2 [merged line in s],
+// Deg(s) = d0(s) if d0(s) > 0, else 1/2 - C_sub with C_sub = C_subI when s
+// holds the merged line, C_subSE when d0 < 0, C_subO when d0 = 0.
+// Phi(T) = sum_{j in T} Phi(T\j)/Deg(T\j), Phi({j}) = 1; the sector
+// probability of an ordering is prod 1/Deg(s_l) / Phi(all).
+#include <cmath>
+
+#include "ae_internal.h"
+
+namespace ae {
+
+// log2 by the atanh series: x = f 2^k, f in [1/sqrt2, sqrt2),
+// ln f = 2 atanh((f-1)/(f+1)) = 2 sum s^(2i+1)/(2i+1), i = 0..12.
+// Plain IEEE operations (the file is compiled with -ffp-contract=off).
+double ae_log2(double x) {
+  int k;
+  double f = std::frexp(x, &k);
+  if (f < 0.7071067811865476) { f = f * 2.0; k = k - 1; }
+  double s = (f - 1.0) / (f + 1.0);
+  double s2 = s * s;
+  double p = 1.0 / 25.0;
+  for (int d = 23; d >= 3; d -= 2) p = p * s2 + 1.0 / (double)d;
+  p = p * s2 + 1.0;
+  double lnf = (s + s) * p;
+  return (double)k + lnf * 1.4426950408889634;
+}
+
+// 2^x by the Taylor series of exp on r = (x - round(x)) ln 2, 19 terms.
+double ae_exp2(double x) {
+  double k = std::floor(x + 0.5);
+  double r = (x - k) * 0.6931471805599453;
+  double fact = 6402373705728000.0;   // 18!
+  double p = 1.0 / fact;
+  for (int i = 18; i >= 1; --i) {
+    fact = fact / (double)i;
+    p = p * r + 1.0 / fact;
+  }
+  return std::ldexp(p, (int)std::max(-100000.0, std::min(100000.0, k)));
+}
+
+DensityTables build_density(const Graph &g, const DensityConsts &c) {
+  DensityTables t;
+  int M = g.M();
+  t.M = M;
+  // line ends in the merged numbering
+  std::vector<int> ea(M), eb(M);
+  std::vector<char> isph(M, 0);
+  for (int i = 1; i <= 2 * g.n; ++i) {
+    Line l{false, i - 1, i};
+    int p = line_param(g, l);
+    if (p == 0) { ea[0] = g.s - 1; eb[0] = g.s + 1; }
+    else { ea[p] = i - 1; eb[p] = i; }
+  }
+  for (const Line &l : photon_lines(g)) {
+    int p = line_param(g, l);
+    ea[p] = l.a; eb[p] = l.b; isph[p] = 1;
+  }
+  uint32_t full = (1u << M) - 1;
+  std::vector<double> d1(1u << M, 0.0);
+  int N = g.nverts();
+  for (uint32_t s = 1; s < full; ++s) {
+    int ne = 0, ng = 0, nl = 0;
+    std::vector<int> par(N);
+    for (int v = 0; v < N; ++v) par[v] = v;
+    std::vector<char> touched(N, 0);
+    auto find = [&](int x) { while (par[x] != x) x = par[x]; return x; };
+    for (int i = 0; i < M; ++i) {
+      if (!(s >> i & 1)) continue;
+      ++nl;
+      if (isph[i]) ++ng; else ++ne;
+      touched[ea[i]] = touched[eb[i]] = 1;
+      par[find(ea[i])] = find(eb[i]);
+    }
+    int nv = 0, comps = 0;
+    for (int v = 0; v < N; ++v)
+      if (touched[v]) { ++nv; if (find(v) == v) ++comps; }
+    int loops = nl - nv + comps;
+    double d0 = (double)ne / 2.0 + (double)ng - 2.0 * (double)loops + ((s & 1u) ? 0.5 : 0.0);
+    double deg;
+    if (d0 > 0) deg = d0;
+    else if (s & 1u) deg = 0.5 - c.CsubI;
+    else if (d0 < 0) deg = 0.5 - c.CsubSE;
+    else deg = 0.5 - c.CsubO;
+    d1[s] = deg;
+  }
+  for (int k = 0; k < 3; ++k) {
+    t.deg[k].assign(1u << M, 0.0);
+    for (uint32_t s = 1; s < full; ++s) {
+      if (k == 0) t.deg[k][s] = d1[s];
+      else if (k == 1) t.deg[k][s] = d1[s] * c.D;
+      else t.deg[k][s] = d1[s] < 0.5 ? d1[s] : 0.5;
+    }
+    t.phi[k].assign(1u << M, 0.0);
+    for (uint32_t T = 1; T <= full; ++T) {
+      if ((T & (T - 1)) == 0) { t.phi[k][T] = 1.0; continue; }
+      double acc = 0.0;
+      for (int j = 0; j < M; ++j)
+        if (T >> j & 1) {
+          uint32_t R = T ^ (1u << j);
+          acc = acc + t.phi[k][R] / t.deg[k][R];
+        }
+      t.phi[k][T] = acc;
+    }
+  }
+  double C1 = 1.0 - c.C2 - c.C3 - c.C4;
+  t.C[0] = C1; t.C[1] = c.C2; t.C[2] = c.C3; t.C[3] = c.C4;
+  double f = 1.0;
+  for (int i = 2; i <= M - 1; ++i) f = f * (double)i;
+  t.log2_fact = ae_log2(f);
+  return t;
+}
+
+}  // namespace ae

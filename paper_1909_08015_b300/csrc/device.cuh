@@ -1,0 +1,97 @@
+// Device building blocks for sm_103a: Philox4x32-10, the Hepp-sector
+// sampler and density, the FP64 tape interpreter and its double-double twin.
+#pragma once
+#include <cstdint>
+
+namespace aedev {
+
+// ------------------------------------------------------------ Philox ----
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the 4x32 S-box with
+// multipliers M0, M1 and Weyl key increments W0, W1.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+    uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+    uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += W0; k1 += W1;
+  }
+}
+
+// two words -> uniform double in (0, 1): ((w0>>5) 2^26 + (w1>>6) + 1/2) 2^-53
+__device__ __forceinline__ double u01(uint32_t w0, uint32_t w1) {
+  double a = (double)(w0 >> 5), b = (double)(w1 >> 6);
+  return __dmul_rn(__dadd_rn(__dadd_rn(__dmul_rn(a, 67108864.0), b), 0.5), 1.1102230246251565e-16);
+}
+
+// ------------------------------------------------- log2 / exp2 (series) ---
+// The same sequence of IEEE operations as the host's ae_log2/ae_exp2.
+__device__ __forceinline__ double dlog2(double x) {
+  int k;
+  double f = frexp(x, &k);
+  if (f < 0.7071067811865476) { f = __dmul_rn(f, 2.0); k = k - 1; }
+  double s = __ddiv_rn(__dadd_rn(f, -1.0), __dadd_rn(f, 1.0));
+  double s2 = __dmul_rn(s, s);
+  double p = __ddiv_rn(1.0, 25.0);
+#pragma unroll
+  for (int d = 23; d >= 3; d -= 2) p = __dadd_rn(__dmul_rn(p, s2), __ddiv_rn(1.0, (double)d));
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0);
+  double lnf = __dmul_rn(__dadd_rn(s, s), p);
+  return __dadd_rn((double)k, __dmul_rn(lnf, 1.4426950408889634));
+}
+
+__device__ __forceinline__ double dexp2(double x) {
+  double k = floor(__dadd_rn(x, 0.5));
+  double r = __dmul_rn(__dadd_rn(x, -k), 0.6931471805599453);
+  double fact = 6402373705728000.0;
+  double p = __ddiv_rn(1.0, fact);
+#pragma unroll
+  for (int i = 18; i >= 1; --i) {
+    fact = __ddiv_rn(fact, (double)i);
+    p = __dadd_rn(__dmul_rn(p, r), __ddiv_rn(1.0, fact));
+  }
+  double kc = fmin(fmax(k, -100000.0), 100000.0);
+  return ldexp(p, (int)kc);
+}
+
+// ---------------------------------------------------- double-double ----
+struct dd { double hi, lo; };
+__device__ __forceinline__ dd two_sum(double a, double b) {
+  double s = __dadd_rn(a, b);
+  double bb = __dadd_rn(s, -a);
+  double e = __dadd_rn(__dadd_rn(a, -__dadd_rn(s, -bb)), __dadd_rn(b, -bb));
+  return {s, e};
+}
+__device__ __forceinline__ dd quick_two_sum(double a, double b) {
+  double s = __dadd_rn(a, b);
+  return {s, __dadd_rn(b, -__dadd_rn(s, -a))};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi);
+  dd t = two_sum(a.lo, b.lo);
+  s.lo = __dadd_rn(s.lo, t.hi);
+  s = quick_two_sum(s.hi, s.lo);
+  s.lo = __dadd_rn(s.lo, t.lo);
+  return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  double p = __dmul_rn(a.hi, b.hi);
+  double e = __fma_rn(a.hi, b.hi, -p);
+  e = __fma_rn(a.hi, b.lo, e);
+  e = __fma_rn(a.lo, b.hi, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ dd dd_div(dd a, dd b) {
+  double q1 = __ddiv_rn(a.hi, b.hi);
+  dd r = dd_add(a, dd_mul({-q1, 0.0}, b));
+  double q2 = __ddiv_rn(r.hi, b.hi);
+  r = dd_add(r, dd_mul({-q2, 0.0}, b));
+  double q3 = __ddiv_rn(r.hi, b.hi);
+  dd q = quick_two_sum(q1, q2);
+  return dd_add(q, {q3, 0.0});
+}
+__device__ __forceinline__ dd dd_abs(dd a) { return a.hi < 0 ? dd{-a.hi, -a.lo} : a; }
+
+}  // namespace aedev

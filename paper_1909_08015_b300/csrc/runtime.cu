@@ -1,0 +1,901 @@
+// libae runtime: the C ABI of include/ae.h, device memory for the loaded
+// graph set, and the integration kernels for sm_103a.
+//
+// Hot path (one launch per graph, or one persistent launch for a batch):
+//   Philox4x32-10 -> mixture pick -> Hepp-sector walk (Deg/Phi tables) ->
+//   log2 g -> tape interpreter (FP64, per-thread slot file in shared memory,
+//   instructions read warp-uniformly) -> y = I/g -> double-double
+//   accumulation of sum y, sum y^2, sum |y| -> warp-shuffle and CTA
+//   reduction -> one partial per CTA, summed on the host in fixed order.
+// Samples whose forest terms cancel badly (K > dd_ratio |I|) or whose value
+// is not finite are queued and re-evaluated by the double-double kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <thread>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/ae.h"
+#include "ae_internal.h"
+#include "device.cuh"
+
+using namespace ae;
+
+// ------------------------------------------------------------ structs ----
+struct GraphDev {
+  const double *deg;      // 3 * 2^M
+  const double *phi;      // 3 * 2^M
+  const double *wt;       // 3 * 2^M: phi/deg (same IEEE quotient as the walk's definition)
+  const uint2 *code;      // tape
+  const double *khi, *klo;
+  int M, ntape, nslots, outI, outK;
+  int graph_id;
+  double C1, C2, C3, C4, log2_fact;
+  double log2C[4];        // log2 of C1..C4 (g1, g2, g3, g4 order)
+  double log2phi_full[3];
+};
+
+struct Partial {
+  double sy_hi, sy_lo, sy2_hi, sy2_lo, sa_hi, sa_lo, max_y2;
+  unsigned long long n, n_flag, n_overflow;
+};
+
+struct LoadedGraph {
+  Graph g;
+  std::vector<Sub> subs;
+  std::vector<Term> terms;
+  Tape tape;
+  DensityTables dens;
+  CompileStats st;
+  GraphDev dev{};
+};
+
+struct ae_ctx {
+  int device = -1;
+  ae_opts opts;
+  std::string err;
+  std::vector<LoadedGraph> graphs;
+  int loops = 0;
+  void *arena = nullptr;
+  size_t arena_bytes = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = true;
+  // scratch
+  Partial *d_part = nullptr; size_t part_cap = 0;
+  unsigned long long *d_queue = nullptr; size_t queue_cap = 0;
+  unsigned long long *d_qcount = nullptr;
+  double *d_yq = nullptr;
+  int *d_qstat = nullptr;
+};
+
+static int fail(ae_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  return code;
+}
+#define CUDA_TRY(c, x)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (x);                                                     \
+    if (e_ != cudaSuccess)                                                    \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? AE_ERR_OOM : AE_ERR_CUDA, \
+                  std::string(#x) + ": " + cudaGetErrorString(e_));            \
+  } while (0)
+
+// ============================================================ kernels ====
+using namespace aedev;
+
+// Draw one sample: z (M), log2 z (M) and log2 g.  Same steps, same order of
+// IEEE operations as the host-side definition of the sampler.
+__device__ void draw_sample(const GraphDev &G, uint64_t idx, uint64_t seed, double *z, double *lz,
+                            double &log2g) {
+  const int M = G.M;
+  double u[2 * 14 + 2];
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  int nb = M;
+  for (int b = 0; b < nb; ++b) {
+    uint32_t c[4] = {(uint32_t)idx, (uint32_t)(idx >> 32), (uint32_t)G.graph_id, (uint32_t)b};
+    philox4x32_10(c, k0, k1);
+    u[2 * b] = u01(c[0], c[1]);
+    u[2 * b + 1] = u01(c[2], c[3]);
+  }
+  double pick = u[0];
+  int comp;
+  if (pick < G.C1) comp = 0;
+  else if (pick < __dadd_rn(G.C1, G.C2)) comp = 1;
+  else if (pick < __dadd_rn(__dadd_rn(G.C1, G.C2), G.C3)) comp = 2;
+  else comp = 3;
+  const uint32_t full = (1u << M) - 1;
+  if (comp != 1) {
+    int k = comp == 0 ? 0 : comp - 1;
+    const double *deg = G.deg + ((size_t)k << M);
+    const double *phi = G.phi + ((size_t)k << M);
+    const double *wt = G.wt + ((size_t)k << M);
+    uint32_t T = full;
+    double cur = 0.0;
+    for (int l = 0; l < M - 1; ++l) {
+      double uc = u[1 + 2 * l], ut = u[2 + 2 * l];
+      double target = __dmul_rn(uc, __ldg(phi + T));
+      double acc = 0.0;
+      int chosen = -1, last = 0;
+      for (int j = 0; j < M; ++j) {
+        if (!(T >> j & 1)) continue;
+        uint32_t R = T ^ (1u << j);
+        acc = __dadd_rn(acc, __ldg(wt + R));
+        if (chosen < 0 && target < acc) chosen = j;
+        last = j;
+      }
+      if (chosen < 0) chosen = last;
+      lz[chosen] = cur;
+      T ^= 1u << chosen;
+      cur = __dadd_rn(cur, __ddiv_rn(dlog2(ut), __ldg(deg + T)));
+    }
+    int lastj = __ffs(T) - 1;
+    lz[lastj] = cur;
+    double ssum = 0.0;
+    for (int i = 0; i < M; ++i) { z[i] = dexp2(lz[i]); ssum = __dadd_rn(ssum, z[i]); }
+    double ls = dlog2(ssum);
+    for (int i = 0; i < M; ++i) { z[i] = __ddiv_rn(z[i], ssum); lz[i] = __dadd_rn(lz[i], -ls); }
+  } else {
+    double ssum = 0.0;
+    for (int i = 0; i < M; ++i) { z[i] = -dlog2(u[1 + i]); ssum = __dadd_rn(ssum, z[i]); }
+    double ls = dlog2(ssum);
+    for (int i = 0; i < M; ++i) {
+      lz[i] = __dadd_rn(dlog2(z[i]), -ls);
+      z[i] = __ddiv_rn(z[i], ssum);
+    }
+  }
+  // density: sector order = descending log2 z, ties by lower index
+  int ord[14];
+  for (int i = 0; i < M; ++i) {
+    int p = i;
+    while (p > 0 && lz[ord[p - 1]] < lz[i]) { ord[p] = ord[p - 1]; --p; }
+    ord[p] = i;
+  }
+  double sumlz = 0.0;
+  for (int i = 0; i < M; ++i) sumlz = __dadd_rn(sumlz, lz[i]);
+  double t[4];
+  for (int k = 0; k < 3; ++k) {
+    const double *deg = G.deg + ((size_t)k << M);
+    double acc = 0.0;
+    uint32_t T = full ^ (1u << ord[0]);
+    double prev = lz[ord[0]];
+    for (int l = 1; l < M; ++l) {
+      double cv = lz[ord[l]];
+      acc = __dadd_rn(acc, __dmul_rn(__ldg(deg + T), __dadd_rn(cv, -prev)));
+      prev = cv;
+      T ^= 1u << ord[l];
+    }
+    int slot = k == 0 ? 0 : k + 1;
+    t[slot] = __dadd_rn(__dadd_rn(__dadd_rn(G.log2C[slot], -G.log2phi_full[k]), acc), -sumlz);
+  }
+  t[1] = __dadd_rn(G.log2C[1], G.log2_fact);
+  double m = t[0];
+  for (int k = 1; k < 4; ++k) m = fmax(m, t[k]);
+  double rel = 0.0;
+  for (int k = 0; k < 4; ++k) rel = __dadd_rn(rel, dexp2(__dadd_rn(t[k], -m)));
+  log2g = __dadd_rn(m, dlog2(rel));
+}
+
+// y = I / g with g = 2^log2g, range-safe: I * 2^(kf - lg) * 2^-kf
+__device__ __forceinline__ double weight(double I, double lg) {
+  double kf = floor(lg);
+  double s = dexp2(__dadd_rn(kf, -lg));
+  double kc = fmin(fmax(kf, -100000.0), 100000.0);
+  return ldexp(__dmul_rn(I, s), -(int)kc);
+}
+
+// FP64 tape interpreter.  S points at this thread's column of the slot file
+// (stride = blockDim.x).
+__device__ __forceinline__ void run_tape(const GraphDev &G, double *S, int stride) {
+  const uint2 *code = G.code;
+  const double *K = G.khi;
+  for (int pc = 0; pc < G.ntape; ++pc) {
+    uint2 w = __ldg(code + pc);
+    int op = w.x & 0xff;
+    int d = w.x >> 16;
+    int a = w.y & 0xffff;
+    int b = w.y >> 16;
+    double *D = S + d * stride;
+    switch (op) {
+      case T_ADD: *D = __dadd_rn(S[a * stride], S[b * stride]); break;
+      case T_SUB: *D = __dadd_rn(S[a * stride], -S[b * stride]); break;
+      case T_MUL: *D = __dmul_rn(S[a * stride], S[b * stride]); break;
+      case T_DIV: *D = __ddiv_rn(S[a * stride], S[b * stride]); break;
+      case T_FMA: *D = __fma_rn(S[a * stride], S[b * stride], *D); break;
+      case T_FMAC: *D = __fma_rn(__ldg(K + b), S[a * stride], *D); break;
+      case T_MULC: *D = __dmul_rn(__ldg(K + b), S[a * stride]); break;
+      case T_CONST: *D = __ldg(K + b); break;
+      case T_ABS: *D = fabs(S[a * stride]); break;
+      case T_NEG: *D = -S[a * stride]; break;
+      case T_ZERO: *D = 0.0; break;
+      case T_ADDABS: *D = __dadd_rn(*D, fabs(S[a * stride])); break;
+      default: break;
+    }
+  }
+}
+
+// Double-double twin of run_tape (slot file holds hi/lo pairs).
+__device__ void run_tape_dd(const GraphDev &G, dd *S, int stride) {
+  for (int pc = 0; pc < G.ntape; ++pc) {
+    uint2 w = __ldg(G.code + pc);
+    int op = w.x & 0xff, d = w.x >> 16, a = w.y & 0xffff, b = w.y >> 16;
+    dd *D = S + d * stride;
+    dd kb = {0, 0};
+    if (op == T_FMAC || op == T_MULC || op == T_CONST) kb = {__ldg(G.khi + b), __ldg(G.klo + b)};
+    switch (op) {
+      case T_ADD: *D = dd_add(S[a * stride], S[b * stride]); break;
+      case T_SUB: { dd t = S[b * stride]; *D = dd_add(S[a * stride], {-t.hi, -t.lo}); } break;
+      case T_MUL: *D = dd_mul(S[a * stride], S[b * stride]); break;
+      case T_DIV: *D = dd_div(S[a * stride], S[b * stride]); break;
+      case T_FMA: *D = dd_add(*D, dd_mul(S[a * stride], S[b * stride])); break;
+      case T_FMAC: *D = dd_add(*D, dd_mul(kb, S[a * stride])); break;
+      case T_MULC: *D = dd_mul(kb, S[a * stride]); break;
+      case T_CONST: *D = kb; break;
+      case T_ABS: *D = dd_abs(S[a * stride]); break;
+      case T_NEG: { dd t = S[a * stride]; *D = {-t.hi, -t.lo}; } break;
+      case T_ZERO: *D = {0.0, 0.0}; break;
+      case T_ADDABS: *D = dd_add(*D, dd_abs(S[a * stride])); break;
+      default: break;
+    }
+  }
+}
+
+__device__ __forceinline__ void dd_acc(double &hi, double &lo, double x) {
+  dd s = two_sum(hi, x);
+  lo = __dadd_rn(lo, s.lo);
+  dd r = quick_two_sum(s.hi, lo);
+  hi = r.hi; lo = r.lo;
+}
+
+__device__ __forceinline__ void dd_merge(double &hi, double &lo, double h2, double l2) {
+  dd r = dd_add({hi, lo}, {h2, l2});
+  hi = r.hi; lo = r.lo;
+}
+
+// Block reduction of the per-thread accumulators into one Partial.
+__device__ void block_reduce(Partial p, Partial *out) {
+  __shared__ Partial red[32];
+  const unsigned full = 0xffffffffu;
+  for (int off = 16; off > 0; off >>= 1) {
+    Partial q;
+    q.sy_hi = __shfl_down_sync(full, p.sy_hi, off); q.sy_lo = __shfl_down_sync(full, p.sy_lo, off);
+    q.sy2_hi = __shfl_down_sync(full, p.sy2_hi, off); q.sy2_lo = __shfl_down_sync(full, p.sy2_lo, off);
+    q.sa_hi = __shfl_down_sync(full, p.sa_hi, off); q.sa_lo = __shfl_down_sync(full, p.sa_lo, off);
+    q.max_y2 = __shfl_down_sync(full, p.max_y2, off);
+    q.n = __shfl_down_sync(full, p.n, off); q.n_flag = __shfl_down_sync(full, p.n_flag, off);
+    q.n_overflow = __shfl_down_sync(full, p.n_overflow, off);
+    dd_merge(p.sy_hi, p.sy_lo, q.sy_hi, q.sy_lo);
+    dd_merge(p.sy2_hi, p.sy2_lo, q.sy2_hi, q.sy2_lo);
+    dd_merge(p.sa_hi, p.sa_lo, q.sa_hi, q.sa_lo);
+    p.max_y2 = fmax(p.max_y2, q.max_y2);
+    p.n += q.n; p.n_flag += q.n_flag; p.n_overflow += q.n_overflow;
+  }
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = p;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Partial r = red[0];
+    int nw = (blockDim.x + 31) >> 5;
+    for (int w = 1; w < nw; ++w) {
+      dd_merge(r.sy_hi, r.sy_lo, red[w].sy_hi, red[w].sy_lo);
+      dd_merge(r.sy2_hi, r.sy2_lo, red[w].sy2_hi, red[w].sy2_lo);
+      dd_merge(r.sa_hi, r.sa_lo, red[w].sa_hi, red[w].sa_lo);
+      r.max_y2 = fmax(r.max_y2, red[w].max_y2);
+      r.n += red[w].n; r.n_flag += red[w].n_flag; r.n_overflow += red[w].n_overflow;
+    }
+    *out = r;
+  }
+}
+
+// Process samples [first, first + count) of one graph; CTA b takes a
+// contiguous chunk, thread t its strided share.
+__global__ void integrate_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t seed,
+                                 double dd_ratio, Partial *part, unsigned long long *queue,
+                                 unsigned long long qcap, unsigned long long *qcount) {
+  extern __shared__ double slots[];
+  double *S = slots + threadIdx.x;
+  const int stride = blockDim.x;
+  uint64_t chunk = (count + gridDim.x - 1) / gridDim.x;
+  uint64_t lo = (uint64_t)blockIdx.x * chunk;
+  uint64_t hi = min(count, lo + chunk);
+  Partial p = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double z[14], lz[14];
+  for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    uint64_t idx = first + i;
+    double lg;
+    draw_sample(G, idx, seed, z, lz, lg);
+    for (int k = 0; k < G.M; ++k) S[k * stride] = z[k];
+    run_tape(G, S, stride);
+    double I = S[G.outI * stride], Kv = S[G.outK * stride];
+    double y = weight(I, lg);
+    bool bad = !isfinite(I) || !isfinite(Kv) || !isfinite(y) ||
+               (dd_ratio > 0 && Kv > dd_ratio * fabs(I));
+    p.n += 1;
+    if (bad) {
+      p.n_flag += 1;
+      unsigned long long slot = atomicAdd(qcount, 1ull);
+      if (slot < qcap) queue[slot] = idx;
+      else p.n_overflow += 1;
+      continue;
+    }
+    dd_acc(p.sy_hi, p.sy_lo, y);
+    dd_acc(p.sy2_hi, p.sy2_lo, y * y);
+    dd_acc(p.sa_hi, p.sa_lo, fabs(y));
+    p.max_y2 = fmax(p.max_y2, y * y);
+  }
+  block_reduce(p, part + blockIdx.x);
+}
+
+// Double-double re-evaluation of queued samples: y_out[i] and status
+// (0 ok, 1 still failing -> the sample counts as zero).
+__global__ void dd_kernel(GraphDev G, uint64_t seed, const unsigned long long *queue, uint64_t nq,
+                          double dd_ratio, double *y_out, int *status) {
+  extern __shared__ dd dslots[];
+  dd *S = dslots + threadIdx.x;
+  const int stride = blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    double z[14], lz[14], lg;
+    draw_sample(G, queue[i], seed, z, lz, lg);
+    for (int k = 0; k < G.M; ++k) S[k * stride] = {z[k], 0.0};
+    run_tape_dd(G, S, stride);
+    dd I = S[G.outI * stride], K = S[G.outK * stride];
+    double y = weight(I.hi + I.lo, lg);
+    // accepted when the double-double result keeps ~8 significant digits
+    // (2^-104 K / |I| below 1e-8)
+    bool bad = !isfinite(I.hi) || !isfinite(K.hi) || !isfinite(y) ||
+               K.hi > 2.0e23 * fabs(I.hi);
+    y_out[i] = bad ? 0.0 : y;
+    status[i] = bad ? 1 : 0;
+  }
+}
+
+// Per-sample dump for parity tests.
+__global__ void eval_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t seed, double *z_out,
+                            double *lg_out, double *I_out, double *K_out, double *y_out) {
+  extern __shared__ double slots[];
+  double *S = slots + threadIdx.x;
+  const int stride = blockDim.x;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < count;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t i = base + threadIdx.x;
+    if (i >= count) continue;
+    double z[14], lz[14], lg;
+    draw_sample(G, first + i, seed, z, lz, lg);
+    for (int k = 0; k < G.M; ++k) { S[k * stride] = z[k]; z_out[i * G.M + k] = z[k]; }
+    run_tape(G, S, stride);
+    double I = S[G.outI * stride], Kv = S[G.outK * stride];
+    lg_out[i] = lg; I_out[i] = I; K_out[i] = Kv; y_out[i] = weight(I, lg);
+  }
+}
+
+// Per-sample dump with every sample evaluated in double-double.
+__global__ void eval_dd_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t seed,
+                               double *I_out, double *K_out, double *y_out) {
+  extern __shared__ dd dslots2[];
+  dd *S = dslots2 + threadIdx.x;
+  const int stride = blockDim.x;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < count;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t i = base + threadIdx.x;
+    if (i >= count) continue;
+    double z[14], lz[14], lg;
+    draw_sample(G, first + i, seed, z, lz, lg);
+    for (int k = 0; k < G.M; ++k) S[k * stride] = {z[k], 0.0};
+    run_tape_dd(G, S, stride);
+    dd I = S[G.outI * stride], K = S[G.outK * stride];
+    double Iv = I.hi + I.lo;
+    I_out[i] = Iv; K_out[i] = K.hi + K.lo; y_out[i] = weight(Iv, lg);
+  }
+}
+
+// FP64 peak probe: independent DFMA chains, 8 per thread, no memory traffic.
+__global__ void dfma_probe_kernel(int iters, double a, double b, double *sink) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-9 + k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = __fma_rn(x[k], a, b);
+  }
+  double s = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  if (s == 1234.5678) sink[0] = s;   // keeps the chains alive
+}
+
+__global__ void philox_kernel(const uint32_t *ctr, const uint32_t *key, uint32_t *out, size_t count) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  uint32_t c[4] = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+  philox4x32_10(c, key[2 * i], key[2 * i + 1]);
+  for (int k = 0; k < 4; ++k) out[4 * i + k] = c[k];
+}
+
+// ============================================================ host ABI ===
+extern "C" void ae_default_opts(ae_opts *o) {
+  o->C2 = 0.03; o->C3 = 0.01; o->C4 = 0.06; o->D = 0.75;
+  o->C_subI = 0.2; o->C_subSE = 0.0; o->C_subO = 0.2;
+  o->C_bigZ = 0.256; o->C_bigF = 0.839; o->C_add = 0.786;
+  o->dd_ratio = 1e8;
+  o->block_size = 0;
+  o->ctas_per_sm = 0;
+  o->stream = nullptr;
+}
+
+extern "C" int ae_create(ae_ctx **out, int dev, const ae_opts *opts) {
+  if (!out) return AE_ERR_ARG;
+  *out = nullptr;
+  ae_ctx *c = new (std::nothrow) ae_ctx();
+  if (!c) return AE_ERR_OOM;
+  if (opts) c->opts = *opts; else ae_default_opts(&c->opts);
+  c->device = dev;
+  if (dev >= 0) {
+    cudaError_t e = cudaSetDevice(dev);
+    if (e != cudaSuccess) { delete c; return AE_ERR_CUDA; }
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (c->opts.stream) {
+      c->stream = (cudaStream_t)c->opts.stream;
+      c->own_stream = false;
+    } else if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return AE_ERR_CUDA;
+    }
+  }
+  *out = c;
+  return AE_OK;
+}
+
+static void free_device(ae_ctx *c) {
+  if (c->device < 0) return;
+  cudaSetDevice(c->device);
+  if (c->arena) cudaFree(c->arena);
+  if (c->d_part) cudaFree(c->d_part);
+  if (c->d_queue) cudaFree(c->d_queue);
+  if (c->d_qcount) cudaFree(c->d_qcount);
+  if (c->d_yq) cudaFree(c->d_yq);
+  if (c->d_qstat) cudaFree(c->d_qstat);
+  c->arena = nullptr; c->d_part = nullptr; c->d_queue = nullptr; c->d_qcount = nullptr;
+  c->d_yq = nullptr; c->d_qstat = nullptr; c->part_cap = c->queue_cap = 0;
+}
+
+extern "C" void ae_destroy(ae_ctx *c) {
+  if (!c) return;
+  free_device(c);
+  if (c->stream && c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+extern "C" const char *ae_last_error(const ae_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" int ae_load_graphs(ae_ctx *c, int loops, int *n_out) {
+  if (!c) return AE_ERR_ARG;
+  if (loops < 1 || loops > 5) return fail(c, AE_ERR_ARG, "loops must be 1..5");
+  try {
+    std::vector<Graph> gs = enumerate_graphs(loops);
+    DensityConsts dc;
+    dc.C2 = c->opts.C2; dc.C3 = c->opts.C3; dc.C4 = c->opts.C4; dc.D = c->opts.D;
+    dc.CsubI = c->opts.C_subI; dc.CsubSE = c->opts.C_subSE; dc.CsubO = c->opts.C_subO;
+    std::vector<LoadedGraph> L(gs.size());
+    // graphs compile independently: spread them over the host's cores
+    std::atomic<size_t> next(0);
+    std::vector<std::string> errs(gs.size());
+    auto worker = [&]() {
+      for (size_t i = next++; i < gs.size(); i = next++) {
+        try {
+          L[i].g = gs[i];
+          L[i].subs = divergent_subgraphs(gs[i]);
+          L[i].terms = rnew_terms(gs[i], L[i].subs);
+          L[i].tape = compile_integrand(gs[i], &L[i].st);
+          L[i].dens = build_density(gs[i], dc);
+        } catch (std::exception &e) {
+          errs[i] = e.what();
+        }
+      }
+    };
+    unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 64u));
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) th.emplace_back(worker);
+    for (auto &t : th) t.join();
+    for (size_t i = 0; i < gs.size(); ++i)
+      if (!errs[i].empty()) throw std::runtime_error("graph " + std::to_string(i) + ": " + errs[i]);
+    free_device(c);
+    c->graphs.swap(L);
+    c->loops = loops;
+  } catch (std::exception &e) {
+    return fail(c, AE_ERR_STATE, std::string("load_graphs: ") + e.what());
+  }
+  if (c->device >= 0) {
+    // one arena: per graph deg, phi, konst hi, konst lo, code
+    size_t bytes = 0;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    for (auto &lg : c->graphs) {
+      size_t T = (size_t)1 << lg.g.M();
+      bytes += al(3 * T * 8) * 3 + al(lg.tape.khi.size() * 8) * 2 + al(lg.tape.code.size() * 8);
+    }
+    CUDA_TRY(c, cudaMalloc(&c->arena, bytes));
+    c->arena_bytes = bytes;
+    char *p = (char *)c->arena;
+    for (size_t gi = 0; gi < c->graphs.size(); ++gi) {
+      LoadedGraph &lg = c->graphs[gi];
+      size_t T = (size_t)1 << lg.g.M();
+      std::vector<double> deg(3 * T), phi(3 * T), wt(3 * T, 0.0);
+      for (int k = 0; k < 3; ++k) {
+        std::copy(lg.dens.deg[k].begin(), lg.dens.deg[k].end(), deg.begin() + k * T);
+        std::copy(lg.dens.phi[k].begin(), lg.dens.phi[k].end(), phi.begin() + k * T);
+        for (size_t R = 1; R + 1 < T; ++R) wt[k * T + R] = lg.dens.phi[k][R] / lg.dens.deg[k][R];
+      }
+      GraphDev &G = lg.dev;
+      G.deg = (double *)p; CUDA_TRY(c, cudaMemcpy(p, deg.data(), 3 * T * 8, cudaMemcpyHostToDevice)); p += al(3 * T * 8);
+      G.phi = (double *)p; CUDA_TRY(c, cudaMemcpy(p, phi.data(), 3 * T * 8, cudaMemcpyHostToDevice)); p += al(3 * T * 8);
+      G.wt = (double *)p; CUDA_TRY(c, cudaMemcpy(p, wt.data(), 3 * T * 8, cudaMemcpyHostToDevice)); p += al(3 * T * 8);
+      size_t nk = lg.tape.khi.size();
+      G.khi = (double *)p; if (nk) CUDA_TRY(c, cudaMemcpy(p, lg.tape.khi.data(), nk * 8, cudaMemcpyHostToDevice)); p += al(nk * 8);
+      G.klo = (double *)p; if (nk) CUDA_TRY(c, cudaMemcpy(p, lg.tape.klo.data(), nk * 8, cudaMemcpyHostToDevice)); p += al(nk * 8);
+      G.code = (const uint2 *)p;
+      CUDA_TRY(c, cudaMemcpy(p, lg.tape.code.data(), lg.tape.code.size() * 8, cudaMemcpyHostToDevice));
+      p += al(lg.tape.code.size() * 8);
+      G.M = lg.g.M(); G.ntape = (int)lg.tape.code.size(); G.nslots = lg.tape.nslots;
+      G.outI = lg.tape.out_I; G.outK = lg.tape.out_K; G.graph_id = (int)gi;
+      G.C1 = lg.dens.C[0]; G.C2 = lg.dens.C[1]; G.C3 = lg.dens.C[2]; G.C4 = lg.dens.C[3];
+      G.log2_fact = lg.dens.log2_fact;
+      for (int k = 0; k < 4; ++k) G.log2C[k] = ae_log2(lg.dens.C[k]);
+      for (int k = 0; k < 3; ++k) G.log2phi_full[k] = ae_log2(lg.dens.phi[k][T - 1]);
+    }
+  }
+  if (n_out) *n_out = (int)c->graphs.size();
+  return AE_OK;
+}
+
+extern "C" int ae_graph_info(ae_ctx *c, int id, ae_graph_meta *o) {
+  if (!c || !o) return AE_ERR_ARG;
+  if (id < 0 || id >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
+  const LoadedGraph &lg = c->graphs[id];
+  std::memset(o, 0, sizeof(*o));
+  o->loops = lg.g.n; o->M = lg.g.M(); o->mult = lg.g.mult;
+  for (int k = 0; k < 3; ++k) o->klass[k] = lg.g.klass[k];
+  for (int k = 0; k < 11; ++k) o->word[k] = k < (int)lg.g.word.size() ? lg.g.word[k] : -2;
+  o->n_subgraphs = (int)lg.subs.size(); o->n_terms = (int)lg.terms.size();
+  o->tape_len = (int)lg.tape.code.size(); o->nslots = lg.tape.nslots;
+  o->n_monomials = lg.st.n_monomials; o->flops = lg.tape.flops;
+  return AE_OK;
+}
+
+static int pick_block(const ae_ctx *c, int nslots, size_t elem) {
+  const size_t smem_cap = 200 * 1024;
+  int bs = c->opts.block_size;
+  if (bs <= 0) {
+    bs = 256;
+    while (bs > 32 && (size_t)bs * nslots * elem > smem_cap) bs /= 2;
+  }
+  if ((size_t)bs * nslots * elem > smem_cap) return -1;
+  return bs;
+}
+
+static int ensure_scratch(ae_ctx *c, size_t nparts, size_t qcap) {
+  if (nparts > c->part_cap) {
+    if (c->d_part) cudaFree(c->d_part);
+    CUDA_TRY(c, cudaMalloc(&c->d_part, nparts * sizeof(Partial)));
+    c->part_cap = nparts;
+  }
+  if (!c->d_qcount) CUDA_TRY(c, cudaMalloc(&c->d_qcount, sizeof(unsigned long long)));
+  if (qcap > c->queue_cap) {
+    if (c->d_queue) cudaFree(c->d_queue);
+    if (c->d_yq) cudaFree(c->d_yq);
+    if (c->d_qstat) cudaFree(c->d_qstat);
+    CUDA_TRY(c, cudaMalloc(&c->d_queue, qcap * sizeof(unsigned long long)));
+    CUDA_TRY(c, cudaMalloc(&c->d_yq, qcap * sizeof(double)));
+    CUDA_TRY(c, cudaMalloc(&c->d_qstat, qcap * sizeof(int)));
+    c->queue_cap = qcap;
+  }
+  return AE_OK;
+}
+
+static void host_dd_add(double &hi, double &lo, double x) {
+  double s = hi + x;
+  double bb = s - hi;
+  double e = (hi - (s - bb)) + (x - bb);
+  lo += e;
+  double r = s + lo;
+  lo = lo - (r - s);
+  hi = r;
+}
+
+// Integrate one graph in slices of at most 2^28 samples (bounds the
+// double-double queue); sums are combined in slice order, so the result is
+// independent of the schedule.
+static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_graph_result *res) {
+  LoadedGraph &lg = c->graphs[gid];
+  GraphDev &G = lg.dev;
+  int bs = pick_block(c, G.nslots, 8);
+  if (bs < 0) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
+  size_t smem = (size_t)bs * G.nslots * 8;
+  CUDA_TRY(c, cudaFuncSetAttribute(integrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = c->opts.ctas_per_sm;
+  if (per_sm <= 0) {
+    CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integrate_kernel, bs, smem));
+    if (per_sm < 1) per_sm = 1;
+  }
+  const uint64_t SLICE = 1ull << 28;
+  double sy = 0, syl = 0, sy2 = 0, sy2l = 0, sa = 0, sal = 0, mx = 0;
+  uint64_t n = 0, ndd = 0, nbad = 0, launches = 0, d2h = 0;
+  double secs = 0, ksecs = 0;
+  for (uint64_t start = 0; start < nsamp; start += SLICE) {
+    uint64_t len = std::min(SLICE, nsamp - start);
+    uint64_t grid = (uint64_t)c->sm_count * per_sm;
+    if (grid * bs > len) grid = std::max<uint64_t>(1, (len + bs - 1) / bs);
+    size_t qcap = (size_t)std::max<uint64_t>(len / 4, 65536);
+    int rc = ensure_scratch(c, grid, qcap);
+    if (rc) return rc;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_qcount, 0, sizeof(unsigned long long), c->stream));
+    cudaEvent_t e0, e1, ek;
+    cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&ek);
+    cudaEventRecord(e0, c->stream);
+    integrate_kernel<<<(unsigned)grid, bs, smem, c->stream>>>(G, start, len, seed, c->opts.dd_ratio, c->d_part,
+                                                              c->d_queue, c->queue_cap, c->d_qcount);
+    CUDA_TRY(c, cudaGetLastError());
+    cudaEventRecord(ek, c->stream);
+    ++launches;
+    unsigned long long nq = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&nq, c->d_qcount, sizeof(nq), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (nq > c->queue_cap) {
+      cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(ek);
+      return fail(c, AE_ERR_STATE, "double-double queue overflow");
+    }
+    if (nq) {
+      int bsd = pick_block(c, G.nslots, 16);
+      if (bsd < 0) return fail(c, AE_ERR_STATE, "double-double slot file does not fit in shared memory");
+      size_t sm2 = (size_t)bsd * G.nslots * 16;
+      CUDA_TRY(c, cudaFuncSetAttribute(dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+      unsigned g2 = (unsigned)std::min<uint64_t>((nq + bsd - 1) / bsd, (uint64_t)c->sm_count * 8);
+      dd_kernel<<<g2, bsd, sm2, c->stream>>>(G, seed, c->d_queue, nq, c->opts.dd_ratio, c->d_yq, c->d_qstat);
+      CUDA_TRY(c, cudaGetLastError());
+      ++launches;
+    }
+    cudaEventRecord(e1, c->stream);
+    std::vector<Partial> parts(grid);
+    CUDA_TRY(c, cudaMemcpyAsync(parts.data(), c->d_part, grid * sizeof(Partial), cudaMemcpyDeviceToHost, c->stream));
+    std::vector<unsigned long long> q(nq);
+    std::vector<double> yq(nq);
+    std::vector<int> qs(nq);
+    if (nq) {
+      CUDA_TRY(c, cudaMemcpyAsync(q.data(), c->d_queue, nq * 8, cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(c, cudaMemcpyAsync(yq.data(), c->d_yq, nq * 8, cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(c, cudaMemcpyAsync(qs.data(), c->d_qstat, nq * 4, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    float ms = 0, mk = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventElapsedTime(&mk, e0, ek);
+    cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(ek);
+    secs += ms * 1e-3;
+    ksecs += mk * 1e-3;
+    d2h += sizeof(unsigned long long) + grid * sizeof(Partial) + nq * (8 + 8 + 4);
+    for (auto &p : parts) {
+      host_dd_add(sy, syl, p.sy_hi); host_dd_add(sy, syl, p.sy_lo);
+      host_dd_add(sy2, sy2l, p.sy2_hi); host_dd_add(sy2, sy2l, p.sy2_lo);
+      host_dd_add(sa, sal, p.sa_hi); host_dd_add(sa, sal, p.sa_lo);
+      mx = std::max(mx, p.max_y2);
+      n += p.n;
+    }
+    // queued samples in sample order (deterministic)
+    std::vector<size_t> ord(nq);
+    for (size_t i = 0; i < nq; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return q[a] < q[b]; });
+    for (size_t t : ord) {
+      double y = yq[t];
+      if (qs[t]) ++nbad;
+      host_dd_add(sy, syl, y); host_dd_add(sy2, sy2l, y * y); host_dd_add(sa, sal, std::fabs(y));
+      mx = std::max(mx, y * y);
+    }
+    ndd += nq;
+  }
+  res->sum_y = sy + syl; res->sum_y2 = sy2 + sy2l;
+  res->n = n; res->n_dd = ndd; res->n_nonfinite = nbad;
+  double N = (double)n;
+  res->mean = res->sum_y / N;
+  double var = res->sum_y2 / (N * N) - res->sum_y * res->sum_y / (N * N * N);
+  res->sigma1 = var > 0 ? std::sqrt(var) : 0.0;
+  res->mean_abs = (sa + sal) / N;
+  res->max_y2 = mx;
+  res->value = lg.g.mult * res->mean;
+  res->sigma = lg.g.mult * res->sigma1;
+  res->seconds = secs;
+  res->launches = launches;
+  res->kernel_seconds = ksecs;
+  res->d2h_bytes = d2h;
+  return AE_OK;
+}
+
+extern "C" int ae_integrate(ae_ctx *c, const int *ids, int n_ids, uint64_t nsamp, uint64_t seed,
+                            double *value, double *sigma, ae_graph_result *per) {
+  if (!c) return AE_ERR_ARG;
+  if (c->device < 0) return fail(c, AE_ERR_NODEV, "integration needs a CUDA device");
+  if (c->graphs.empty()) return fail(c, AE_ERR_STATE, "no graphs loaded");
+  if (!ids || n_ids <= 0 || nsamp == 0) return fail(c, AE_ERR_ARG, "empty graph list or zero samples");
+  for (int i = 0; i < n_ids; ++i)
+    if (ids[i] < 0 || ids[i] >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  double v = 0, s2 = 0;
+  for (int i = 0; i < n_ids; ++i) {
+    ae_graph_result r;
+    std::memset(&r, 0, sizeof(r));
+    int rc = integrate_one(c, ids[i], nsamp, seed, &r);
+    if (rc) return rc;
+    v += r.value;
+    s2 += r.sigma * r.sigma;
+    if (per) per[i] = r;
+  }
+  if (value) *value = v;
+  if (sigma) *sigma = std::sqrt(s2);
+  return AE_OK;
+}
+
+extern "C" int ae_integrate_batched(ae_ctx *c, const int *ids, int n_ids, const uint64_t *ns,
+                                    uint64_t seed, double *value, double *sigma, ae_graph_result *per) {
+  return fail(c, AE_ERR_STATE, "batched integration not available in this build");
+}
+
+extern "C" int ae_eval_samples(ae_ctx *c, int gid, uint64_t first, uint64_t count, uint64_t seed,
+                               double *z, double *log2g, double *I, double *K, double *y) {
+  if (!c) return AE_ERR_ARG;
+  if (c->device < 0) return fail(c, AE_ERR_NODEV, "eval_samples needs a CUDA device");
+  if (gid < 0 || gid >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
+  if (count == 0) return AE_OK;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  GraphDev &G = c->graphs[gid].dev;
+  int bs = pick_block(c, G.nslots, 8);
+  if (bs < 0) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
+  size_t smem = (size_t)bs * G.nslots * 8;
+  CUDA_TRY(c, cudaFuncSetAttribute(eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  double *d = nullptr;
+  size_t per = (size_t)G.M + 4;
+  CUDA_TRY(c, cudaMalloc(&d, count * per * 8));
+  double *dz = d, *dl = d + count * G.M, *dI = dl + count, *dK = dI + count, *dy = dK + count;
+  unsigned grid = (unsigned)std::min<uint64_t>((count + bs - 1) / bs, (uint64_t)c->sm_count * 8);
+  eval_kernel<<<grid, bs, smem, c->stream>>>(G, first, count, seed, dz, dl, dI, dK, dy);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && z) e = cudaMemcpy(z, dz, count * G.M * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && log2g) e = cudaMemcpy(log2g, dl, count * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && I) e = cudaMemcpy(I, dI, count * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && K) e = cudaMemcpy(K, dK, count * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && y) e = cudaMemcpy(y, dy, count * 8, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(c, AE_ERR_CUDA, std::string("eval_samples: ") + cudaGetErrorString(e));
+  return AE_OK;
+}
+
+extern "C" int ae_eval_samples_dd(ae_ctx *c, int gid, uint64_t first, uint64_t count, uint64_t seed,
+                                  double *I, double *K, double *y) {
+  if (!c) return AE_ERR_ARG;
+  if (c->device < 0) return fail(c, AE_ERR_NODEV, "eval_samples_dd needs a CUDA device");
+  if (gid < 0 || gid >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
+  if (count == 0) return AE_OK;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  GraphDev &G = c->graphs[gid].dev;
+  int bs = pick_block(c, G.nslots, 16);
+  if (bs < 0) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
+  size_t smem = (size_t)bs * G.nslots * 16;
+  CUDA_TRY(c, cudaFuncSetAttribute(eval_dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  double *d = nullptr;
+  CUDA_TRY(c, cudaMalloc(&d, count * 3 * 8));
+  unsigned grid = (unsigned)std::min<uint64_t>((count + bs - 1) / bs, (uint64_t)c->sm_count * 8);
+  eval_dd_kernel<<<grid, bs, smem, c->stream>>>(G, first, count, seed, d, d + count, d + 2 * count);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && I) e = cudaMemcpy(I, d, count * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && K) e = cudaMemcpy(K, d + count, count * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && y) e = cudaMemcpy(y, d + 2 * count, count * 8, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(c, AE_ERR_CUDA, std::string("eval_samples_dd: ") + cudaGetErrorString(e));
+  return AE_OK;
+}
+
+extern "C" int ae_philox(ae_ctx *c, const uint32_t *ctr, const uint32_t *key, uint32_t *out, size_t count) {
+  if (!c || !ctr || !key || !out) return AE_ERR_ARG;
+  if (c->device < 0) return fail(c, AE_ERR_NODEV, "philox needs a CUDA device");
+  if (count == 0) return AE_OK;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  uint32_t *d = nullptr;
+  CUDA_TRY(c, cudaMalloc(&d, count * 40));
+  uint32_t *dc = d, *dk = d + 4 * count, *dout = dk + 2 * count;
+  cudaError_t e = cudaMemcpy(dc, ctr, count * 16, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dk, key, count * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    philox_kernel<<<(unsigned)((count + 255) / 256), 256, 0, c->stream>>>(dc, dk, dout, count);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, count * 16, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(c, AE_ERR_CUDA, std::string("philox: ") + cudaGetErrorString(e));
+  return AE_OK;
+}
+
+extern "C" int ae_fp64_peak(ae_ctx *c, double *tflops) {
+  if (!c || !tflops) return AE_ERR_ARG;
+  if (c->device < 0) return fail(c, AE_ERR_NODEV, "fp64 probe needs a CUDA device");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  double *sink = nullptr;
+  CUDA_TRY(c, cudaMalloc(&sink, 8));
+  const int iters = 1 << 14, bs = 256;
+  int per_sm = 0;
+  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dfma_probe_kernel, bs, 0));
+  unsigned grid = (unsigned)(c->sm_count * std::max(per_sm, 1));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0); cudaEventCreate(&e1);
+  double best = 0;
+  for (int rep = 0; rep < 6; ++rep) {
+    cudaEventRecord(e0, c->stream);
+    dfma_probe_kernel<<<grid, bs, 0, c->stream>>>(iters, 0.999999, 1e-7, sink);
+    cudaEventRecord(e1, c->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { cudaFree(sink); return fail(c, AE_ERR_CUDA, cudaGetErrorString(e)); }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    double fl = 2.0 * 8.0 * iters * (double)grid * bs;
+    if (rep > 0) best = std::max(best, fl / (ms * 1e-3) / 1e12);
+  }
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  cudaFree(sink);
+  *tflops = best;
+  return AE_OK;
+}
+
+extern "C" int ae_density_tables(ae_ctx *c, int gid, double *deg, double *phi) {
+  if (!c || !deg || !phi) return AE_ERR_ARG;
+  if (gid < 0 || gid >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
+  const DensityTables &d = c->graphs[gid].dens;
+  size_t T = (size_t)1 << d.M;
+  for (int k = 0; k < 3; ++k) {
+    std::copy(d.deg[k].begin(), d.deg[k].end(), deg + k * T);
+    std::copy(d.phi[k].begin(), d.phi[k].end(), phi + k * T);
+  }
+  return AE_OK;
+}
+
+extern "C" int ae_subgraphs(ae_ctx *c, int gid, int *buf, int cap, int *len) {
+  if (!c || !len) return AE_ERR_ARG;
+  if (gid < 0 || gid >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
+  std::vector<int> v;
+  for (auto &s : c->graphs[gid].subs) { v.push_back(s.lo); v.push_back(s.hi); v.push_back(s.se ? 0 : (s.inJ ? 2 : 1)); }
+  *len = (int)v.size();
+  if (buf && cap >= (int)v.size()) std::copy(v.begin(), v.end(), buf);
+  else if (buf) return fail(c, AE_ERR_ARG, "buffer too small");
+  return AE_OK;
+}
+
+extern "C" int ae_terms(ae_ctx *c, int gid, int *buf, int cap, int *len) {
+  if (!c || !len) return AE_ERR_ARG;
+  if (gid < 0 || gid >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
+  const LoadedGraph &lg = c->graphs[gid];
+  std::vector<int> v;
+  for (auto &t : lg.terms) {
+    v.push_back(t.sign); v.push_back((int)t.elems.size());
+    for (size_t i = 0; i < t.elems.size(); ++i) {
+      v.push_back(lg.subs[t.elems[i]].lo); v.push_back(lg.subs[t.elems[i]].hi); v.push_back(t.ops[i]);
+    }
+  }
+  *len = (int)v.size();
+  if (buf && cap >= (int)v.size()) std::copy(v.begin(), v.end(), buf);
+  else if (buf) return fail(c, AE_ERR_ARG, "buffer too small");
+  return AE_OK;
+}
+
+extern "C" int aetest_tape_replay(ae_ctx *c, int gid, const double *z, size_t count, double *I, double *K) {
+  if (!c || !z || !I || !K) return AE_ERR_ARG;
+  if (gid < 0 || gid >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
+  const Tape &t = c->graphs[gid].tape;
+  for (size_t i = 0; i < count; ++i) tape_replay(t, z + i * t.M, I + i, K + i);
+  return AE_OK;
+}

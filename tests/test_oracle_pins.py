@@ -1,0 +1,271 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test ties one part of the oracle to something other than itself: a
+count or expression printed in the paper, a published test vector, a closed
+form, an invariant, or brute force on a tiny input.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dirac
+from oracle.forest import divergent_subgraphs, terms as forest_terms
+from oracle.graphs import Graph, enumerate_graphs, class_counts, perfect_matchings, is_1pi, word_of
+from oracle.integrand import Integrand
+from oracle.philox import philox4x32_10, uniforms
+from oracle.sampler import Density, sample, log2_series, exp2_series, deg_table, phi_table
+from oracle.estimate import GraphOracle, summarize, weight
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------ graph set ---
+def test_graph_counts_and_table_I():
+    """3213 graphs at 5 loops (Sec. I) and Table I's N_diag per class."""
+    gs = enumerate_graphs(5)
+    assert len(gs) == 3213
+    want = {}
+    for line in open(os.path.join(GOLD, "table1_ndiag.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, m, mp, nd = map(int, line.split())
+        want[(k, m, mp)] = nd
+    assert class_counts(gs) == want
+
+
+def test_small_counts_by_brute_force():
+    """1..4 loops: compare with a direct count of all oriented 1PI graphs
+    (no canonical-form machinery): oriented = sum of multiplicities."""
+    for n in (1, 2, 3, 4):
+        oriented = 0
+        for m in perfect_matchings(list(range(2 * n))):
+            for s in range(2 * n + 1):
+                pos = lambda x: x if x < s else x + 1
+                partner = [None] * (2 * n + 1)
+                for a, b in m:
+                    partner[pos(a)] = pos(b)
+                    partner[pos(b)] = pos(a)
+                if is_1pi(partner, s):
+                    oriented += 1
+        gs = enumerate_graphs(n)
+        # every labelled matching is a distinct oriented graph
+        assert sum(g.mult for g in gs) == oriented
+    assert [len(enumerate_graphs(n)) for n in (1, 2, 3, 4)] == [1, 4, 28, 269]
+
+
+def test_subgraphs_are_intervals():
+    for n in (2, 3, 4):
+        for g in enumerate_graphs(n)[::7]:
+            for S in divergent_subgraphs(g):
+                v = sorted(S.verts)
+                assert v == list(range(v[0], v[-1] + 1))
+
+
+def _parse_example():
+    lines = [l.split() for l in open(os.path.join(GOLD, "worked_example.txt"))
+             if l.strip() and not l.startswith("#")]
+    photons = [tuple(map(int, t.split("-"))) for t in lines[0][1:]]
+    ext = int(lines[1][1])
+    brackets = []
+    for l in lines[2:]:
+        alts = " ".join(l[1:]).split("|")
+        opts = []
+        for a in alts:
+            a = a.strip()
+            sign = -1 if a[0] == "-" else 1
+            items = [x for x in a[1:].split(",") if x]
+            opts.append((sign, [tuple(x.split("@")) for x in items]))
+        brackets.append(opts)
+    return photons, ext, brackets
+
+
+def test_worked_example_expression():
+    """R^new of the graph of Sec. II equals the printed expression
+    (Eq. eq_example_expression) term by term."""
+    photons, ext, brackets = _parse_example()
+    partner = [None] * 11
+    for a, b in photons:
+        partner[a], partner[b] = b, a
+    g = Graph(partner, ext)
+    name = lambda S: "".join("abcdefghijk"[v] for v in sorted(S.verts))
+    got = {}
+    for sign, ops in forest_terms(g):
+        key = tuple(sorted((op.replace("L-U", "LmU"), name(S)) for S, op in ops))
+        got[key] = got.get(key, 0) + sign
+    want = {}
+    for combo in itertools.product(*brackets):
+        sign = 1
+        items = []
+        for s, its in combo:
+            sign *= s
+            items += [(op, sub) for op, sub in its]
+        key = tuple(sorted(items))
+        want[key] = want.get(key, 0) + sign
+    assert got == want
+
+
+# --------------------------------------------------------------- Philox ---
+def test_philox_known_answers():
+    for line in open(os.path.join(GOLD, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        assert list(philox4x32_10(w[:4], w[4:6])) == w[6:10]
+
+
+def test_uniforms_open_interval():
+    u = uniforms(np.arange(20000), 3, 12345, 4)
+    assert u.min() > 0 and u.max() < 1
+    assert abs(u.mean() - 0.5) < 0.005
+
+
+# --------------------------------------------------- elementary functions ---
+def test_log2_exp2_series_accuracy():
+    rng = np.random.default_rng(0)
+    x = np.exp(rng.uniform(-700, 700, 20000))
+    l = log2_series(x)
+    assert np.all(np.abs(l - np.log2(x)) <= 4 * np.spacing(np.abs(np.log2(x))) + 1e-300)
+    t = rng.uniform(-1000, 1000, 20000)
+    assert np.all(np.abs(exp2_series(t) / np.exp2(t) - 1) < 4e-16)
+
+
+# ---------------------------------------------------------------- pdf -----
+@pytest.mark.parametrize("n,gi", [(1, 0), (2, 1), (3, 5)])
+def test_density_normalisation(n, gi):
+    """E_g[1/g] = simplex volume 1/(M-1)!; E_g[z_0/g] = 1/M!."""
+    g = enumerate_graphs(n)[gi]
+    d = Density(g)
+    M = d.M
+    N = 200000
+    u = uniforms(np.arange(N), gi, 7, M)
+    z, lg, _ = sample(d, u)
+    w = np.exp2(-lg)
+    m1 = w.mean() * math.factorial(M - 1)
+    s1 = w.std() / math.sqrt(N) * math.factorial(M - 1)
+    assert abs(m1 - 1) < 4 * s1 + 1e-3
+    m2 = (z[:, 0] * w).mean() * math.factorial(M)
+    s2 = (z[:, 0] * w).std() / math.sqrt(N) * math.factorial(M)
+    assert abs(m2 - 1) < 4 * s2 + 1e-3
+
+
+def test_sector_probabilities_exact():
+    """Sector frequencies of the pure-g1 walk against prod 1/Deg / Phi(all)
+    by explicit enumeration of all orderings (M = 5)."""
+    g = enumerate_graphs(2)[0]
+    d = Density(g, C2=0.0, C3=0.0, C4=0.0)
+    M = d.M
+    deg = d.deg[0]
+    probs = {}
+    for perm in itertools.permutations(range(M)):
+        T = (1 << M) - 1
+        p = 1.0
+        for j in perm[:-1]:
+            T ^= 1 << j
+            p /= deg[T]
+        probs[perm] = p
+    tot = sum(probs.values())
+    assert abs(tot - d.phi[0][(1 << M) - 1]) < 1e-12 * tot
+    N = 100000
+    u = uniforms(np.arange(N), 0, 3, M)
+    z, lg, _ = sample(d, u)
+    order = np.argsort(-z, axis=1, kind="stable")
+    cnt = {}
+    for row in order:
+        cnt[tuple(row)] = cnt.get(tuple(row), 0) + 1
+    chi2 = sum((cnt.get(k, 0) - N * v / tot) ** 2 / (N * v / tot) for k, v in probs.items())
+    dof = len(probs) - 1
+    assert chi2 < dof + 5 * math.sqrt(2 * dof)
+
+
+# --------------------------------------------------------------- Dirac ----
+def test_dirac_identities():
+    rng = np.random.default_rng(1)
+    sl = lambda v: sum(dirac.METRIC[m] * v[m] * dirac.GAMMA[m] for m in range(4))
+    a, b, c, d = (rng.normal(size=4) for _ in range(4))
+    dot = lambda x, y: float(np.sum(dirac.METRIC * x * y))
+    assert abs(dirac.trace([dirac.ONE]) - 4) < 1e-12
+    assert abs(dirac.trace([("g", 1), ("g", 1)]) - 16) < 1e-12
+    t4 = dirac.trace([sl(a), sl(b), sl(c), sl(d)])
+    assert abs(t4 - 4 * (dot(a, b) * dot(c, d) - dot(a, c) * dot(b, d) + dot(a, d) * dot(b, c))) < 1e-9
+    lhs = dirac.trace([("g", 1), sl(a), sl(b), sl(c), ("g", 1), sl(d)])
+    rhs = -2 * np.trace(sl(c) @ sl(b) @ sl(a) @ sl(d))
+    assert abs(lhs - rhs) < 1e-9
+
+
+# ------------------------------------------------------------ integrand ---
+def test_one_loop_quadrature_is_half():
+    """A_1^(2) = 1/2 (Sec. I) by Gauss-Legendre on the 1-simplex; the
+    1-loop integrand is a polynomial, so the rule is exact."""
+    g = enumerate_graphs(1)[0]
+    I = Integrand(g)
+    x, w = np.polynomial.legendre.leggauss(8)
+    t = 0.5 * (x + 1)
+    val = sum(0.5 * wi * I.evaluate(np.array([ti, 1 - ti]))[0] for ti, wi in zip(t, w))
+    assert abs(val - 0.5) < 1e-14
+
+
+def _mirror_graph(g):
+    N = g.nverts
+    p = [None] * N
+    for v in range(N):
+        if v != g.s:
+            p[N - 1 - v] = N - 1 - g.partner[v]
+    return Graph(p, N - 1 - g.s)
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_mirror_invariance(n):
+    """A graph and its arrow-reversed image give the same integrand at
+    corresponding points (charge conjugation; graphs that differ only by
+    arrow direction are one graph, Sec. I).  Fails if the AMM projector
+    picks up the q^mu structure."""
+    rng = np.random.default_rng(n)
+    for g in enumerate_graphs(n):
+        if g.mult != 2:
+            continue
+        h = _mirror_graph(g)
+        Ig, Ih = Integrand(g), Integrand(h)
+        ig, ih = g.line_index(), h.line_index()
+        N = g.nverts
+        for _ in range(2):
+            z = rng.dirichlet(np.ones(3 * n - 1))
+            zh = np.empty_like(z)
+            for key, i in ig.items():
+                if key[0] == 'e':
+                    mk = ('e', N - key[1])
+                else:
+                    mk = ('g', N - 1 - key[2], N - 1 - key[1])
+                zh[ih[mk]] = z[i]
+            a, b = Ig.evaluate(z)[0], Ih.evaluate(zh)[0]
+            assert abs(a - b) <= 1e-11 * max(abs(a), 1.0)
+        if n == 3:
+            break
+
+
+def test_two_loop_finiteness():
+    """Subtracted integrands are integrable: shrinking any subset of lines,
+    |I| * lambda^|s| vanishes as a positive power of lambda (UV and IR)."""
+    rng = np.random.default_rng(5)
+    for g in enumerate_graphs(2):
+        I = Integrand(g)
+        M = 5
+        for r in range(1, M):
+            for s in itertools.combinations(range(M), r):
+                z0 = rng.dirichlet(np.ones(M))
+                vals = []
+                for lam in (1e-6, 1e-8):
+                    z = z0.copy()
+                    z[list(s)] *= lam
+                    z /= z.sum()
+                    vals.append(abs(I.evaluate(z)[0]) * lam ** r + 1e-300)
+                slope = math.log(vals[1] / vals[0]) / math.log(1e-8 / 1e-6)
+                assert slope > 0.3, (g.word, s, slope)
+
+
+def test_weight_range_safe():
+    assert weight(3.0, 1.0) == 1.5
+    assert weight(1.0, 2000.0) == 2.0 ** -2000 or weight(1.0, 2000.0) == 0.0
+    assert weight(2.0 ** -1000, -1500.0) == 2.0 ** 500
