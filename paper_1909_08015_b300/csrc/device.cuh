@@ -27,16 +27,29 @@ __device__ __forceinline__ double u01(uint32_t w0, uint32_t w1) {
 }
 
 // ------------------------------------------------- log2 / exp2 (series) ---
-// The same sequence of IEEE operations as the host's ae_log2/ae_exp2.
+// The same sequence of IEEE operations as the host's ae_log2/ae_exp2.  The
+// series coefficients 1/(2i+1) and 1/k! are the exact double quotients of
+// those definitions (IEEE division is deterministic), stored as constants.
+__device__ __constant__ double kInvOdd[12] = {
+    0.04, 0.043478260869565216, 0.047619047619047616, 0.05263157894736842,
+    0.058823529411764705, 0.06666666666666667, 0.07692307692307693, 0.09090909090909091,
+    0.1111111111111111, 0.14285714285714285, 0.2, 0.3333333333333333};   // 1/25, 1/23, ..., 1/3
+__device__ __constant__ double kInvFact[19] = {
+    1.5619206968586225e-16, 2.8114572543455206e-15, 4.779477332387385e-14, 7.647163731819816e-13,
+    1.1470745597729725e-11, 1.6059043836821613e-10, 2.08767569878681e-09, 2.505210838544172e-08,
+    2.755731922398589e-07, 2.7557319223985893e-06, 2.48015873015873e-05, 0.0001984126984126984,
+    0.001388888888888889, 0.008333333333333333, 0.041666666666666664, 0.16666666666666666,
+    0.5, 1.0, 1.0};   // 1/18!, 1/17!, ..., 1/0!
+
 __device__ __forceinline__ double dlog2(double x) {
   int k;
   double f = frexp(x, &k);
   if (f < 0.7071067811865476) { f = __dmul_rn(f, 2.0); k = k - 1; }
   double s = __ddiv_rn(__dadd_rn(f, -1.0), __dadd_rn(f, 1.0));
   double s2 = __dmul_rn(s, s);
-  double p = __ddiv_rn(1.0, 25.0);
+  double p = kInvOdd[0];
 #pragma unroll
-  for (int d = 23; d >= 3; d -= 2) p = __dadd_rn(__dmul_rn(p, s2), __ddiv_rn(1.0, (double)d));
+  for (int i = 1; i < 12; ++i) p = __dadd_rn(__dmul_rn(p, s2), kInvOdd[i]);
   p = __dadd_rn(__dmul_rn(p, s2), 1.0);
   double lnf = __dmul_rn(__dadd_rn(s, s), p);
   return __dadd_rn((double)k, __dmul_rn(lnf, 1.4426950408889634));
@@ -45,13 +58,9 @@ __device__ __forceinline__ double dlog2(double x) {
 __device__ __forceinline__ double dexp2(double x) {
   double k = floor(__dadd_rn(x, 0.5));
   double r = __dmul_rn(__dadd_rn(x, -k), 0.6931471805599453);
-  double fact = 6402373705728000.0;
-  double p = __ddiv_rn(1.0, fact);
+  double p = kInvFact[0];
 #pragma unroll
-  for (int i = 18; i >= 1; --i) {
-    fact = __ddiv_rn(fact, (double)i);
-    p = __dadd_rn(__dmul_rn(p, r), __ddiv_rn(1.0, fact));
-  }
+  for (int i = 1; i < 19; ++i) p = __dadd_rn(__dmul_rn(p, r), kInvFact[i]);
   double kc = fmin(fmax(k, -100000.0), 100000.0);
   return ldexp(p, (int)kc);
 }

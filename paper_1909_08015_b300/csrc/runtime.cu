@@ -632,7 +632,7 @@ static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_g
     uint64_t len = std::min(SLICE, nsamp - start);
     uint64_t grid = (uint64_t)c->sm_count * per_sm;
     if (grid * bs > len) grid = std::max<uint64_t>(1, (len + bs - 1) / bs);
-    size_t qcap = (size_t)std::max<uint64_t>(len / 4, 65536);
+    size_t qcap = (size_t)std::max<uint64_t>(len, 65536);   // every sample may need re-evaluation
     int rc = ensure_scratch(c, grid, qcap);
     if (rc) return rc;
     CUDA_TRY(c, cudaMemsetAsync(c->d_qcount, 0, sizeof(unsigned long long), c->stream));
