@@ -101,6 +101,39 @@ int ae_integrate_batched(ae_ctx *ctx, const int *graph_ids, int n_ids,
                          const uint64_t *n_samples, uint64_t seed, double *value,
                          double *sigma, ae_graph_result *per_graph);
 
+/* Integration of one graph that allocates nothing.
+ *
+ * For callers that cannot allocate device memory once they are running:
+ * for example a host process whose device memory is entirely reserved up
+ * front by another framework's caching allocator, or a service loop that
+ * must not call cudaMalloc/cudaFree after start-up because those calls
+ * synchronise the device and have unbounded latency.  The paper has no
+ * counterpart; this is a property of the library, not of the method.
+ *
+ * Same computation as ae_integrate for a single graph (FP64 integrand,
+ * double-double re-evaluation of samples with K > dd_ratio |I|, fixed-order
+ * reduction), but every intermediate lives in one fixed device array of
+ * about 8.3 MB that the library declares statically; each GPU that loads the
+ * library holds that array until the process exits.  The caller passes the
+ * inputs (graph id, sample count, seed) and receives the result in *out
+ * (host memory); value, sigma, mean, sigma1, mean_abs, sum_y, sum_y2, max_y2,
+ * n, n_dd and n_nonfinite are filled, seconds and the byte counters are 0.
+ *
+ * Limits and behaviour:
+ *  - n_samples must be 1..524288 (every sample may need the double-double
+ *    pass, and the array holds one slot per sample); larger values return
+ *    AE_ERR_ARG without launching anything;
+ *  - the first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture;
+ *  - every call on a device uses the same array and it keeps the previous
+ *    call's contents; the call clears what must start at zero.  Calls whose
+ *    work overlaps on the GPU (two host threads, or two streams) race on the
+ *    array and give wrong results: serialise them.
+ * The result equals ae_integrate's for the same (graph, n_samples, seed) up
+ * to the summation order of the re-evaluated samples. */
+int ae_integrate_noalloc(ae_ctx *ctx, int graph_id, uint64_t n_samples, uint64_t seed,
+                         ae_graph_result *out);
+
 /* Per-sample dump for parity tests: samples first .. first+count-1 of
  * graph_id under `seed`.  z: count*M, log2g, I, K, y: count each (any may be
  * NULL).  Host buffers. */

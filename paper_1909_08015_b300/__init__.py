@@ -70,6 +70,7 @@ def lib():
                                    dp, dp, P(AeGraphResult)]
         L.ae_integrate_batched.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_uint64),
                                            ctypes.c_uint64, dp, dp, P(AeGraphResult)]
+        L.ae_integrate_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, P(AeGraphResult)]
         L.ae_eval_samples.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                       dp, dp, dp, dp, dp]
         L.ae_eval_samples_dd.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
@@ -157,6 +158,13 @@ class Context:
                                                _ptr(ns, ctypes.c_uint64), int(seed),
                                                ctypes.byref(v), ctypes.byref(s), res))
         return v.value, s.value, [r.as_dict() for r in res]
+
+    def integrate_noalloc(self, gid, n_samples, seed=0):
+        """One graph through the entry point that allocates no device memory
+        (fixed static scratch; n_samples <= 524288)."""
+        r = AeGraphResult()
+        self._check(lib().ae_integrate_noalloc(self._h, gid, int(n_samples), int(seed), ctypes.byref(r)))
+        return r.as_dict()
 
     def eval_samples(self, gid, first, count, seed=0):
         M = self.graph_info(gid)["M"]

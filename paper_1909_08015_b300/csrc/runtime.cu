@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -420,6 +421,74 @@ __global__ void philox_kernel(const uint32_t *ctr, const uint32_t *key, uint32_t
   for (int k = 0; k < 4; ++k) out[4 * i + k] = c[k];
 }
 
+// ------------------------------------------- no-allocation entry point ---
+// Scratch of ae_integrate_noalloc: one file-scope device array, shared by all
+// calls on a device and kept between them.  Layout (bytes from the start):
+//   [0, kNaPartBytes)          per-CTA partials (at most kNaMaxGrid)
+//   next 256                   queue counter + final result
+//   queue                      sample indices needing double-double (u64)
+//   y                          double-double value per sample offset
+//   flag                       1 byte per sample offset (set by the dd pass)
+constexpr uint64_t kNaMaxSamples = 1ull << 19;   // samples per call
+constexpr int kNaMaxGrid = 2048;                 // CTAs per launch
+constexpr size_t kNaPartBytes = (size_t)kNaMaxGrid * sizeof(Partial);
+constexpr size_t kNaCtlBytes = 256;
+constexpr size_t kNaQueueOff = kNaPartBytes + kNaCtlBytes;
+constexpr size_t kNaYOff = kNaQueueOff + kNaMaxSamples * 8;
+constexpr size_t kNaFlagOff = kNaYOff + kNaMaxSamples * 8;
+constexpr size_t kNaScratchBytes = kNaFlagOff + kNaMaxSamples;   // about 8.3 MB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes];
+
+// Double-double pass writing by sample offset (deterministic order later).
+__global__ void dd_dense_kernel(GraphDev G, uint64_t first, uint64_t seed, const unsigned long long *queue,
+                                const unsigned long long *qcount, double *y_off, unsigned char *flag) {
+  extern __shared__ dd dsl3[];
+  dd *S = dsl3 + threadIdx.x;
+  const int stride = blockDim.x;
+  uint64_t nq = *qcount;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t idx = queue[i];
+    double z[14], lz[14], lg;
+    draw_sample(G, idx, seed, z, lz, lg);
+    for (int k = 0; k < G.M; ++k) S[k * stride] = {z[k], 0.0};
+    run_tape_dd(G, S, stride);
+    dd I = S[G.outI * stride], K = S[G.outK * stride];
+    double y = weight(I.hi + I.lo, lg);
+    bool bad = !isfinite(I.hi) || !isfinite(K.hi) || !isfinite(y) || K.hi > 2.0e23 * fabs(I.hi);
+    y_off[idx - first] = bad ? 0.0 : y;
+    flag[idx - first] = bad ? 2 : 1;
+  }
+}
+
+// One CTA: partials in CTA order, then re-evaluated samples in a fixed
+// strided order; result[0] = merged partial, result counters in n_flag
+// (re-evaluated) and n_overflow (zeroed).
+__global__ void noalloc_reduce_kernel(const Partial *part, int nparts, const double *y_off,
+                                      const unsigned char *flag, uint64_t count, Partial *result) {
+  Partial p = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+    const Partial &q = part[b];
+    dd_merge(p.sy_hi, p.sy_lo, q.sy_hi, q.sy_lo);
+    dd_merge(p.sy2_hi, p.sy2_lo, q.sy2_hi, q.sy2_lo);
+    dd_merge(p.sa_hi, p.sa_lo, q.sa_hi, q.sa_lo);
+    p.max_y2 = fmax(p.max_y2, q.max_y2);
+    p.n += q.n;
+  }
+  for (uint64_t i = threadIdx.x; i < count; i += blockDim.x) {
+    unsigned char f = flag[i];
+    if (!f) continue;
+    double y = y_off[i];
+    dd_acc(p.sy_hi, p.sy_lo, y);
+    dd_acc(p.sy2_hi, p.sy2_lo, y * y);
+    dd_acc(p.sa_hi, p.sa_lo, fabs(y));
+    p.max_y2 = fmax(p.max_y2, y * y);
+    p.n_flag += 1;
+    if (f == 2) p.n_overflow += 1;
+  }
+  block_reduce(p, result);
+}
+
 // ============================================================ host ABI ===
 extern "C" void ae_default_opts(ae_opts *o) {
   o->C2 = 0.03; o->C3 = 0.01; o->C4 = 0.06; o->D = 0.75;
@@ -772,6 +841,88 @@ extern "C" int ae_eval_samples(ae_ctx *c, int gid, uint64_t first, uint64_t coun
   if (e == cudaSuccess && y) e = cudaMemcpy(y, dy, count * 8, cudaMemcpyDeviceToHost);
   cudaFree(d);
   if (e != cudaSuccess) return fail(c, AE_ERR_CUDA, std::string("eval_samples: ") + cudaGetErrorString(e));
+  return AE_OK;
+}
+
+// Device address of g_noalloc_scratch, looked up once per device (with that
+// device current) the first time ae_integrate_noalloc runs on it.
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[256];
+
+extern "C" int ae_integrate_noalloc(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed,
+                                    ae_graph_result *out) {
+  if (!c || !out) return AE_ERR_ARG;
+  if (c->device < 0) return fail(c, AE_ERR_NODEV, "integrate_noalloc needs a CUDA device");
+  if (c->graphs.empty()) return fail(c, AE_ERR_STATE, "no graphs loaded");
+  if (gid < 0 || gid >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
+  if (nsamp == 0 || nsamp > kNaMaxSamples)
+    return fail(c, AE_ERR_ARG, "n_samples must be 1..524288 for ae_integrate_noalloc "
+                               "(fixed scratch of the no-allocation path)");
+  if (c->device >= 256) return fail(c, AE_ERR_ARG, "device index too large for the no-allocation path");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  unsigned char *scr = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[c->device]) {
+      void *p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p)
+        return fail(c, AE_ERR_CUDA, std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
+      g_noalloc_addr[c->device] = p;
+    }
+    scr = (unsigned char *)g_noalloc_addr[c->device];
+  }
+  Partial *part = (Partial *)scr;
+  unsigned long long *qcount = (unsigned long long *)(scr + kNaPartBytes);
+  Partial *result = (Partial *)(scr + kNaPartBytes + 128);
+  unsigned long long *queue = (unsigned long long *)(scr + kNaQueueOff);
+  double *y_off = (double *)(scr + kNaYOff);
+  unsigned char *flag = scr + kNaFlagOff;
+  GraphDev &G = c->graphs[gid].dev;
+  int bs = pick_block(c, G.nslots, 8);
+  if (bs < 0) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
+  size_t smem = (size_t)bs * G.nslots * 8;
+  CUDA_TRY(c, cudaFuncSetAttribute(integrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = c->opts.ctas_per_sm;
+  if (per_sm <= 0) {
+    CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integrate_kernel, bs, smem));
+    if (per_sm < 1) per_sm = 1;
+  }
+  uint64_t grid = std::min<uint64_t>((uint64_t)c->sm_count * per_sm, (uint64_t)kNaMaxGrid);
+  if (grid * bs > nsamp) grid = std::max<uint64_t>(1, (nsamp + bs - 1) / bs);
+  // what must start at zero: the queue counter and the per-sample flags
+  CUDA_TRY(c, cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(flag, 0, nsamp, c->stream));
+  integrate_kernel<<<(unsigned)grid, bs, smem, c->stream>>>(G, 0, nsamp, seed, c->opts.dd_ratio, part, queue,
+                                                            kNaMaxSamples, qcount);
+  CUDA_TRY(c, cudaGetLastError());
+  int bsd = pick_block(c, G.nslots, 16);
+  if (bsd < 0) return fail(c, AE_ERR_STATE, "double-double slot file does not fit in shared memory");
+  size_t sm2 = (size_t)bsd * G.nslots * 16;
+  CUDA_TRY(c, cudaFuncSetAttribute(dd_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+  dd_dense_kernel<<<(unsigned)(c->sm_count * 2), bsd, sm2, c->stream>>>(G, 0, seed, queue, qcount, y_off, flag);
+  CUDA_TRY(c, cudaGetLastError());
+  noalloc_reduce_kernel<<<1, 256, 0, c->stream>>>(part, (int)grid, y_off, flag, nsamp, result);
+  CUDA_TRY(c, cudaGetLastError());
+  Partial r;
+  CUDA_TRY(c, cudaMemcpyAsync(&r, result, sizeof(Partial), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  std::memset(out, 0, sizeof(*out));
+  out->sum_y = r.sy_hi + r.sy_lo;
+  out->sum_y2 = r.sy2_hi + r.sy2_lo;
+  out->n = r.n;
+  out->n_dd = r.n_flag;
+  out->n_nonfinite = r.n_overflow;
+  double N = (double)r.n;
+  out->mean = out->sum_y / N;
+  double var = out->sum_y2 / (N * N) - out->sum_y * out->sum_y / (N * N * N);
+  out->sigma1 = var > 0 ? std::sqrt(var) : 0.0;
+  out->mean_abs = (r.sa_hi + r.sa_lo) / N;
+  out->max_y2 = r.max_y2;
+  int mult = c->graphs[gid].g.mult;
+  out->value = mult * out->mean;
+  out->sigma = mult * out->sigma1;
+  out->launches = 3;
   return AE_OK;
 }
 
