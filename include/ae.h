@@ -37,6 +37,8 @@ typedef struct ae_opts {
   double C2, C3, C4, D;              /* mixture weights of g2, g3, g4; g3 flattening */
   double C_subI, C_subSE, C_subO;    /* Deg(s) constants used by the library      */
   double C_bigZ, C_bigF, C_add;      /* Deg(s) constants kept, not used           */
+  double deg_max;                    /* cap on Deg(s) (library reading, see the
+                                        design notes); <= 0 means no cap          */
   double dd_ratio;                   /* re-evaluate in double-double when
                                         K > dd_ratio * |I| (default 1e8); <= 0 off */
   int block_size;                    /* threads per CTA, 0 = automatic            */

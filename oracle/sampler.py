@@ -19,7 +19,11 @@ Readings of what the paper leaves to its missing references:
     (power counting in Feynman-parameter units; the merged line is two
     electron propagators).  Deg(s) = d0(s) when d0(s) > 0, otherwise
     1/2 - C_sub with C_sub = C_subI (merged line in s), C_subSE (d0 < 0) or
-    C_subO (d0 = 0), constants of Eq. eq_mc_settings.  C_bigZ, C_bigF and
+    C_subO (d0 = 0), constants of Eq. eq_mc_settings; then capped at
+    deg_max (default 1): d0 counts only ultraviolet scaling, and where the
+    shrinking set is a forest of electron lines the integrand decays only
+    like lambda^1 (soft photons in the complement), so a steeper density
+    would have infinite variance.  C_bigZ, C_bigF and
     C_add are kept as named parameters; their role is not stated in the
     paper and they are unused.
   * g2 = uniform density (M-1)!; g3 = g1 with Deg -> D*Deg;
@@ -121,7 +125,10 @@ class LineSets:
         return ne / 2.0 + ng - 2.0 * self.loops(mask) + (0.5 if mask & 1 else 0.0)
 
 
-def deg_table(g):
+DEG_MAX = 1.0
+
+
+def deg_table(g, deg_max=DEG_MAX):
     """Deg(s) for every bitmask s (index 0 and the full set are unused)."""
     ls = LineSets(g)
     M = ls.M
@@ -136,6 +143,8 @@ def deg_table(g):
             out[s] = 0.5 - C_SUBSE
         else:
             out[s] = 0.5 - C_SUBO
+        if deg_max > 0 and out[s] > deg_max:
+            out[s] = deg_max
     return out
 
 
@@ -158,10 +167,11 @@ def phi_table(deg, M):
 class Density:
     """Tables of the three sector densities g1, g3, g4 of one graph."""
 
-    def __init__(self, g, C2=CALC2['C2'], C3=CALC2['C3'], C4=CALC2['C4'], D=CALC2['D']):
+    def __init__(self, g, C2=CALC2['C2'], C3=CALC2['C3'], C4=CALC2['C4'], D=CALC2['D'],
+                 deg_max=DEG_MAX):
         self.M = 3 * g.n - 1
         M = self.M
-        d1 = deg_table(g)
+        d1 = deg_table(g, deg_max)
         self.deg = [d1, d1 * D, np.minimum(d1, 0.5)]
         self.phi = [phi_table(d, M) for d in self.deg]
         self.C = [1.0 - C2 - C3 - C4, C3, C4]      # mixture weights of g1, g3, g4

@@ -23,7 +23,7 @@ class AeOpts(ctypes.Structure):
     _fields_ = [("C2", ctypes.c_double), ("C3", ctypes.c_double), ("C4", ctypes.c_double),
                 ("D", ctypes.c_double), ("C_subI", ctypes.c_double), ("C_subSE", ctypes.c_double),
                 ("C_subO", ctypes.c_double), ("C_bigZ", ctypes.c_double), ("C_bigF", ctypes.c_double),
-                ("C_add", ctypes.c_double), ("dd_ratio", ctypes.c_double),
+                ("C_add", ctypes.c_double), ("deg_max", ctypes.c_double), ("dd_ratio", ctypes.c_double),
                 ("block_size", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 

@@ -66,6 +66,7 @@ struct DensityConsts {
   double C2 = 0.03, C3 = 0.01, C4 = 0.06, D = 0.75;  // Calc 2
   double CsubI = 0.2, CsubSE = 0.0, CsubO = 0.2;
   double CbigZ = 0.256, CbigF = 0.839, Cadd = 0.786;  // kept, unused
+  double deg_max = 1.0;                                 // cap on Deg(s); <= 0: none
 };
 // deg[k][mask], phi[k][mask] for the three sector densities g1, g3, g4.
 struct DensityTables {

@@ -1,0 +1,56 @@
+// Host-side context of libae (the object behind the opaque ae_ctx handle).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ae.h"
+#include "ae_internal.h"
+#include "kernels.cuh"
+
+using namespace ae;
+using aek::GraphDev;
+using aek::Partial;
+
+// Learned proposal state of one graph (device tables and network).
+struct LearnedState {
+  bool active = false;
+  double beta = 0.1;
+  void *mem = nullptr;      // device block holding tables and weights
+  size_t bytes = 0;
+  std::vector<float> master;   // FP32 master weights (host copy after training)
+};
+
+struct LoadedGraph {
+  Graph g;
+  std::vector<Sub> subs;
+  std::vector<Term> terms;
+  Tape tape;
+  DensityTables dens;
+  CompileStats st;
+  GraphDev dev{};
+  LearnedState learned;
+};
+
+struct ae_ctx {
+  int device = -1;
+  ae_opts opts;
+  std::string err;
+  std::vector<LoadedGraph> graphs;
+  int loops = 0;
+  void *arena = nullptr;
+  size_t arena_bytes = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = true;
+  // scratch
+  Partial *d_part = nullptr; size_t part_cap = 0;
+  unsigned long long *d_queue = nullptr; size_t queue_cap = 0;
+  unsigned long long *d_qcount = nullptr;
+  double *d_yq = nullptr;
+  int *d_qstat = nullptr;
+};
+
+
+int ae_fail(ae_ctx *c, int code, const std::string &msg);

@@ -5,7 +5,12 @@
 // is the library's reading): power counting in Feynman-parameter units,
 //   d0(s) = n_e(s)/2 + n_gamma(s) - 2 L(s) + 1/2 [merged line in s],
 // Deg(s) = d0(s) if d0(s) > 0, else 1/2 - C_sub with C_sub = C_subI when s
-// holds the merged line, C_subSE when d0 < 0, C_subO when d0 = 0.
+// holds the merged line, C_subSE when d0 < 0, C_subO when d0 = 0; then
+// capped at deg_max.  The cap is needed because d0 counts only ultraviolet
+// scaling: when the shrinking set is a forest of electron lines the
+// photons of the complement are soft and the integrand decays like
+// lambda^1, not lambda^d0, and a steeper density gives infinite variance
+// (finite variance needs Deg(s) < 2 * true exponent).
 // Phi(T) = sum_{j in T} Phi(T\j)/Deg(T\j), Phi({j}) = 1; the sector
 // probability of an ordering is prod 1/Deg(s_l) / Phi(all).
 #include <cmath>
@@ -86,6 +91,7 @@ DensityTables build_density(const Graph &g, const DensityConsts &c) {
     else if (s & 1u) deg = 0.5 - c.CsubI;
     else if (d0 < 0) deg = 0.5 - c.CsubSE;
     else deg = 0.5 - c.CsubO;
+    if (c.deg_max > 0 && deg > c.deg_max) deg = c.deg_max;
     d1[s] = deg;
   }
   for (int k = 0; k < 3; ++k) {

@@ -24,64 +24,17 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ae.h"
-#include "ae_internal.h"
-#include "device.cuh"
+#include "context.h"
 
 using namespace ae;
+using namespace aek;
+using namespace aedev;
 
-// ------------------------------------------------------------ structs ----
-struct GraphDev {
-  const double *deg;      // 3 * 2^M
-  const double *phi;      // 3 * 2^M
-  const double *wt;       // 3 * 2^M: phi/deg (same IEEE quotient as the walk's definition)
-  const uint2 *code;      // tape
-  const double *khi, *klo;
-  int M, ntape, nslots, outI, outK;
-  int graph_id;
-  double C1, C2, C3, C4, log2_fact;
-  double log2C[4];        // log2 of C1..C4 (g1, g2, g3, g4 order)
-  double log2phi_full[3];
-};
-
-struct Partial {
-  double sy_hi, sy_lo, sy2_hi, sy2_lo, sa_hi, sa_lo, max_y2;
-  unsigned long long n, n_flag, n_overflow;
-};
-
-struct LoadedGraph {
-  Graph g;
-  std::vector<Sub> subs;
-  std::vector<Term> terms;
-  Tape tape;
-  DensityTables dens;
-  CompileStats st;
-  GraphDev dev{};
-};
-
-struct ae_ctx {
-  int device = -1;
-  ae_opts opts;
-  std::string err;
-  std::vector<LoadedGraph> graphs;
-  int loops = 0;
-  void *arena = nullptr;
-  size_t arena_bytes = 0;
-  int sm_count = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = true;
-  // scratch
-  Partial *d_part = nullptr; size_t part_cap = 0;
-  unsigned long long *d_queue = nullptr; size_t queue_cap = 0;
-  unsigned long long *d_qcount = nullptr;
-  double *d_yq = nullptr;
-  int *d_qstat = nullptr;
-};
-
-static int fail(ae_ctx *c, int code, const std::string &msg) {
+int ae_fail(ae_ctx *c, int code, const std::string &msg) {
   if (c) c->err = msg;
   return code;
 }
+static int fail(ae_ctx *c, int code, const std::string &msg) { return ae_fail(c, code, msg); }
 #define CUDA_TRY(c, x)                                                        \
   do {                                                                        \
     cudaError_t e_ = (x);                                                     \
@@ -89,212 +42,6 @@ static int fail(ae_ctx *c, int code, const std::string &msg) {
       return fail(c, e_ == cudaErrorMemoryAllocation ? AE_ERR_OOM : AE_ERR_CUDA, \
                   std::string(#x) + ": " + cudaGetErrorString(e_));            \
   } while (0)
-
-// ============================================================ kernels ====
-using namespace aedev;
-
-// Draw one sample: z (M), log2 z (M) and log2 g.  Same steps, same order of
-// IEEE operations as the host-side definition of the sampler.
-__device__ void draw_sample(const GraphDev &G, uint64_t idx, uint64_t seed, double *z, double *lz,
-                            double &log2g) {
-  const int M = G.M;
-  double u[2 * 14 + 2];
-  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  int nb = M;
-  for (int b = 0; b < nb; ++b) {
-    uint32_t c[4] = {(uint32_t)idx, (uint32_t)(idx >> 32), (uint32_t)G.graph_id, (uint32_t)b};
-    philox4x32_10(c, k0, k1);
-    u[2 * b] = u01(c[0], c[1]);
-    u[2 * b + 1] = u01(c[2], c[3]);
-  }
-  double pick = u[0];
-  int comp;
-  if (pick < G.C1) comp = 0;
-  else if (pick < __dadd_rn(G.C1, G.C2)) comp = 1;
-  else if (pick < __dadd_rn(__dadd_rn(G.C1, G.C2), G.C3)) comp = 2;
-  else comp = 3;
-  const uint32_t full = (1u << M) - 1;
-  if (comp != 1) {
-    int k = comp == 0 ? 0 : comp - 1;
-    const double *deg = G.deg + ((size_t)k << M);
-    const double *phi = G.phi + ((size_t)k << M);
-    const double *wt = G.wt + ((size_t)k << M);
-    uint32_t T = full;
-    double cur = 0.0;
-    for (int l = 0; l < M - 1; ++l) {
-      double uc = u[1 + 2 * l], ut = u[2 + 2 * l];
-      double target = __dmul_rn(uc, __ldg(phi + T));
-      double acc = 0.0;
-      int chosen = -1, last = 0;
-      for (int j = 0; j < M; ++j) {
-        if (!(T >> j & 1)) continue;
-        uint32_t R = T ^ (1u << j);
-        acc = __dadd_rn(acc, __ldg(wt + R));
-        if (chosen < 0 && target < acc) chosen = j;
-        last = j;
-      }
-      if (chosen < 0) chosen = last;
-      lz[chosen] = cur;
-      T ^= 1u << chosen;
-      cur = __dadd_rn(cur, __ddiv_rn(dlog2(ut), __ldg(deg + T)));
-    }
-    int lastj = __ffs(T) - 1;
-    lz[lastj] = cur;
-    double ssum = 0.0;
-    for (int i = 0; i < M; ++i) { z[i] = dexp2(lz[i]); ssum = __dadd_rn(ssum, z[i]); }
-    double ls = dlog2(ssum);
-    for (int i = 0; i < M; ++i) { z[i] = __ddiv_rn(z[i], ssum); lz[i] = __dadd_rn(lz[i], -ls); }
-  } else {
-    double ssum = 0.0;
-    for (int i = 0; i < M; ++i) { z[i] = -dlog2(u[1 + i]); ssum = __dadd_rn(ssum, z[i]); }
-    double ls = dlog2(ssum);
-    for (int i = 0; i < M; ++i) {
-      lz[i] = __dadd_rn(dlog2(z[i]), -ls);
-      z[i] = __ddiv_rn(z[i], ssum);
-    }
-  }
-  // density: sector order = descending log2 z, ties by lower index
-  int ord[14];
-  for (int i = 0; i < M; ++i) {
-    int p = i;
-    while (p > 0 && lz[ord[p - 1]] < lz[i]) { ord[p] = ord[p - 1]; --p; }
-    ord[p] = i;
-  }
-  double sumlz = 0.0;
-  for (int i = 0; i < M; ++i) sumlz = __dadd_rn(sumlz, lz[i]);
-  double t[4];
-  for (int k = 0; k < 3; ++k) {
-    const double *deg = G.deg + ((size_t)k << M);
-    double acc = 0.0;
-    uint32_t T = full ^ (1u << ord[0]);
-    double prev = lz[ord[0]];
-    for (int l = 1; l < M; ++l) {
-      double cv = lz[ord[l]];
-      acc = __dadd_rn(acc, __dmul_rn(__ldg(deg + T), __dadd_rn(cv, -prev)));
-      prev = cv;
-      T ^= 1u << ord[l];
-    }
-    int slot = k == 0 ? 0 : k + 1;
-    t[slot] = __dadd_rn(__dadd_rn(__dadd_rn(G.log2C[slot], -G.log2phi_full[k]), acc), -sumlz);
-  }
-  t[1] = __dadd_rn(G.log2C[1], G.log2_fact);
-  double m = t[0];
-  for (int k = 1; k < 4; ++k) m = fmax(m, t[k]);
-  double rel = 0.0;
-  for (int k = 0; k < 4; ++k) rel = __dadd_rn(rel, dexp2(__dadd_rn(t[k], -m)));
-  log2g = __dadd_rn(m, dlog2(rel));
-}
-
-// y = I / g with g = 2^log2g, range-safe: I * 2^(kf - lg) * 2^-kf
-__device__ __forceinline__ double weight(double I, double lg) {
-  double kf = floor(lg);
-  double s = dexp2(__dadd_rn(kf, -lg));
-  double kc = fmin(fmax(kf, -100000.0), 100000.0);
-  return ldexp(__dmul_rn(I, s), -(int)kc);
-}
-
-// FP64 tape interpreter.  S points at this thread's column of the slot file
-// (stride = blockDim.x).
-__device__ __forceinline__ void run_tape(const GraphDev &G, double *S, int stride) {
-  const uint2 *code = G.code;
-  const double *K = G.khi;
-  for (int pc = 0; pc < G.ntape; ++pc) {
-    uint2 w = __ldg(code + pc);
-    int op = w.x & 0xff;
-    int d = w.x >> 16;
-    int a = w.y & 0xffff;
-    int b = w.y >> 16;
-    double *D = S + d * stride;
-    switch (op) {
-      case T_ADD: *D = __dadd_rn(S[a * stride], S[b * stride]); break;
-      case T_SUB: *D = __dadd_rn(S[a * stride], -S[b * stride]); break;
-      case T_MUL: *D = __dmul_rn(S[a * stride], S[b * stride]); break;
-      case T_DIV: *D = __ddiv_rn(S[a * stride], S[b * stride]); break;
-      case T_FMA: *D = __fma_rn(S[a * stride], S[b * stride], *D); break;
-      case T_FMAC: *D = __fma_rn(__ldg(K + b), S[a * stride], *D); break;
-      case T_MULC: *D = __dmul_rn(__ldg(K + b), S[a * stride]); break;
-      case T_CONST: *D = __ldg(K + b); break;
-      case T_ABS: *D = fabs(S[a * stride]); break;
-      case T_NEG: *D = -S[a * stride]; break;
-      case T_ZERO: *D = 0.0; break;
-      case T_ADDABS: *D = __dadd_rn(*D, fabs(S[a * stride])); break;
-      default: break;
-    }
-  }
-}
-
-// Double-double twin of run_tape (slot file holds hi/lo pairs).
-__device__ void run_tape_dd(const GraphDev &G, dd *S, int stride) {
-  for (int pc = 0; pc < G.ntape; ++pc) {
-    uint2 w = __ldg(G.code + pc);
-    int op = w.x & 0xff, d = w.x >> 16, a = w.y & 0xffff, b = w.y >> 16;
-    dd *D = S + d * stride;
-    dd kb = {0, 0};
-    if (op == T_FMAC || op == T_MULC || op == T_CONST) kb = {__ldg(G.khi + b), __ldg(G.klo + b)};
-    switch (op) {
-      case T_ADD: *D = dd_add(S[a * stride], S[b * stride]); break;
-      case T_SUB: { dd t = S[b * stride]; *D = dd_add(S[a * stride], {-t.hi, -t.lo}); } break;
-      case T_MUL: *D = dd_mul(S[a * stride], S[b * stride]); break;
-      case T_DIV: *D = dd_div(S[a * stride], S[b * stride]); break;
-      case T_FMA: *D = dd_add(*D, dd_mul(S[a * stride], S[b * stride])); break;
-      case T_FMAC: *D = dd_add(*D, dd_mul(kb, S[a * stride])); break;
-      case T_MULC: *D = dd_mul(kb, S[a * stride]); break;
-      case T_CONST: *D = kb; break;
-      case T_ABS: *D = dd_abs(S[a * stride]); break;
-      case T_NEG: { dd t = S[a * stride]; *D = {-t.hi, -t.lo}; } break;
-      case T_ZERO: *D = {0.0, 0.0}; break;
-      case T_ADDABS: *D = dd_add(*D, dd_abs(S[a * stride])); break;
-      default: break;
-    }
-  }
-}
-
-__device__ __forceinline__ void dd_acc(double &hi, double &lo, double x) {
-  dd s = two_sum(hi, x);
-  lo = __dadd_rn(lo, s.lo);
-  dd r = quick_two_sum(s.hi, lo);
-  hi = r.hi; lo = r.lo;
-}
-
-__device__ __forceinline__ void dd_merge(double &hi, double &lo, double h2, double l2) {
-  dd r = dd_add({hi, lo}, {h2, l2});
-  hi = r.hi; lo = r.lo;
-}
-
-// Block reduction of the per-thread accumulators into one Partial.
-__device__ void block_reduce(Partial p, Partial *out) {
-  __shared__ Partial red[32];
-  const unsigned full = 0xffffffffu;
-  for (int off = 16; off > 0; off >>= 1) {
-    Partial q;
-    q.sy_hi = __shfl_down_sync(full, p.sy_hi, off); q.sy_lo = __shfl_down_sync(full, p.sy_lo, off);
-    q.sy2_hi = __shfl_down_sync(full, p.sy2_hi, off); q.sy2_lo = __shfl_down_sync(full, p.sy2_lo, off);
-    q.sa_hi = __shfl_down_sync(full, p.sa_hi, off); q.sa_lo = __shfl_down_sync(full, p.sa_lo, off);
-    q.max_y2 = __shfl_down_sync(full, p.max_y2, off);
-    q.n = __shfl_down_sync(full, p.n, off); q.n_flag = __shfl_down_sync(full, p.n_flag, off);
-    q.n_overflow = __shfl_down_sync(full, p.n_overflow, off);
-    dd_merge(p.sy_hi, p.sy_lo, q.sy_hi, q.sy_lo);
-    dd_merge(p.sy2_hi, p.sy2_lo, q.sy2_hi, q.sy2_lo);
-    dd_merge(p.sa_hi, p.sa_lo, q.sa_hi, q.sa_lo);
-    p.max_y2 = fmax(p.max_y2, q.max_y2);
-    p.n += q.n; p.n_flag += q.n_flag; p.n_overflow += q.n_overflow;
-  }
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = p;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    Partial r = red[0];
-    int nw = (blockDim.x + 31) >> 5;
-    for (int w = 1; w < nw; ++w) {
-      dd_merge(r.sy_hi, r.sy_lo, red[w].sy_hi, red[w].sy_lo);
-      dd_merge(r.sy2_hi, r.sy2_lo, red[w].sy2_hi, red[w].sy2_lo);
-      dd_merge(r.sa_hi, r.sa_lo, red[w].sa_hi, red[w].sa_lo);
-      r.max_y2 = fmax(r.max_y2, red[w].max_y2);
-      r.n += red[w].n; r.n_flag += red[w].n_flag; r.n_overflow += red[w].n_overflow;
-    }
-    *out = r;
-  }
-}
 
 // Process samples [first, first + count) of one graph; CTA b takes a
 // contiguous chunk, thread t its strided share.
@@ -494,6 +241,7 @@ extern "C" void ae_default_opts(ae_opts *o) {
   o->C2 = 0.03; o->C3 = 0.01; o->C4 = 0.06; o->D = 0.75;
   o->C_subI = 0.2; o->C_subSE = 0.0; o->C_subO = 0.2;
   o->C_bigZ = 0.256; o->C_bigF = 0.839; o->C_add = 0.786;
+  o->deg_max = 1.0;
   o->dd_ratio = 1e8;
   o->block_size = 0;
   o->ctas_per_sm = 0;
@@ -553,6 +301,7 @@ extern "C" int ae_load_graphs(ae_ctx *c, int loops, int *n_out) {
     DensityConsts dc;
     dc.C2 = c->opts.C2; dc.C3 = c->opts.C3; dc.C4 = c->opts.C4; dc.D = c->opts.D;
     dc.CsubI = c->opts.C_subI; dc.CsubSE = c->opts.C_subSE; dc.CsubO = c->opts.C_subO;
+    dc.deg_max = c->opts.deg_max;
     std::vector<LoadedGraph> L(gs.size());
     // graphs compile independently: spread them over the host's cores
     std::atomic<size_t> next(0);
