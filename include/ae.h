@@ -136,6 +136,41 @@ int ae_integrate_batched(ae_ctx *ctx, const int *graph_ids, int n_ids,
 int ae_integrate_noalloc(ae_ctx *ctx, int graph_id, uint64_t n_samples, uint64_t seed,
                          ae_graph_result *out);
 
+/* Learned proposal (an extension the paper does not have; unbiased by
+ * construction).  A three-hidden-layer MLP (width 64, BF16 weights, FP32
+ * accumulation) maps the sampler state (the set of lines not yet ordered) to
+ * corrections of the walk's choice logits and of the exponent of the next
+ * ratio t; it is tabulated over all 2^M states.  Training: n_train plain
+ * samples (indices from 2^40 on, disjoint from integration samples),
+ * w = |I|/g, loss -sum w ln q_theta / sum w, `steps` full-batch Adam steps with
+ * learning rate lr, all on the device.  Afterwards the graph integrates with
+ * the defensive mixture (1-beta) q_theta + beta g (beta in (0,1]).
+ * Reallocates the graph's proposal buffers (not for the no-allocation path). */
+typedef struct ae_train_report {
+  double loss_initial, loss_final;   /* -sum w ln q_theta / sum w (nats), first/last step */
+  int steps;
+  uint64_t n_train;
+  double seconds;                    /* wall time of data generation and training */
+} ae_train_report;
+int ae_train_proposal(ae_ctx *ctx, int graph_id, uint64_t n_train, uint64_t seed, int steps,
+                      double lr, double beta, ae_train_report *report);
+
+/* Select a graph's density: mode 0 = plain g, 1 = learned mixture with weight
+ * beta on g (needs a trained proposal). */
+int ae_set_proposal(ae_ctx *ctx, int graph_id, int mode, double beta);
+
+/* Test entry: loss and gradient of the proposal for given parameters
+ * (ae_proposal_nparams() floats: W1[64][32], b1, W2[64][64], b2, W3[64][64],
+ * b3, W4[16][64], b4) and given samples (order: n*16 bytes, descending lines;
+ * lt: n*16 floats, ln t at levels 1..M-1; w: n weights), with the plain
+ * tables deg and wplain = Phi/Deg (2^M each).  Outputs: loss, grad
+ * (nparams), optionally log2 P(j|T) (2^M*16) and Deg_theta (2^M). */
+int ae_proposal_eval(ae_ctx *ctx, int M, const float *params, const double *deg,
+                     const double *wplain, const uint8_t *order, const float *lt,
+                     const double *w, uint64_t n, double *loss, float *grad,
+                     double *log2p_out, double *degt_out);
+int ae_proposal_nparams(void);
+
 /* Per-sample dump for parity tests: samples first .. first+count-1 of
  * graph_id under `seed`.  z: count*M, log2g, I, K, y: count each (any may be
  * NULL).  Host buffers. */

@@ -35,6 +35,11 @@ class AeGraphMeta(ctypes.Structure):
                 ("n_monomials", ctypes.c_int), ("flops", ctypes.c_double)]
 
 
+class AeTrainReport(ctypes.Structure):
+    _fields_ = [("loss_initial", ctypes.c_double), ("loss_final", ctypes.c_double), ("steps", ctypes.c_int),
+                ("n_train", ctypes.c_uint64), ("seconds", ctypes.c_double)]
+
+
 class AeGraphResult(ctypes.Structure):
     _fields_ = [("value", ctypes.c_double), ("sigma", ctypes.c_double), ("mean", ctypes.c_double),
                 ("sigma1", ctypes.c_double), ("mean_abs", ctypes.c_double),
@@ -70,6 +75,12 @@ def lib():
                                    dp, dp, P(AeGraphResult)]
         L.ae_integrate_batched.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_uint64),
                                            ctypes.c_uint64, dp, dp, P(AeGraphResult)]
+        L.ae_train_proposal.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_double, P(AeTrainReport)]
+        L.ae_set_proposal.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        L.ae_proposal_eval.argtypes = [vp, ctypes.c_int, P(ctypes.c_float), dp, dp, P(ctypes.c_uint8),
+                                       P(ctypes.c_float), dp, ctypes.c_uint64, dp, P(ctypes.c_float), dp, dp]
+        L.ae_proposal_nparams.restype = ctypes.c_int
         L.ae_integrate_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, P(AeGraphResult)]
         L.ae_eval_samples.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                       dp, dp, dp, dp, dp]
@@ -158,6 +169,32 @@ class Context:
                                                _ptr(ns, ctypes.c_uint64), int(seed),
                                                ctypes.byref(v), ctypes.byref(s), res))
         return v.value, s.value, [r.as_dict() for r in res]
+
+    def train_proposal(self, gid, n_train, seed=0, steps=200, lr=3e-3, beta=0.1):
+        r = AeTrainReport()
+        self._check(lib().ae_train_proposal(self._h, gid, int(n_train), int(seed), int(steps), float(lr),
+                                            float(beta), ctypes.byref(r)))
+        return {k: getattr(r, k) for k, _ in r._fields_}
+
+    def set_proposal(self, gid, mode, beta=0.1):
+        self._check(lib().ae_set_proposal(self._h, gid, int(mode), float(beta)))
+
+    def proposal_eval(self, M, params, deg, wplain, order, lt, w):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        deg = np.ascontiguousarray(deg, dtype=np.float64)
+        wplain = np.ascontiguousarray(wplain, dtype=np.float64)
+        order = np.ascontiguousarray(order, dtype=np.uint8)
+        lt = np.ascontiguousarray(lt, dtype=np.float32)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        n = w.shape[0]
+        loss = ctypes.c_double()
+        grad = np.empty(lib().ae_proposal_nparams(), dtype=np.float32)
+        lp2 = np.empty((1 << M) * 16)
+        dt = np.empty(1 << M)
+        self._check(lib().ae_proposal_eval(self._h, M, _ptr(params, ctypes.c_float), _ptr(deg), _ptr(wplain),
+                                           _ptr(order, ctypes.c_uint8), _ptr(lt, ctypes.c_float), _ptr(w), n,
+                                           ctypes.byref(loss), _ptr(grad, ctypes.c_float), _ptr(lp2), _ptr(dt)))
+        return loss.value, grad, lp2.reshape(1 << M, 16), dt
 
     def integrate_noalloc(self, gid, n_samples, seed=0):
         """One graph through the entry point that allocates no device memory

@@ -23,6 +23,12 @@ struct GraphDev {
   double C1, C2, C3, C4, log2_fact;
   double log2C[4];        // log2 of C1..C4 (g1, g2, g3, g4 order)
   double log2phi_full[3];
+  // learned proposal (null lP: plain density only)
+  const double *lP = nullptr;    // 2^M x 16: P(j | T)
+  const double *lP2 = nullptr;   // log2 P(j | T)
+  const double *lD = nullptr;    // Deg_theta(T)
+  const double *lD2 = nullptr;   // log2 Deg_theta(T)
+  double beta = 0.1;             // weight of the plain density in the mixture
 };
 
 struct Partial {
@@ -33,7 +39,7 @@ struct Partial {
 
 // Draw one sample: z (M), log2 z (M) and log2 g.  Same steps, same order of
 // IEEE operations as the host-side definition of the sampler.
-__device__ void draw_sample(const GraphDev &G, uint64_t idx, uint64_t seed, double *z, double *lz,
+static __device__ void draw_sample(const GraphDev &G, uint64_t idx, uint64_t seed, double *z, double *lz,
                             double &log2g) {
   const int M = G.M;
   double u[2 * 14 + 2];
@@ -131,6 +137,135 @@ __device__ __forceinline__ double weight(double I, double lg) {
   return ldexp(__dmul_rn(I, s), -(int)kc);
 }
 
+// Defensive mixture q = (1-beta) q_theta + beta g.  u[0] < beta selects the
+// plain density (its component pick rescaled to u[0]/beta), otherwise the
+// learned walk; the returned log2 density is that of the mixture.
+static __device__ void draw_mix(const GraphDev &G, uint64_t idx, uint64_t seed, double *z, double *lz, double &log2q) {
+  const int M = G.M;
+  double u[2 * 14 + 2];
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int b = 0; b < M; ++b) {
+    uint32_t c[4] = {(uint32_t)idx, (uint32_t)(idx >> 32), (uint32_t)G.graph_id, (uint32_t)b};
+    philox4x32_10(c, k0, k1);
+    u[2 * b] = u01(c[0], c[1]);
+    u[2 * b + 1] = u01(c[2], c[3]);
+  }
+  const uint32_t full = (1u << M) - 1;
+  bool plain = u[0] < G.beta;
+  if (plain) {
+    double pick = u[0] / G.beta;
+    int comp;
+    if (pick < G.C1) comp = 0;
+    else if (pick < G.C1 + G.C2) comp = 1;
+    else if (pick < G.C1 + G.C2 + G.C3) comp = 2;
+    else comp = 3;
+    if (comp != 1) {
+      int k = comp == 0 ? 0 : comp - 1;
+      const double *deg = G.deg + ((size_t)k << M);
+      const double *wt = G.wt + ((size_t)k << M);
+      const double *phi = G.phi + ((size_t)k << M);
+      uint32_t T = full;
+      double cur = 0.0;
+      for (int l = 0; l < M - 1; ++l) {
+        double target = u[1 + 2 * l] * __ldg(phi + T);
+        double acc = 0.0;
+        int chosen = -1, last = 0;
+        for (int j = 0; j < M; ++j) {
+          if (!(T >> j & 1)) continue;
+          acc += __ldg(wt + (T ^ (1u << j)));
+          if (chosen < 0 && target < acc) chosen = j;
+          last = j;
+        }
+        if (chosen < 0) chosen = last;
+        lz[chosen] = cur;
+        T ^= 1u << chosen;
+        cur += dlog2(u[2 + 2 * l]) / __ldg(deg + T);
+      }
+      lz[__ffs(T) - 1] = cur;
+    } else {
+      for (int i = 0; i < M; ++i) lz[i] = dlog2(-dlog2(u[1 + i]));
+    }
+  } else {
+    uint32_t T = full;
+    double cur = 0.0;
+    for (int l = 0; l < M - 1; ++l) {
+      double uc = u[1 + 2 * l];
+      double acc = 0.0;
+      int chosen = -1, last = 0;
+      for (int j = 0; j < M; ++j) {
+        if (!(T >> j & 1)) continue;
+        acc += __ldg(G.lP + (size_t)T * 16 + j);
+        if (chosen < 0 && uc < acc) chosen = j;
+        last = j;
+      }
+      if (chosen < 0) chosen = last;
+      lz[chosen] = cur;
+      T ^= 1u << chosen;
+      cur += dlog2(u[2 + 2 * l]) / __ldg(G.lD + T);
+    }
+    lz[__ffs(T) - 1] = cur;
+  }
+  // normalise: z = 2^lz / sum, log2 z = lz - log2 sum
+  double ssum = 0.0;
+  for (int i = 0; i < M; ++i) { z[i] = dexp2(lz[i]); ssum += z[i]; }
+  double ls = dlog2(ssum);
+  for (int i = 0; i < M; ++i) { z[i] = z[i] / ssum; lz[i] = lz[i] - ls; }
+  // densities at z
+  int ord[14];
+  for (int i = 0; i < M; ++i) {
+    int p = i;
+    while (p > 0 && lz[ord[p - 1]] < lz[i]) { ord[p] = ord[p - 1]; --p; }
+    ord[p] = i;
+  }
+  double sumlz = 0.0;
+  for (int i = 0; i < M; ++i) sumlz += lz[i];
+  double t[4];
+  for (int k = 0; k < 3; ++k) {
+    const double *deg = G.deg + ((size_t)k << M);
+    double acc = 0.0;
+    uint32_t T = full ^ (1u << ord[0]);
+    double prev = lz[ord[0]];
+    for (int l = 1; l < M; ++l) {
+      double cv = lz[ord[l]];
+      acc += __ldg(deg + T) * (cv - prev);
+      prev = cv;
+      T ^= 1u << ord[l];
+    }
+    int slot = k == 0 ? 0 : k + 1;
+    t[slot] = G.log2C[slot] - G.log2phi_full[k] + acc - sumlz;
+  }
+  t[1] = G.log2C[1] + G.log2_fact;
+  double m = fmax(fmax(t[0], t[1]), fmax(t[2], t[3]));
+  double rel = 0.0;
+  for (int k = 0; k < 4; ++k) rel += dexp2(t[k] - m);
+  double lg = m + dlog2(rel);
+  // learned density along the same order
+  double lq = 0.0;
+  {
+    uint32_t T = full;
+    double prev = 0.0;
+    for (int l = 0; l < M - 1; ++l) {
+      int j = ord[l];
+      lq += __ldg(G.lP2 + (size_t)T * 16 + j);
+      T ^= 1u << j;
+      double cv = lz[ord[l + 1]];
+      double pv = l == 0 ? lz[ord[0]] : prev;
+      lq += __ldg(G.lD2 + T) + __ldg(G.lD + T) * (cv - pv);
+      prev = cv;
+    }
+    lq -= sumlz;
+  }
+  double a = dlog2(1.0 - G.beta) + lq, b = dlog2(G.beta) + lg;
+  double mm = fmax(a, b);
+  log2q = mm + dlog2(dexp2(a - mm) + dexp2(b - mm));
+}
+
+__device__ __forceinline__ void draw_any(const GraphDev &G, uint64_t idx, uint64_t seed, double *z, double *lz,
+                                         double &lg) {
+  if (G.lP) draw_mix(G, idx, seed, z, lz, lg);
+  else draw_sample(G, idx, seed, z, lz, lg);
+}
+
 // FP64 tape interpreter.  S points at this thread's column of the slot file
 // (stride = blockDim.x).
 __device__ __forceinline__ void run_tape(const GraphDev &G, double *S, int stride) {
@@ -162,7 +297,7 @@ __device__ __forceinline__ void run_tape(const GraphDev &G, double *S, int strid
 }
 
 // Double-double twin of run_tape (slot file holds hi/lo pairs).
-__device__ void run_tape_dd(const GraphDev &G, dd *S, int stride) {
+static __device__ void run_tape_dd(const GraphDev &G, dd *S, int stride) {
   for (int pc = 0; pc < G.ntape; ++pc) {
     uint2 w = __ldg(G.code + pc);
     int op = w.x & 0xff, d = w.x >> 16, a = w.y & 0xffff, b = w.y >> 16;
@@ -200,7 +335,7 @@ __device__ __forceinline__ void dd_merge(double &hi, double &lo, double h2, doub
 }
 
 // Block reduction of the per-thread accumulators into one Partial.
-__device__ void block_reduce(Partial p, Partial *out) {
+static __device__ void block_reduce(Partial p, Partial *out) {
   __shared__ Partial red[32];
   const unsigned full = 0xffffffffu;
   for (int off = 16; off > 0; off >>= 1) {

@@ -59,7 +59,7 @@ __global__ void integrate_kernel(GraphDev G, uint64_t first, uint64_t count, uin
   for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     uint64_t idx = first + i;
     double lg;
-    draw_sample(G, idx, seed, z, lz, lg);
+    draw_any(G, idx, seed, z, lz, lg);
     for (int k = 0; k < G.M; ++k) S[k * stride] = z[k];
     run_tape(G, S, stride);
     double I = S[G.outI * stride], Kv = S[G.outK * stride];
@@ -92,7 +92,7 @@ __global__ void dd_kernel(GraphDev G, uint64_t seed, const unsigned long long *q
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
        i += (uint64_t)gridDim.x * blockDim.x) {
     double z[14], lz[14], lg;
-    draw_sample(G, queue[i], seed, z, lz, lg);
+    draw_any(G, queue[i], seed, z, lz, lg);
     for (int k = 0; k < G.M; ++k) S[k * stride] = {z[k], 0.0};
     run_tape_dd(G, S, stride);
     dd I = S[G.outI * stride], K = S[G.outK * stride];
@@ -117,7 +117,7 @@ __global__ void eval_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t
     uint64_t i = base + threadIdx.x;
     if (i >= count) continue;
     double z[14], lz[14], lg;
-    draw_sample(G, first + i, seed, z, lz, lg);
+    draw_any(G, first + i, seed, z, lz, lg);
     for (int k = 0; k < G.M; ++k) { S[k * stride] = z[k]; z_out[i * G.M + k] = z[k]; }
     run_tape(G, S, stride);
     double I = S[G.outI * stride], Kv = S[G.outK * stride];
@@ -136,7 +136,7 @@ __global__ void eval_dd_kernel(GraphDev G, uint64_t first, uint64_t count, uint6
     uint64_t i = base + threadIdx.x;
     if (i >= count) continue;
     double z[14], lz[14], lg;
-    draw_sample(G, first + i, seed, z, lz, lg);
+    draw_any(G, first + i, seed, z, lz, lg);
     for (int k = 0; k < G.M; ++k) S[k * stride] = {z[k], 0.0};
     run_tape_dd(G, S, stride);
     dd I = S[G.outI * stride], K = S[G.outK * stride];
@@ -197,7 +197,7 @@ __global__ void dd_dense_kernel(GraphDev G, uint64_t first, uint64_t seed, const
        i += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t idx = queue[i];
     double z[14], lz[14], lg;
-    draw_sample(G, idx, seed, z, lz, lg);
+    draw_any(G, idx, seed, z, lz, lg);
     for (int k = 0; k < G.M; ++k) S[k * stride] = {z[k], 0.0};
     run_tape_dd(G, S, stride);
     dd I = S[G.outI * stride], K = S[G.outK * stride];

@@ -269,3 +269,51 @@ def test_weight_range_safe():
     assert weight(3.0, 1.0) == 1.5
     assert weight(1.0, 2000.0) == 2.0 ** -2000 or weight(1.0, 2000.0) == 0.0
     assert weight(2.0 ** -1000, -1500.0) == 2.0 ** 500
+
+
+# ------------------------------------------------------ learned proposal ---
+def test_proposal_gradient_finite_differences():
+    """The oracle's backpropagation against central differences of its own
+    loss (float64, unrounded weights)."""
+    from oracle import proposal as pr
+    from tests import proposal_inputs as pin
+    g = enumerate_graphs(2)[1]
+    d = Density(g)
+    M = d.M
+    p = pin.params(3).astype(np.float64)
+    order, lt, w = pin.records(3, 40, M)
+    wplain = np.ones(1 << M)
+    wplain[1:-1] = d.phi[0][1:-1] / d.deg[0][1:-1]
+    deg = d.deg[0].copy()
+    grad = pr.grad_unrounded(p, deg, wplain, order, lt, w, M)
+    rng = np.random.default_rng(0)
+    idx = list(rng.choice(pr.NPARAM, 12, replace=False)) + [pr.NPARAM - 1, pr.NPARAM - 16 - 5]
+    for k in idx:
+        h = 1e-5
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd = (pr.loss_only(pp, deg, wplain, order, lt, w, M) - pr.loss_only(pm, deg, wplain, order, lt, w, M)) / (2 * h)
+        assert abs(fd - grad[k]) <= 1e-5 * max(1.0, abs(fd)), (k, fd, grad[k])
+
+
+def test_proposal_zero_output_is_plain_walk():
+    """With a zero output layer the learned walk is exactly the plain walk:
+    P(j|T) = Phi(T\\j)/Deg(T\\j)/Phi(T) and Deg_theta = Deg."""
+    from oracle import proposal as pr
+    g = enumerate_graphs(2)[0]
+    d = Density(g)
+    M = d.M
+    p = np.zeros(pr.NPARAM)
+    f = pr.forward(p, M)
+    wplain = np.ones(1 << M)
+    wplain[1:-1] = d.phi[0][1:-1] / d.deg[0][1:-1]
+    logp, degt = pr.tables(f["o"], d.deg[0], wplain, M)
+    for T in range(1, 1 << M):
+        js = [j for j in range(M) if T >> j & 1]
+        if len(js) < 2:
+            continue
+        for j in js:
+            want = d.phi[0][T ^ (1 << j)] / d.deg[0][T ^ (1 << j)] / d.phi[0][T]
+            assert abs(np.exp(logp[T, j]) - want) < 1e-12
+    assert np.allclose(degt[1:-1], d.deg[0][1:-1])
