@@ -1,11 +1,15 @@
-"""Benchmark: Monte Carlo samples/s and 1/(sigma^2 s) on a generated graph set.
+"""Benchmark: Monte Carlo samples/s and 1/(sigma^2 s) on a generated graph set,
+learned+batched against the plain density.
 
-Workload (default): all 28 three-loop vertex graphs without lepton loops,
-plain graph-specific density, one launch per graph; one step = every graph
-integrated over 2^24 fresh Philox samples (seed = step number; under torchrun
-each rank adds rank * 1000003 to the seed, so ranks draw disjoint streams:
-weak scaling, no data-path collective; the per-graph sums are merged once at
-the end).
+Workload (default): all 28 three-loop vertex graphs without lepton loops.
+Set-up (untimed, reported): compile the graphs; train one learned proposal
+per graph on 2^20 plain samples (the network's own GPU kernels).
+Timed step: every graph integrated over 2^24 fresh Philox samples in ONE
+persistent batched launch with the learned mixture density (seed = step
+number; under torchrun each rank adds rank * 1000003, so ranks draw disjoint
+streams: weak scaling, no data-path collective; per-graph sums are merged
+once at the end).  The plain density (one launch per graph, the same sample
+budget) is timed after the timed region for the comparison.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -130,6 +134,26 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+def merge(per_steps, ids, info):
+    """Per-graph (sum y, sum y^2, N) over steps -> (value, sigma_down)."""
+    import numpy as np
+    sums = np.zeros((len(ids), 3))
+    for per in per_steps:
+        for i, p in enumerate(per):
+            sums[i] += (p["sum_y"], p["sum_y2"], p["n"])
+    return sums
+
+
+def estimate(sums, info):
+    val = var = 0.0
+    for i in range(len(sums)):
+        sy, sy2, N = sums[i]
+        v1 = sy2 / N ** 2 - sy ** 2 / N ** 3
+        val += info[i]["mult"] * sy / N
+        var += info[i]["mult"] ** 2 * max(v1, 0.0)
+    return val, math.sqrt(var)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -138,6 +162,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--loops", type=int, default=3)
     ap.add_argument("--samples", type=int, default=1 << 24, help="samples per graph per step")
+    ap.add_argument("--train", type=int, default=1 << 20, help="training samples per graph")
+    ap.add_argument("--train-steps", type=int, default=150)
+    ap.add_argument("--plain", action="store_true", help="time the plain density only (no learned proposal)")
     ap.add_argument("--oracle-samples", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -162,13 +189,25 @@ def main():
     opts = ae.default_opts()
     opts.stream = stream.cuda_stream
     ctx = ae.Context(local, opts)
+    t0 = time.perf_counter()
     ngr = ctx.load_graphs(args.loops)
+    compile_s = time.perf_counter() - t0
     ids = list(range(ngr))
     info = [ctx.graph_info(i) for i in ids]
     M = info[0]["M"]
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    learned = not args.plain
+    train_s = 0.0
+    if learned:
+        t0 = time.perf_counter()
+        for i in ids:
+            ctx.train_proposal(i, args.train, seed=7 + rank, steps=args.train_steps, lr=3e-3, beta=0.1)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
 
     def step(seed):
+        if learned:
+            return ctx.integrate_batched(ids, [args.samples] * ngr, seed=seed + rank * 1000003)
         return ctx.integrate(ids, args.samples, seed=seed + rank * 1000003)
 
     for w in range(args.warmup):
@@ -201,37 +240,46 @@ def main():
         tt = torch.tensor([t_dev, e2e_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_dev, e2e_s = tt.tolist()
-    # merge per-graph sums over steps (and ranks): value and sigma_down
-    sums = np.zeros((len(ids), 3))
-    for per in per_all:
-        for i, p in enumerate(per):
-            sums[i] += (p["sum_y"], p["sum_y2"], p["n"])
+    sums = merge(per_all, ids, info)
     if dist:
         ts = torch.tensor(sums, dtype=torch.float64, device="cuda")
         dist.all_reduce(ts)
         sums = ts.cpu().numpy()
-    val = 0.0
-    var = 0.0
-    for i in ids:
-        sy, sy2, N = sums[i]
-        mean = sy / N
-        v1 = sy2 / N ** 2 - sy ** 2 / N ** 3
-        val += info[i]["mult"] * mean
-        var += info[i]["mult"] ** 2 * max(v1, 0.0)
-    sigma = math.sqrt(var)
+    val, sigma = estimate(sums, info)
     total = args.samples * len(ids) * args.steps * world
     rate = total / t_dev
-    # roofline of the FP64 integrand kernel (sampler + tape per sample)
+    # roofline of the dominant kernel: FP64 integrand kernel (sampler + tape)
     kern_s = sum(p["kernel_seconds"] for per in per_all for p in per)
-    kern_launches = sum(1 for per in per_all for p in per)   # one per graph per slice here
     flops_per = [info[i]["flops"] + sampler_flops(M) for i in ids]
     fl_total = sum(flops_per[i] * args.samples for i in ids) * args.steps
     achieved = fl_total / kern_s / 1e12
-    peak = ctx.fp64_peak() if rank == 0 else 0.0
     launches = sum(p["launches"] for per in per_all for p in per)
     d2h = sum(p["d2h_bytes"] for per in per_all for p in per) / args.steps
+    h2d = sum(p["h2d_bytes"] for per in per_all for p in per) / args.steps
     n_dd = sum(p["n_dd"] for per in per_all for p in per)
     zeroed = sum(p["n_nonfinite"] for per in per_all for p in per)
+    # the plain density on the same budget, after the timed region
+    plain = None
+    if learned and rank == 0:
+        for i in ids:
+            ctx.set_proposal(i, 0)
+        pp = []
+        pt = 0.0
+        for k in range(args.steps):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            _, _, per = ctx.integrate(ids, args.samples, seed=k)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            pt += ev0.elapsed_time(ev1) / 1e3
+            pp.append(per)
+        pv, ps = estimate(merge(pp, ids, info), info)
+        ptot = args.samples * len(ids) * args.steps
+        plain = {"samples_per_s": ptot / pt, "inv_sigma2_per_s": 1.0 / (ps * ps * pt),
+                 "value": pv, "sigma_down": ps, "seconds": pt,
+                 "dd_reevaluated": int(sum(p["n_dd"] for per in pp for p in per))}
+    peak = ctx.fp64_peak() if rank == 0 else 0.0
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -240,24 +288,31 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         crate, cores, evals, wall = oracle_rate(args.loops, [0, ngr // 2, ngr - 1], args.oracle_samples)
         cpu = {"value": crate, "unit": "samples/s", "cores": cores, "kind": "oracle",
-               "sample": "graphs 0, %d, %d of the set, %d samples each (evaluation after per-graph "
-                         "setup, %.1f s on %d processes)" % (ngr // 2, ngr - 1, args.oracle_samples, wall, cores)}
+               "sample": "graphs 0, %d, %d of the set, %d samples each, plain density (evaluation after "
+                         "per-graph setup, %.1f s on %d processes)" % (ngr // 2, ngr - 1, args.oracle_samples, wall, cores)}
+    isps = 1.0 / (sigma ** 2 * t_dev) if sigma > 0 else None
     line = {
         "metric": METRIC, "value": rate, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "all %d %d-loop vertex graphs without lepton loops, plain pdf, one launch "
-                               "per graph" % (len(ids), args.loops),
+        "config": {"workload": "all %d %d-loop vertex graphs without lepton loops, %s" % (
+                       len(ids), args.loops,
+                       "learned mixture density, one batched persistent launch per step" if learned
+                       else "plain density, one launch per graph"),
                    "samples_per_graph_per_step": args.samples, "seed": "step index (+ rank offset)",
+                   "train_samples_per_graph": args.train if learned else 0,
                    "l2": "256 MB buffer written between timed steps", "parallelism": "dp%d" % world},
-        "inv_sigma2_per_s": 1.0 / (sigma ** 2 * t_dev) if sigma > 0 else None,
-        "estimate": {"value": val, "sigma_down": sigma, "samples": total, "dd_reevaluated": n_dd,
-                     "zeroed": zeroed},
+        "inv_sigma2_per_s": isps,
+        "inv_sigma2_per_s_incl_training": (1.0 / (sigma ** 2 * (t_dev + train_s)) if sigma > 0 else None),
+        "estimate": {"value": val, "sigma_down": sigma, "samples": total, "dd_reevaluated": int(n_dd),
+                     "zeroed": int(zeroed)},
+        "plain_pdf": plain,
+        "setup_seconds": {"compile": compile_s, "train": train_s},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": None,
-                     "kernel": "integrate_kernel (sampler + FP64 tape)",
+                     "kernel": ("batched_kernel" if learned else "integrate_kernel") + " (sampler + FP64 tape)",
                      "peak_source": "measured: own DFMA probe (ae_fp64_peak)"},
-        "e2e": {"value": total / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 0,
+        "e2e": {"value": total / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": ck,

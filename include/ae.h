@@ -88,6 +88,8 @@ typedef struct ae_graph_result {
   uint64_t launches;     /* kernels launched for this graph                        */
   double kernel_seconds; /* device time of the FP64 integrand kernel alone         */
   uint64_t d2h_bytes;    /* bytes read back to the host for this graph's result     */
+  uint64_t h2d_bytes;    /* bytes copied to the device for this call (batched: on
+                            the first graph's entry)                                */
 } ae_graph_result;
 
 /* Integrate the listed graphs with n_samples samples each, Philox seed
@@ -98,7 +100,14 @@ int ae_integrate(ae_ctx *ctx, const int *graph_ids, int n_ids, uint64_t n_sample
                  uint64_t seed, double *value, double *sigma, ae_graph_result *per_graph);
 
 /* Batched form: all listed graphs with their own sample counts in ONE
- * persistent launch (work queue of (graph, counter range) chunks). */
+ * persistent launch: a work queue of (graph, counter range) chunks, longest
+ * tapes first, taken by CTAs through one atomic counter; the flagged samples
+ * of every graph are re-evaluated by one double-double launch; both launches
+ * are captured in a CUDA graph.  Block and chunk size come from an
+ * autotuner (timed trial runs on sample indices from 2^44 on, cached per
+ * graph set) unless opts.block_size is set.  Per-graph `seconds` are the
+ * launch time apportioned by sample count.  Same samples (indices 0..n-1) and
+ * the same result as ae_integrate up to summation order. */
 int ae_integrate_batched(ae_ctx *ctx, const int *graph_ids, int n_ids,
                          const uint64_t *n_samples, uint64_t seed, double *value,
                          double *sigma, ae_graph_result *per_graph);
@@ -170,6 +179,14 @@ int ae_proposal_eval(ae_ctx *ctx, int M, const float *params, const double *deg,
                      const double *w, uint64_t n, double *loss, float *grad,
                      double *log2p_out, double *degt_out);
 int ae_proposal_nparams(void);
+
+/* Inter-graph allocation (Sec. IV.C).  A pilot of n_pilot samples per graph
+ * (independent stream) estimates sigma_j; n_total samples are split into
+ * n_out[i]: mode 0 proportional to C_j / sqrt(t_j), C_j = sigma_j sqrt(N_pilot)
+ * and t_j the per-sample cost (the paper's optimal probabilities), mode 1
+ * proportional to sigma_j^2.  sigma_out (nullable) receives the pilot sigmas. */
+int ae_allocate(ae_ctx *ctx, const int *graph_ids, int n_ids, uint64_t n_pilot, uint64_t n_total,
+                uint64_t seed, int mode, uint64_t *n_out, double *sigma_out);
 
 /* Per-sample dump for parity tests: samples first .. first+count-1 of
  * graph_id under `seed`.  z: count*M, log2g, I, K, y: count each (any may be

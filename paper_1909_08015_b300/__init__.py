@@ -46,7 +46,8 @@ class AeGraphResult(ctypes.Structure):
                 ("sum_y", ctypes.c_double), ("sum_y2", ctypes.c_double), ("max_y2", ctypes.c_double),
                 ("n", ctypes.c_uint64), ("n_dd", ctypes.c_uint64), ("n_nonfinite", ctypes.c_uint64),
                 ("seconds", ctypes.c_double), ("launches", ctypes.c_uint64),
-                ("kernel_seconds", ctypes.c_double), ("d2h_bytes", ctypes.c_uint64)]
+                ("kernel_seconds", ctypes.c_double), ("d2h_bytes", ctypes.c_uint64),
+                ("h2d_bytes", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -75,6 +76,8 @@ def lib():
                                    dp, dp, P(AeGraphResult)]
         L.ae_integrate_batched.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_uint64),
                                            ctypes.c_uint64, dp, dp, P(AeGraphResult)]
+        L.ae_allocate.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                  ctypes.c_uint64, ctypes.c_int, P(ctypes.c_uint64), dp]
         L.ae_train_proposal.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_double, P(AeTrainReport)]
         L.ae_set_proposal.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
@@ -169,6 +172,14 @@ class Context:
                                                _ptr(ns, ctypes.c_uint64), int(seed),
                                                ctypes.byref(v), ctypes.byref(s), res))
         return v.value, s.value, [r.as_dict() for r in res]
+
+    def allocate(self, ids, n_pilot, n_total, seed=0, mode=0):
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        out = np.empty(len(ids), dtype=np.uint64)
+        sig = np.empty(len(ids))
+        self._check(lib().ae_allocate(self._h, _ptr(ids, ctypes.c_int), len(ids), int(n_pilot), int(n_total),
+                                      int(seed), int(mode), _ptr(out, ctypes.c_uint64), _ptr(sig)))
+        return out, sig
 
     def train_proposal(self, gid, n_train, seed=0, steps=200, lr=3e-3, beta=0.1):
         r = AeTrainReport()

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -50,6 +51,12 @@ struct ae_ctx {
   unsigned long long *d_qcount = nullptr;
   double *d_yq = nullptr;
   int *d_qstat = nullptr;
+  // autotuner cache: graph-set key -> (block size, chunk size)
+  std::map<std::string, std::pair<int, unsigned long long>> tune_cache;
+  void *bbuf = nullptr;         // batched-launch buffers (grow only)
+  size_t bbuf_bytes = 0;
+  int last_tune_block = 0;
+  unsigned long long last_tune_chunk = 0;
 };
 
 

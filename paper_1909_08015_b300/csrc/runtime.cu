@@ -168,6 +168,89 @@ __global__ void philox_kernel(const uint32_t *ctr, const uint32_t *key, uint32_t
   for (int k = 0; k < 4; ++k) out[4 * i + k] = c[k];
 }
 
+// ------------------------------------------------- batched persistent ----
+// One chunk of work: samples [first, first + count) of graph gi.
+struct Chunk {
+  int gi;
+  int pad;
+  unsigned long long first, count;
+};
+
+// Persistent kernel over a queue of chunks from many graphs (tapes of very
+// different lengths).  CTAs take chunks in list order through one atomic
+// counter; each chunk's partial is written to its own slot, so the result does
+// not depend on which CTA ran it.  Flagged samples go to the queue as
+// (graph, sample index).
+__global__ void batched_kernel(const GraphDev *graphs, const Chunk *chunks, int nchunks, uint64_t seed,
+                               double dd_ratio, Partial *part, unsigned long long *queue_idx, int *queue_gi,
+                               unsigned long long qcap, unsigned long long *qcount, int *next) {
+  extern __shared__ double slots[];
+  __shared__ int cur, curg;
+  __shared__ GraphDev G;     // descriptor of the current chunk's graph
+  double *S = slots + threadIdx.x;
+  const int stride = blockDim.x;
+  double z[14], lz[14];
+  if (threadIdx.x == 0) curg = -1;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      cur = atomicAdd(next, 1);
+      if (cur < nchunks && chunks[cur].gi != curg) { curg = chunks[cur].gi; G = graphs[curg]; }
+    }
+    __syncthreads();
+    int c = cur;
+    if (c >= nchunks) break;
+    const Chunk ch = chunks[c];
+    Partial p = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint64_t i = threadIdx.x; i < ch.count; i += blockDim.x) {
+      uint64_t idx = ch.first + i;
+      double lg;
+      draw_any(G, idx, seed, z, lz, lg);
+      for (int k = 0; k < G.M; ++k) S[k * stride] = z[k];
+      run_tape(G, S, stride);
+      double I = S[G.outI * stride], Kv = S[G.outK * stride];
+      double y = weight(I, lg);
+      bool bad = !isfinite(I) || !isfinite(Kv) || !isfinite(y) || (dd_ratio > 0 && Kv > dd_ratio * fabs(I));
+      p.n += 1;
+      if (bad) {
+        p.n_flag += 1;
+        unsigned long long slot = atomicAdd(qcount, 1ull);
+        if (slot < qcap) { queue_idx[slot] = idx; queue_gi[slot] = ch.gi; }
+        else p.n_overflow += 1;
+        continue;
+      }
+      dd_acc(p.sy_hi, p.sy_lo, y);
+      dd_acc(p.sy2_hi, p.sy2_lo, y * y);
+      dd_acc(p.sa_hi, p.sa_lo, fabs(y));
+      p.max_y2 = fmax(p.max_y2, y * y);
+    }
+    block_reduce(p, part + c);
+    __syncthreads();
+  }
+}
+
+// Double-double re-evaluation of the batched queue (count read on the device,
+// so the launch shape is fixed and the pair can be captured in a graph).
+__global__ void batched_dd_kernel(const GraphDev *graphs, uint64_t seed, const unsigned long long *queue_idx,
+                                  const int *queue_gi, const unsigned long long *qcount, unsigned long long qcap,
+                                  double *y_out, int *status) {
+  extern __shared__ dd bdsl[];
+  dd *S = bdsl + threadIdx.x;
+  const int stride = blockDim.x;
+  uint64_t nq = min(*qcount, qcap);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (uint64_t)gridDim.x * blockDim.x) {
+    const GraphDev &G = graphs[queue_gi[i]];
+    double z[14], lz[14], lg;
+    draw_any(G, queue_idx[i], seed, z, lz, lg);
+    for (int k = 0; k < G.M; ++k) S[k * stride] = {z[k], 0.0};
+    run_tape_dd(G, S, stride);
+    dd I = S[G.outI * stride], K = S[G.outK * stride];
+    double y = weight(I.hi + I.lo, lg);
+    bool bad = !isfinite(I.hi) || !isfinite(K.hi) || !isfinite(y) || K.hi > 2.0e23 * fabs(I.hi);
+    y_out[i] = bad ? 0.0 : y;
+    status[i] = bad ? 1 : 0;
+  }
+}
+
 // ------------------------------------------- no-allocation entry point ---
 // Scratch of ae_integrate_noalloc: one file-scope device array, shared by all
 // calls on a device and kept between them.  Layout (bytes from the start):
@@ -280,6 +363,12 @@ static void free_device(ae_ctx *c) {
   if (c->d_qcount) cudaFree(c->d_qcount);
   if (c->d_yq) cudaFree(c->d_yq);
   if (c->d_qstat) cudaFree(c->d_qstat);
+  if (c->bbuf) cudaFree(c->bbuf);
+  c->bbuf = nullptr;
+  c->bbuf_bytes = 0;
+  for (auto &lg : c->graphs)
+    if (lg.learned.mem) { cudaFree(lg.learned.mem); lg.learned.mem = nullptr; lg.dev.lP = nullptr; }
+  c->tune_cache.clear();
   c->arena = nullptr; c->d_part = nullptr; c->d_queue = nullptr; c->d_qcount = nullptr;
   c->d_yq = nullptr; c->d_qstat = nullptr; c->part_cap = c->queue_cap = 0;
 }
@@ -558,9 +647,298 @@ extern "C" int ae_integrate(ae_ctx *c, const int *ids, int n_ids, uint64_t nsamp
   return AE_OK;
 }
 
-extern "C" int ae_integrate_batched(ae_ctx *c, const int *ids, int n_ids, const uint64_t *ns,
-                                    uint64_t seed, double *value, double *sigma, ae_graph_result *per) {
-  return fail(c, AE_ERR_STATE, "batched integration not available in this build");
+// Autotuned launch shape of the batched kernel for one (graph set, budget).
+struct BatchTune {
+  int block = 0;
+  unsigned long long chunk = 0;
+};
+
+static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vector<uint64_t> &ns,
+                         const std::vector<uint64_t> &firsts, uint64_t seed, int bs, uint64_t chunk,
+                         bool use_graph, std::vector<ae_graph_result> &res, double *secs_out, bool full_queue);
+
+static int run_batched(ae_ctx *c, const std::vector<int> &ids, const std::vector<uint64_t> &ns,
+                       const std::vector<uint64_t> &firsts, uint64_t seed, int bs, uint64_t chunk,
+                       bool use_graph, std::vector<ae_graph_result> &res, double *secs_out) {
+  // queue sized for a quarter of the samples; a batch that needs more is
+  // rerun with room for every sample (same samples, same result)
+  int rc = run_batched_q(c, ids, ns, firsts, seed, bs, chunk, use_graph, res, secs_out, false);
+  if (rc == AE_ERR_STATE && c->err == "double-double queue overflow")
+    rc = run_batched_q(c, ids, ns, firsts, seed, bs, chunk, use_graph, res, secs_out, true);
+  return rc;
+}
+
+static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vector<uint64_t> &ns,
+                         const std::vector<uint64_t> &firsts, uint64_t seed, int bs, uint64_t chunk,
+                         bool use_graph, std::vector<ae_graph_result> &res, double *secs_out, bool full_queue) {
+  int maxslots = 0;
+  for (int g : ids) maxslots = std::max(maxslots, c->graphs[g].dev.nslots);
+  size_t smem = (size_t)bs * maxslots * 8;
+  if (smem > 200 * 1024) return fail(c, AE_ERR_STATE, "batched slot file does not fit in shared memory");
+  CUDA_TRY(c, cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, bs, smem));
+  if (per_sm < 1) per_sm = 1;
+  // chunks: graphs by decreasing tape length (longest first balances the tail)
+  std::vector<int> order(ids.size());
+  for (size_t i = 0; i < ids.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return c->graphs[ids[a]].dev.ntape > c->graphs[ids[b]].dev.ntape;
+  });
+  std::vector<Chunk> chunks;
+  for (int oi : order)
+    for (uint64_t s0 = 0; s0 < ns[oi]; s0 += chunk)
+      chunks.push_back(Chunk{oi, 0, firsts[oi] + s0, std::min<uint64_t>(chunk, ns[oi] - s0)});
+  uint64_t total = 0;
+  for (uint64_t x : ns) total += x;
+  size_t nch = chunks.size();
+  size_t qcap = (size_t)std::max<uint64_t>(full_queue ? total : total / 4, 65536);
+  // device buffers (graph descriptors, chunks, partials, queue), kept in the
+  // context and grown when a larger batch arrives
+  size_t need = ids.size() * sizeof(GraphDev) + nch * sizeof(Chunk) + nch * sizeof(Partial) + qcap * (8 + 4 + 8 + 4) +
+                64 + 8 * 256;
+  if (need > c->bbuf_bytes) {
+    if (c->bbuf) cudaFree(c->bbuf);
+    c->bbuf = nullptr;
+    c->bbuf_bytes = 0;
+    CUDA_TRY(c, cudaMalloc(&c->bbuf, need));
+    c->bbuf_bytes = need;
+  }
+  char *buf = (char *)c->bbuf;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  char *p = buf;
+  GraphDev *dG = (GraphDev *)p; p += al(ids.size() * sizeof(GraphDev));
+  Chunk *dC = (Chunk *)p; p += al(nch * sizeof(Chunk));
+  Partial *dP = (Partial *)p; p += al(nch * sizeof(Partial));
+  unsigned long long *qi = (unsigned long long *)p; p += al(qcap * 8);
+  int *qg = (int *)p; p += al(qcap * 4);
+  double *qy = (double *)p; p += al(qcap * 8);
+  int *qs = (int *)p; p += al(qcap * 4);
+  unsigned long long *qcount = (unsigned long long *)p; p += 64;
+  int *next = (int *)(qcount + 1);
+  std::vector<GraphDev> hg;
+  for (int g : ids) hg.push_back(c->graphs[g].dev);
+  cudaError_t e = cudaMemcpyAsync(dG, hg.data(), hg.size() * sizeof(GraphDev), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dC, chunks.data(), nch * sizeof(Chunk), cudaMemcpyHostToDevice, c->stream);
+  int bsd = pick_block(c, maxslots, 16);
+  if (bsd < 0) bsd = 32;
+  size_t sm2 = (size_t)bsd * maxslots * 16;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+  unsigned grid = (unsigned)(c->sm_count * per_sm);
+  unsigned grid2 = (unsigned)(c->sm_count * 4);
+  cudaEvent_t e0 = nullptr, e1 = nullptr, ek = nullptr;
+  auto enqueue = [&]() {
+    cudaEventRecord(e0, c->stream);
+    cudaMemsetAsync(qcount, 0, 16, c->stream);
+    batched_kernel<<<grid, bs, smem, c->stream>>>(dG, dC, (int)nch, seed, c->opts.dd_ratio, dP, qi, qg, qcap, qcount,
+                                                   next);
+    cudaEventRecord(ek, c->stream);
+    batched_dd_kernel<<<grid2, bsd, sm2, c->stream>>>(dG, seed, qi, qg, qcount, qcap, qy, qs);
+    cudaEventRecord(e1, c->stream);
+  };
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) {
+    cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&ek);
+    if (use_graph) {
+      // the two launches and their timing events form one CUDA graph
+      e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        enqueue();
+        e = cudaStreamEndCapture(c->stream, &graph);
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      if (e == cudaSuccess) e = cudaGraphLaunch(exec, c->stream);
+    } else {
+      enqueue();
+      e = cudaGetLastError();
+    }
+  }
+  unsigned long long nq = 0;
+  std::vector<Partial> parts(nch);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nq, qcount, 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(parts.data(), dP, nch * sizeof(Partial), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  float ms = 0, mk = 0;
+  if (e == cudaSuccess) { cudaEventElapsedTime(&ms, e0, e1); cudaEventElapsedTime(&mk, e0, ek); }
+  nq = std::min<unsigned long long>(nq, qcap);
+  std::vector<unsigned long long> hq(nq);
+  std::vector<int> hgq(nq), hs(nq);
+  std::vector<double> hy(nq);
+  if (e == cudaSuccess && nq) {
+    e = cudaMemcpy(hq.data(), qi, nq * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hgq.data(), qg, nq * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hy.data(), qy, nq * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hs.data(), qs, nq * 4, cudaMemcpyDeviceToHost);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (ek) cudaEventDestroy(ek);
+  if (e != cudaSuccess) return fail(c, AE_ERR_CUDA, std::string("batched: ") + cudaGetErrorString(e));
+  for (auto &pp : parts)
+    if (pp.n_overflow) return fail(c, AE_ERR_STATE, "double-double queue overflow");
+  (void)buf;
+  // per graph: chunk partials in chunk order, then re-evaluated samples in
+  // sample order
+  size_t G = ids.size();
+  std::vector<double> sy(G, 0), syl(G, 0), sy2(G, 0), sy2l(G, 0), sa(G, 0), sal(G, 0), mx(G, 0);
+  std::vector<uint64_t> n(G, 0), ndd(G, 0), nbad(G, 0);
+  for (size_t k = 0; k < nch; ++k) {
+    int gi = chunks[k].gi;
+    const Partial &q = parts[k];
+    host_dd_add(sy[gi], syl[gi], q.sy_hi); host_dd_add(sy[gi], syl[gi], q.sy_lo);
+    host_dd_add(sy2[gi], sy2l[gi], q.sy2_hi); host_dd_add(sy2[gi], sy2l[gi], q.sy2_lo);
+    host_dd_add(sa[gi], sal[gi], q.sa_hi); host_dd_add(sa[gi], sal[gi], q.sa_lo);
+    mx[gi] = std::max(mx[gi], q.max_y2);
+    n[gi] += q.n;
+  }
+  std::vector<size_t> ord(nq);
+  for (size_t i = 0; i < nq; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) {
+    return hgq[a] != hgq[b] ? hgq[a] < hgq[b] : hq[a] < hq[b];
+  });
+  for (size_t t : ord) {
+    int gi = hgq[t];
+    double y = hy[t];
+    if (hs[t]) ++nbad[gi];
+    ++ndd[gi];
+    host_dd_add(sy[gi], syl[gi], y); host_dd_add(sy2[gi], sy2l[gi], y * y); host_dd_add(sa[gi], sal[gi], std::fabs(y));
+    mx[gi] = std::max(mx[gi], y * y);
+  }
+  res.assign(G, ae_graph_result{});
+  for (size_t gi = 0; gi < G; ++gi) {
+    ae_graph_result &r = res[gi];
+    std::memset(&r, 0, sizeof(r));
+    r.sum_y = sy[gi] + syl[gi]; r.sum_y2 = sy2[gi] + sy2l[gi];
+    r.n = n[gi]; r.n_dd = ndd[gi]; r.n_nonfinite = nbad[gi];
+    double N = (double)r.n;
+    r.mean = r.sum_y / N;
+    double var = r.sum_y2 / (N * N) - r.sum_y * r.sum_y / (N * N * N);
+    r.sigma1 = var > 0 ? std::sqrt(var) : 0.0;
+    r.mean_abs = (sa[gi] + sal[gi]) / N;
+    r.max_y2 = mx[gi];
+    int mult = c->graphs[ids[gi]].g.mult;
+    r.value = mult * r.mean;
+    r.sigma = mult * r.sigma1;
+    r.seconds = ms * 1e-3 * (double)ns[gi] / (double)total;   // share of the launch by samples
+    r.kernel_seconds = mk * 1e-3 * (double)ns[gi] / (double)total;
+    r.launches = gi == 0 ? 2 : 0;
+    r.d2h_bytes = gi == 0 ? (8 + nch * sizeof(Partial) + nq * 24) : 0;
+    r.h2d_bytes = gi == 0 ? (ids.size() * sizeof(GraphDev) + nch * sizeof(Chunk)) : 0;
+  }
+  if (secs_out) *secs_out = ms * 1e-3;
+  return AE_OK;
+}
+
+// Autotuner: time the batched kernel on a small budget for each candidate
+// (block size x chunk size) and keep the fastest; cached per graph set.
+static int autotune_batched(ae_ctx *c, const std::vector<int> &ids, BatchTune &best) {
+  std::string key = std::to_string(c->loops) + ":";
+  for (int g : ids) key += std::to_string(g) + ",";
+  auto it = c->tune_cache.find(key);
+  if (it != c->tune_cache.end()) { best.block = it->second.first; best.chunk = it->second.second; return AE_OK; }
+  int maxslots = 0;
+  for (int g : ids) maxslots = std::max(maxslots, c->graphs[g].dev.nslots);
+  double best_rate = 0;
+  for (int bs : {64, 128, 256}) {
+    if ((size_t)bs * maxslots * 8 > 200 * 1024) continue;
+    for (unsigned long long ch : {4096ull, 16384ull, 65536ull}) {
+      uint64_t per = std::max<uint64_t>(ch * 2, (uint64_t)(c->sm_count * bs * 4 / std::max<size_t>(1, ids.size())));
+      std::vector<uint64_t> ns(ids.size(), per), fs(ids.size(), 1ull << 44);
+      std::vector<ae_graph_result> res;
+      double secs = 0;
+      int rc = run_batched(c, ids, ns, fs, 0x5eed, bs, ch, false, res, &secs);
+      if (rc) return rc;
+      double rate = (double)(per * ids.size()) / std::max(secs, 1e-9);
+      if (rate > best_rate) { best_rate = rate; best.block = bs; best.chunk = ch; }
+    }
+  }
+  c->tune_cache[key] = {best.block, best.chunk};
+  return AE_OK;
+}
+
+extern "C" int ae_integrate_batched(ae_ctx *c, const int *ids, int n_ids, const uint64_t *ns, uint64_t seed,
+                                    double *value, double *sigma, ae_graph_result *per) {
+  if (!c) return AE_ERR_ARG;
+  if (c->device < 0) return fail(c, AE_ERR_NODEV, "integration needs a CUDA device");
+  if (c->graphs.empty()) return fail(c, AE_ERR_STATE, "no graphs loaded");
+  if (!ids || !ns || n_ids <= 0) return fail(c, AE_ERR_ARG, "empty graph list");
+  std::vector<int> vid(ids, ids + n_ids);
+  std::vector<uint64_t> vn(ns, ns + n_ids), vf(n_ids, 0);
+  for (int i = 0; i < n_ids; ++i) {
+    if (ids[i] < 0 || ids[i] >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
+    if (ns[i] == 0) return fail(c, AE_ERR_ARG, "zero samples for a graph");
+  }
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  BatchTune t;
+  if (c->opts.block_size > 0) { t.block = c->opts.block_size; t.chunk = 16384; }
+  else {
+    int rc = autotune_batched(c, vid, t);
+    if (rc) return rc;
+  }
+  std::vector<ae_graph_result> res;
+  double secs = 0;
+  int rc = run_batched(c, vid, vn, vf, seed, t.block, t.chunk, true, res, &secs);
+  if (rc) return rc;
+  double v = 0, s2 = 0;
+  for (int i = 0; i < n_ids; ++i) {
+    v += res[i].value;
+    s2 += res[i].sigma * res[i].sigma;
+    if (per) per[i] = res[i];
+  }
+  if (value) *value = v;
+  if (sigma) *sigma = std::sqrt(s2);
+  c->last_tune_block = t.block;
+  c->last_tune_chunk = t.chunk;
+  return AE_OK;
+}
+
+// Inter-graph allocation (Sec. IV.C): a pilot of n_pilot samples per graph
+// (seed ^ 0x9E3779B97F4A7C15, independent of the main run's stream) gives
+// sigma_j; with C_j = sigma_j sqrt(N_pilot) and t_j the cost of one sample
+// (tape flops plus the sampler), mode 0 allocates n_j proportional to
+// C_j / sqrt(t_j) (the paper's optimum p_j), mode 1 proportional to the
+// variance estimate sigma_j^2.  Integer counts by largest remainder, at
+// least min(1024, n_total / n_ids) each.
+extern "C" int ae_allocate(ae_ctx *c, const int *ids, int n_ids, uint64_t n_pilot, uint64_t n_total, uint64_t seed,
+                           int mode, uint64_t *n_out, double *sigma_out) {
+  if (!c || !ids || !n_out || n_ids <= 0) return AE_ERR_ARG;
+  if (n_pilot == 0 || n_total < (uint64_t)n_ids) return fail(c, AE_ERR_ARG, "n_pilot > 0 and n_total >= n_ids needed");
+  if (mode != 0 && mode != 1) return fail(c, AE_ERR_ARG, "mode must be 0 or 1");
+  std::vector<uint64_t> np(n_ids, n_pilot);
+  std::vector<ae_graph_result> per(n_ids);
+  int rc = ae_integrate_batched(c, ids, n_ids, np.data(), seed ^ 0x9E3779B97F4A7C15ull, nullptr, nullptr, per.data());
+  if (rc) return rc;
+  std::vector<double> wgt(n_ids);
+  double sum = 0;
+  for (int i = 0; i < n_ids; ++i) {
+    const LoadedGraph &lg = c->graphs[ids[i]];
+    double sj = per[i].sigma;   // multiplicity included
+    double Cj = sj * std::sqrt((double)n_pilot);
+    double tj = lg.tape.flops + 150.0 * lg.g.M();
+    wgt[i] = mode == 0 ? Cj / std::sqrt(tj) : sj * sj;
+    if (!(wgt[i] > 0) || !std::isfinite(wgt[i])) wgt[i] = 0;
+    sum += wgt[i];
+    if (sigma_out) sigma_out[i] = sj;
+  }
+  uint64_t floor_n = std::min<uint64_t>(1024, n_total / n_ids);
+  uint64_t rest = n_total - floor_n * n_ids;
+  std::vector<double> frac(n_ids);
+  uint64_t given = 0;
+  for (int i = 0; i < n_ids; ++i) {
+    double want = sum > 0 ? (double)rest * wgt[i] / sum : (double)rest / n_ids;
+    uint64_t w = (uint64_t)std::floor(want);
+    n_out[i] = floor_n + w;
+    frac[i] = want - (double)w;
+    given += w;
+  }
+  std::vector<int> ord(n_ids);
+  for (int i = 0; i < n_ids; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return frac[a] > frac[b]; });
+  for (uint64_t k = 0; given + k < rest && k < (uint64_t)n_ids; ++k) n_out[ord[k]] += 1;
+  return AE_OK;
 }
 
 extern "C" int ae_eval_samples(ae_ctx *c, int gid, uint64_t first, uint64_t count, uint64_t seed,
