@@ -165,6 +165,7 @@ def main():
     ap.add_argument("--train", type=int, default=1 << 20, help="training samples per graph")
     ap.add_argument("--train-steps", type=int, default=150)
     ap.add_argument("--plain", action="store_true", help="time the plain density only (no learned proposal)")
+    ap.add_argument("--no-alloc", action="store_true", help="equal samples per graph in the learned+batched form")
     ap.add_argument("--oracle-samples", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -205,9 +206,20 @@ def main():
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
 
+    # inter-graph allocation (Sec. IV.C) from a pilot, for the learned+batched
+    # form: the same total budget per step, split n_j ~ sigma_j / sqrt(t_j)
+    alloc = [args.samples] * ngr
+    pilot_s = 0.0
+    if learned and not args.no_alloc:
+        t0 = time.perf_counter()
+        n_j, _ = ctx.allocate(ids, 1 << 18, args.samples * ngr, seed=99 + rank, mode=0)
+        alloc = [int(x) for x in n_j]
+        torch.cuda.synchronize()
+        pilot_s = time.perf_counter() - t0
+
     def step(seed):
         if learned:
-            return ctx.integrate_batched(ids, [args.samples] * ngr, seed=seed + rank * 1000003)
+            return ctx.integrate_batched(ids, alloc, seed=seed + rank * 1000003)
         return ctx.integrate(ids, args.samples, seed=seed + rank * 1000003)
 
     for w in range(args.warmup):
@@ -251,7 +263,7 @@ def main():
     # roofline of the dominant kernel: FP64 integrand kernel (sampler + tape)
     kern_s = sum(p["kernel_seconds"] for per in per_all for p in per)
     flops_per = [info[i]["flops"] + sampler_flops(M) for i in ids]
-    fl_total = sum(flops_per[i] * args.samples for i in ids) * args.steps
+    fl_total = sum(flops_per[i] * alloc[i] for i in ids) * args.steps
     achieved = fl_total / kern_s / 1e12
     launches = sum(p["launches"] for per in per_all for p in per)
     d2h = sum(p["d2h_bytes"] for per in per_all for p in per) / args.steps
@@ -303,11 +315,13 @@ def main():
                    "train_samples_per_graph": args.train if learned else 0,
                    "l2": "256 MB buffer written between timed steps", "parallelism": "dp%d" % world},
         "inv_sigma2_per_s": isps,
-        "inv_sigma2_per_s_incl_training": (1.0 / (sigma ** 2 * (t_dev + train_s)) if sigma > 0 else None),
+        "inv_sigma2_per_s_incl_training": (1.0 / (sigma ** 2 * (t_dev + train_s + pilot_s)) if sigma > 0 else None),
         "estimate": {"value": val, "sigma_down": sigma, "samples": total, "dd_reevaluated": int(n_dd),
                      "zeroed": int(zeroed)},
         "plain_pdf": plain,
-        "setup_seconds": {"compile": compile_s, "train": train_s},
+        "setup_seconds": {"compile": compile_s, "train": train_s, "pilot_allocation": pilot_s},
+        "allocation": {"min": min(alloc), "max": max(alloc), "mode": "pilot, n_j ~ sigma_j/sqrt(t_j)"}
+        if learned and not args.no_alloc else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": None,
                      "kernel": ("batched_kernel" if learned else "integrate_kernel") + " (sampler + FP64 tape)",

@@ -32,7 +32,7 @@ class AeGraphMeta(ctypes.Structure):
                 ("klass", ctypes.c_int * 3), ("word", ctypes.c_int * 11),
                 ("n_subgraphs", ctypes.c_int), ("n_terms", ctypes.c_int),
                 ("tape_len", ctypes.c_int), ("nslots", ctypes.c_int),
-                ("n_monomials", ctypes.c_int), ("flops", ctypes.c_double)]
+                ("n_monomials", ctypes.c_int), ("flops", ctypes.c_double), ("canonical_id", ctypes.c_int)]
 
 
 class AeTrainReport(ctypes.Structure):
@@ -71,6 +71,8 @@ def lib():
         L.ae_last_error.argtypes = [vp]
         L.ae_last_error.restype = ctypes.c_char_p
         L.ae_load_graphs.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
+        L.ae_seeded_subset.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64, P(ctypes.c_int)]
+        L.ae_load_graph_subset.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)]
         L.ae_graph_info.argtypes = [vp, ctypes.c_int, P(AeGraphMeta)]
         L.ae_integrate.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
                                    dp, dp, P(AeGraphResult)]
@@ -101,6 +103,14 @@ def lib():
 
 def _ptr(a, ct=ctypes.c_double):
     return None if a is None else a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def seeded_subset(n_total, k, seed=0):
+    """k of n_total indices chosen by the library's Philox-driven shuffle."""
+    out = np.empty(k, dtype=np.int32)
+    if lib().ae_seeded_subset(int(n_total), int(k), int(seed), _ptr(out, ctypes.c_int)) != 0:
+        raise AeError("AE_ERR_ARG: bad subset arguments")
+    return out.tolist()
 
 
 def default_opts():
@@ -142,6 +152,13 @@ class Context:
     def load_graphs(self, loops):
         n = ctypes.c_int()
         self._check(lib().ae_load_graphs(self._h, loops, ctypes.byref(n)))
+        self.n_graphs = n.value
+        return n.value
+
+    def load_graph_subset(self, loops, canonical_ids):
+        ids = np.ascontiguousarray(canonical_ids, dtype=np.int32)
+        n = ctypes.c_int()
+        self._check(lib().ae_load_graph_subset(self._h, loops, _ptr(ids, ctypes.c_int), len(ids), ctypes.byref(n)))
         self.n_graphs = n.value
         return n.value
 

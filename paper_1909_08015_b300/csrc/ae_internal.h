@@ -98,6 +98,12 @@ enum TapeOp : uint8_t {
   T_NEG = 10,  // d = -a
   T_ZERO = 11, // d = 0
   T_ADDABS = 12, // d = d + |a|
+  // register accumulator r (one per thread): accumulation chains without a
+  // shared-memory round trip per step
+  T_RZERO = 13,  // r = 0
+  T_RFMAC = 14,  // r = r + K[b] * a
+  T_RFMA = 15,   // r = r + a * b
+  T_RST = 16,    // d = r
 };
 struct Ins {
   uint8_t op;

@@ -723,8 +723,11 @@ static std::vector<int> emit_numerator(Builder &B, const FactorVals &fv, const s
     std::sort(vars.begin(), vars.end());
     order.push_back({vars, &m});
   }
+  // by Wick order j first (each j-accumulator's chain is contiguous and can
+  // live in the register accumulator), then lexicographically for prefix reuse
   std::sort(order.begin(), order.end(), [](const std::pair<std::vector<int>, const Mono *> &x,
                                            const std::pair<std::vector<int>, const Mono *> &y) {
+    if (x.second->j != y.second->j) return x.second->j < y.second->j;
     return x.first < y.first;
   });
   ProdStack ps;
@@ -903,13 +906,65 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
     B.prog.swap(np);
     B.flops = fl;
   }
+  // ------------------------------------------- register accumulators --
+  // A chain ZERO d; {FMAC|FMA} d ...; (first plain read of d) becomes
+  // RZERO; {RFMAC|RFMA} ...; RST d when no other register chain is open.
+  {
+    std::vector<Builder::SIns> np;
+    np.reserve(B.prog.size() + 16);
+    size_t i = 0;
+    const size_t N = B.prog.size();
+    auto reads_plain = [&](const Builder::SIns &in, int v) {
+      bool b_val = in.op == T_ADD || in.op == T_SUB || in.op == T_MUL || in.op == T_DIV || in.op == T_FMA;
+      return in.a == v || (b_val && in.b == v);
+    };
+    while (i < N) {
+      const auto &z = B.prog[i];
+      if (z.op != T_ZERO) { np.push_back(z); ++i; continue; }
+      int d = z.d;
+      // find the extent: accumulations into d up to the first other use of d
+      size_t last = i;
+      bool other = false;
+      for (size_t k = i + 1; k < N; ++k) {
+        const auto &in = B.prog[k];
+        bool acc_d = (in.op == T_FMAC || in.op == T_FMA) && in.d == d && !(in.op == T_FMA && (in.a == d || in.b == d));
+        if (acc_d) { last = k; continue; }
+        if (reads_plain(in, d) || in.d == d) break;
+        if (in.op == T_ZERO) { other = true; break; }   // another chain would start inside
+      }
+      (void)other;
+      // only worth it when the chain has at least two steps
+      size_t nacc = 0;
+      for (size_t k = i + 1; k <= last; ++k)
+        if ((B.prog[k].op == T_FMAC || B.prog[k].op == T_FMA) && B.prog[k].d == d) ++nacc;
+      bool clean = nacc >= 2;
+      for (size_t k = i + 1; k <= last && clean; ++k) {
+        const auto &in = B.prog[k];
+        if (in.op == T_ZERO || in.op == T_ADDABS) clean = false;
+        if ((in.op == T_FMAC || in.op == T_FMA) && in.d != d) clean = false;
+      }
+      if (!clean) { np.push_back(z); ++i; continue; }
+      np.push_back({T_RZERO, -1, -1, -1});
+      for (size_t k = i + 1; k <= last; ++k) {
+        const auto &in = B.prog[k];
+        if (in.op == T_FMAC && in.d == d) np.push_back({T_RFMAC, -1, in.a, in.b});
+        else if (in.op == T_FMA && in.d == d) np.push_back({T_RFMA, -1, in.a, in.b});
+        else np.push_back(in);
+      }
+      np.push_back({T_RST, d, -1, -1});
+      i = last + 1;
+    }
+    B.prog.swap(np);
+  }
   // ---------------------------------------------------- slot allocation --
   std::vector<int> last(B.nvals, -1);
+  auto bval = [](uint8_t op) {
+    return op == T_ADD || op == T_SUB || op == T_MUL || op == T_DIV || op == T_FMA || op == T_RFMA;
+  };
   for (size_t i = 0; i < B.prog.size(); ++i) {
     auto &in = B.prog[i];
-    bool b_is_val = (in.op == T_ADD || in.op == T_SUB || in.op == T_MUL || in.op == T_DIV || in.op == T_FMA);
     if (in.a >= 0) last[in.a] = (int)i;
-    if (b_is_val && in.b >= 0) last[in.b] = (int)i;
+    if (bval(in.op) && in.b >= 0) last[in.b] = (int)i;
     if (in.op == T_FMA || in.op == T_FMAC || in.op == T_ADDABS) last[in.d] = (int)i;
   }
   last[outI] = last[outK] = (int)B.prog.size();
@@ -921,9 +976,20 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
   tp.M = B.M;
   for (size_t i = 0; i < B.prog.size(); ++i) {
     auto in = B.prog[i];
-    bool b_is_val = (in.op == T_ADD || in.op == T_SUB || in.op == T_MUL || in.op == T_DIV || in.op == T_FMA);
+    bool b_is_val = bval(in.op);
     int sa = in.a >= 0 ? slot[in.a] : 0;
     int sb = b_is_val ? slot[in.b] : in.b;
+    if (in.op == T_RZERO || in.op == T_RFMAC || in.op == T_RFMA) {
+      // register ops: no destination slot; release operands at their last use
+      std::vector<int> rel2;
+      if (in.a >= B.M && last[in.a] == (int)i) rel2.push_back(in.a);
+      if (b_is_val && in.b >= B.M && last[in.b] == (int)i && in.b != in.a) rel2.push_back(in.b);
+      for (int v : rel2) freelist.push_back(slot[v]);
+      Ins ins;
+      ins.op = in.op; ins.pad = 0; ins.d = 0; ins.a = (uint16_t)sa; ins.b = (uint16_t)sb;
+      tp.code.push_back(ins);
+      continue;
+    }
     // release operands whose last use is here (before allocating d, so d may reuse)
     bool accum = (in.op == T_FMA || in.op == T_FMAC || in.op == T_ADDABS);
     std::vector<int> rel;
@@ -960,6 +1026,7 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
 // against the oracle without a GPU.
 void tape_replay(const Tape &t, const double *z, double *I, double *K) {
   std::vector<double> s(t.nslots, 0.0);
+  double r = 0.0;
   for (int i = 0; i < t.M; ++i) s[i] = z[i];
   for (const Ins &in : t.code) {
     double &d = s[in.d];
@@ -976,6 +1043,10 @@ void tape_replay(const Tape &t, const double *z, double *I, double *K) {
       case T_NEG: d = -s[in.a]; break;
       case T_ZERO: d = 0.0; break;
       case T_ADDABS: d = d + std::fabs(s[in.a]); break;
+      case T_RZERO: r = 0.0; break;
+      case T_RFMAC: r = std::fma(t.khi[in.b], s[in.a], r); break;
+      case T_RFMA: r = std::fma(s[in.a], s[in.b], r); break;
+      case T_RST: d = r; break;
       default: throw std::runtime_error("bad opcode");
     }
   }

@@ -32,6 +32,7 @@ struct LoadedGraph {
   CompileStats st;
   GraphDev dev{};
   LearnedState learned;
+  int canonical_id = 0;     // index in the full canonical list of its loop order
 };
 
 struct ae_ctx {

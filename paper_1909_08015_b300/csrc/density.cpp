@@ -13,7 +13,10 @@
 // (finite variance needs Deg(s) < 2 * true exponent).
 // Phi(T) = sum_{j in T} Phi(T\j)/Deg(T\j), Phi({j}) = 1; the sector
 // probability of an ordering is prod 1/Deg(s_l) / Phi(all).
+#include <algorithm>
 #include <cmath>
+#include <cstdint>
+#include <vector>
 
 #include "ae_internal.h"
 
@@ -121,4 +124,36 @@ DensityTables build_density(const Graph &g, const DensityConsts &c) {
   return t;
 }
 
+// Host Philox4x32-10 (same definition as the device generator).
+void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)M0 * c[0], p1 = (uint64_t)M1 * c[2];
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0, n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+    c[0] = n0; c[1] = (uint32_t)p1; c[2] = n2; c[3] = (uint32_t)p0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+}
+
 }  // namespace ae
+
+// Seeded subset of k indices out of n_total: Fisher-Yates driven by Philox
+// (counter = (i, 0, 0xFFFF, 0x5E1EC7), key = seed); ascending output.
+extern "C" int ae_seeded_subset(uint64_t n_total, int k, uint64_t seed, int *out) {
+  if (!out || k < 0 || (uint64_t)k > n_total || n_total > (1ull << 31)) return -1;
+  std::vector<int> a(n_total);
+  for (uint64_t i = 0; i < n_total; ++i) a[i] = (int)i;
+  for (uint64_t t = 0; t < (uint64_t)k; ++t) {
+    uint64_t i = n_total - 1 - t;
+    uint32_t c[4] = {(uint32_t)i, 0u, 0xFFFFu, 0x5E1EC7u};
+    ae::philox_host(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    double u = ((double)(c[0] >> 5) * 67108864.0 + (double)(c[1] >> 6)) * (1.0 / 9007199254740992.0);
+    uint64_t j = (uint64_t)(u * (double)(i + 1));
+    if (j > i) j = i;
+    std::swap(a[i], a[j]);
+  }
+  std::vector<int> sel(a.end() - k, a.end());
+  std::sort(sel.begin(), sel.end());
+  for (int t = 0; t < k; ++t) out[t] = sel[t];
+  return 0;
+}

@@ -267,21 +267,29 @@ __device__ __forceinline__ void draw_any(const GraphDev &G, uint64_t idx, uint64
 }
 
 // FP64 tape interpreter.  S points at this thread's column of the slot file
-// (stride = blockDim.x).
+// (stride = blockDim.x); r is the register accumulator.  The next
+// instruction word is fetched while the current one executes.
 __device__ __forceinline__ void run_tape(const GraphDev &G, double *S, int stride) {
   const uint2 *code = G.code;
   const double *K = G.khi;
-  for (int pc = 0; pc < G.ntape; ++pc) {
-    uint2 w = __ldg(code + pc);
+  const int n = G.ntape;
+  double r = 0.0;
+  uint2 w = __ldg(code);
+  for (int pc = 0; pc < n; ++pc) {
+    uint2 wn = __ldg(code + min(pc + 1, n - 1));
     int op = w.x & 0xff;
     int d = w.x >> 16;
     int a = w.y & 0xffff;
     int b = w.y >> 16;
     double *D = S + d * stride;
     switch (op) {
+      case T_RFMAC: r = __fma_rn(__ldg(K + b), S[a * stride], r); break;
+      case T_MUL: *D = __dmul_rn(S[a * stride], S[b * stride]); break;
+      case T_RFMA: r = __fma_rn(S[a * stride], S[b * stride], r); break;
+      case T_RZERO: r = 0.0; break;
+      case T_RST: *D = r; break;
       case T_ADD: *D = __dadd_rn(S[a * stride], S[b * stride]); break;
       case T_SUB: *D = __dadd_rn(S[a * stride], -S[b * stride]); break;
-      case T_MUL: *D = __dmul_rn(S[a * stride], S[b * stride]); break;
       case T_DIV: *D = __ddiv_rn(S[a * stride], S[b * stride]); break;
       case T_FMA: *D = __fma_rn(S[a * stride], S[b * stride], *D); break;
       case T_FMAC: *D = __fma_rn(__ldg(K + b), S[a * stride], *D); break;
@@ -293,30 +301,36 @@ __device__ __forceinline__ void run_tape(const GraphDev &G, double *S, int strid
       case T_ADDABS: *D = __dadd_rn(*D, fabs(S[a * stride])); break;
       default: break;
     }
+    w = wn;
   }
 }
 
 // Double-double twin of run_tape (slot file holds hi/lo pairs).
 static __device__ void run_tape_dd(const GraphDev &G, dd *S, int stride) {
+  dd r = {0.0, 0.0};
   for (int pc = 0; pc < G.ntape; ++pc) {
     uint2 w = __ldg(G.code + pc);
     int op = w.x & 0xff, d = w.x >> 16, a = w.y & 0xffff, b = w.y >> 16;
     dd *D = S + d * stride;
     dd kb = {0, 0};
-    if (op == T_FMAC || op == T_MULC || op == T_CONST) kb = {__ldg(G.khi + b), __ldg(G.klo + b)};
+    if (op == T_FMAC || op == T_MULC || op == T_CONST || op == T_RFMAC) kb = {__ldg(G.khi + b), __ldg(G.klo + b)};
     switch (op) {
-      case T_ADD: *D = dd_add(S[a * stride], S[b * stride]); break;
-      case T_SUB: { dd t = S[b * stride]; *D = dd_add(S[a * stride], {-t.hi, -t.lo}); } break;
-      case T_MUL: *D = dd_mul(S[a * stride], S[b * stride]); break;
+      case T_RZERO: r = {0.0, 0.0}; break;
+      case T_RFMAC: r = dd_fma_fast(r, kb, S[a * stride]); break;
+      case T_RFMA: r = dd_fma_fast(r, S[a * stride], S[b * stride]); break;
+      case T_RST: *D = r; break;
+      case T_ADD: *D = dd_add_fast(S[a * stride], S[b * stride]); break;
+      case T_SUB: { dd t = S[b * stride]; *D = dd_add_fast(S[a * stride], {-t.hi, -t.lo}); } break;
+      case T_MUL: *D = dd_mul_fast(S[a * stride], S[b * stride]); break;
       case T_DIV: *D = dd_div(S[a * stride], S[b * stride]); break;
-      case T_FMA: *D = dd_add(*D, dd_mul(S[a * stride], S[b * stride])); break;
-      case T_FMAC: *D = dd_add(*D, dd_mul(kb, S[a * stride])); break;
-      case T_MULC: *D = dd_mul(kb, S[a * stride]); break;
+      case T_FMA: *D = dd_fma_fast(*D, S[a * stride], S[b * stride]); break;
+      case T_FMAC: *D = dd_fma_fast(*D, kb, S[a * stride]); break;
+      case T_MULC: *D = dd_mul_fast(kb, S[a * stride]); break;
       case T_CONST: *D = kb; break;
       case T_ABS: *D = dd_abs(S[a * stride]); break;
       case T_NEG: { dd t = S[a * stride]; *D = {-t.hi, -t.lo}; } break;
       case T_ZERO: *D = {0.0, 0.0}; break;
-      case T_ADDABS: *D = dd_add(*D, dd_abs(S[a * stride])); break;
+      case T_ADDABS: *D = dd_add_fast(*D, dd_abs(S[a * stride])); break;
       default: break;
     }
   }

@@ -382,11 +382,35 @@ extern "C" void ae_destroy(ae_ctx *c) {
 
 extern "C" const char *ae_last_error(const ae_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
+static int load_impl(ae_ctx *c, int loops, const int *subset, int n_subset, int *n_out);
+
 extern "C" int ae_load_graphs(ae_ctx *c, int loops, int *n_out) {
+  return load_impl(c, loops, nullptr, 0, n_out);
+}
+
+extern "C" int ae_load_graph_subset(ae_ctx *c, int loops, const int *canonical_ids, int n_ids, int *n_out) {
+  if (!c) return AE_ERR_ARG;
+  if (!canonical_ids || n_ids <= 0) return fail(c, AE_ERR_ARG, "empty subset");
+  return load_impl(c, loops, canonical_ids, n_ids, n_out);
+}
+
+static int load_impl(ae_ctx *c, int loops, const int *subset, int n_subset, int *n_out) {
   if (!c) return AE_ERR_ARG;
   if (loops < 1 || loops > 5) return fail(c, AE_ERR_ARG, "loops must be 1..5");
+  std::vector<int> canon;
   try {
-    std::vector<Graph> gs = enumerate_graphs(loops);
+    std::vector<Graph> all = enumerate_graphs(loops);
+    std::vector<Graph> gs;
+    if (subset) {
+      for (int k = 0; k < n_subset; ++k) {
+        if (subset[k] < 0 || subset[k] >= (int)all.size()) return fail(c, AE_ERR_ARG, "canonical id out of range");
+        gs.push_back(all[subset[k]]);
+        canon.push_back(subset[k]);
+      }
+    } else {
+      gs = all;
+      for (size_t k = 0; k < all.size(); ++k) canon.push_back((int)k);
+    }
     DensityConsts dc;
     dc.C2 = c->opts.C2; dc.C3 = c->opts.C3; dc.C4 = c->opts.C4; dc.D = c->opts.D;
     dc.CsubI = c->opts.C_subI; dc.CsubSE = c->opts.C_subSE; dc.CsubO = c->opts.C_subO;
@@ -403,6 +427,7 @@ extern "C" int ae_load_graphs(ae_ctx *c, int loops, int *n_out) {
           L[i].terms = rnew_terms(gs[i], L[i].subs);
           L[i].tape = compile_integrand(gs[i], &L[i].st);
           L[i].dens = build_density(gs[i], dc);
+          L[i].canonical_id = canon[i];
         } catch (std::exception &e) {
           errs[i] = e.what();
         }
@@ -451,7 +476,8 @@ extern "C" int ae_load_graphs(ae_ctx *c, int loops, int *n_out) {
       CUDA_TRY(c, cudaMemcpy(p, lg.tape.code.data(), lg.tape.code.size() * 8, cudaMemcpyHostToDevice));
       p += al(lg.tape.code.size() * 8);
       G.M = lg.g.M(); G.ntape = (int)lg.tape.code.size(); G.nslots = lg.tape.nslots;
-      G.outI = lg.tape.out_I; G.outK = lg.tape.out_K; G.graph_id = (int)gi;
+      G.outI = lg.tape.out_I; G.outK = lg.tape.out_K; G.graph_id = canon[gi];   // Philox stream of the graph
+      lg.canonical_id = canon[gi];
       G.C1 = lg.dens.C[0]; G.C2 = lg.dens.C[1]; G.C3 = lg.dens.C[2]; G.C4 = lg.dens.C[3];
       G.log2_fact = lg.dens.log2_fact;
       for (int k = 0; k < 4; ++k) G.log2C[k] = ae_log2(lg.dens.C[k]);
@@ -473,6 +499,7 @@ extern "C" int ae_graph_info(ae_ctx *c, int id, ae_graph_meta *o) {
   o->n_subgraphs = (int)lg.subs.size(); o->n_terms = (int)lg.terms.size();
   o->tape_len = (int)lg.tape.code.size(); o->nslots = lg.tape.nslots;
   o->n_monomials = lg.st.n_monomials; o->flops = lg.tape.flops;
+  o->canonical_id = lg.canonical_id;
   return AE_OK;
 }
 
@@ -685,10 +712,16 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return c->graphs[ids[a]].dev.ntape > c->graphs[ids[b]].dev.ntape;
   });
+  // Chunks graph by graph.  A graph gets at least ~2 chunks per resident CTA
+  // when its budget allows, so the CTAs work on one or two tapes at a time and
+  // the tape stays in L2 (many different tapes in flight thrash it).
+  uint64_t resident = (uint64_t)c->sm_count * per_sm;
   std::vector<Chunk> chunks;
-  for (int oi : order)
-    for (uint64_t s0 = 0; s0 < ns[oi]; s0 += chunk)
-      chunks.push_back(Chunk{oi, 0, firsts[oi] + s0, std::min<uint64_t>(chunk, ns[oi] - s0)});
+  for (int oi : order) {
+    uint64_t cg = std::min<uint64_t>(chunk, std::max<uint64_t>((ns[oi] + 2 * resident - 1) / (2 * resident), (uint64_t)bs));
+    for (uint64_t s0 = 0; s0 < ns[oi]; s0 += cg)
+      chunks.push_back(Chunk{oi, 0, firsts[oi] + s0, std::min<uint64_t>(cg, ns[oi] - s0)});
+  }
   uint64_t total = 0;
   for (uint64_t x : ns) total += x;
   size_t nch = chunks.size();
@@ -727,14 +760,20 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   unsigned grid = (unsigned)(c->sm_count * per_sm);
   unsigned grid2 = (unsigned)(c->sm_count * 4);
   cudaEvent_t e0 = nullptr, e1 = nullptr, ek = nullptr;
+  // events recorded with cudaEventRecordExternal so that, inside a captured
+  // graph, they become event-record nodes readable after the launch
+  auto rec = [&](cudaEvent_t ev) {
+    if (use_graph) cudaEventRecordWithFlags(ev, c->stream, cudaEventRecordExternal);
+    else cudaEventRecord(ev, c->stream);
+  };
   auto enqueue = [&]() {
-    cudaEventRecord(e0, c->stream);
+    rec(e0);
     cudaMemsetAsync(qcount, 0, 16, c->stream);
     batched_kernel<<<grid, bs, smem, c->stream>>>(dG, dC, (int)nch, seed, c->opts.dd_ratio, dP, qi, qg, qcap, qcount,
                                                    next);
-    cudaEventRecord(ek, c->stream);
+    rec(ek);
     batched_dd_kernel<<<grid2, bsd, sm2, c->stream>>>(dG, seed, qi, qg, qcount, qcap, qy, qs);
-    cudaEventRecord(e1, c->stream);
+    rec(e1);
   };
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -760,7 +799,10 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   if (e == cudaSuccess) e = cudaMemcpyAsync(parts.data(), dP, nch * sizeof(Partial), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   float ms = 0, mk = 0;
-  if (e == cudaSuccess) { cudaEventElapsedTime(&ms, e0, e1); cudaEventElapsedTime(&mk, e0, ek); }
+  if (e == cudaSuccess) {
+    cudaError_t t1 = cudaEventElapsedTime(&ms, e0, e1), t2 = cudaEventElapsedTime(&mk, e0, ek);
+    if (t1 != cudaSuccess || t2 != cudaSuccess) e = t1 != cudaSuccess ? t1 : t2;
+  }
   nq = std::min<unsigned long long>(nq, qcap);
   std::vector<unsigned long long> hq(nq);
   std::vector<int> hgq(nq), hs(nq);
@@ -841,17 +883,28 @@ static int autotune_batched(ae_ctx *c, const std::vector<int> &ids, BatchTune &b
   if (it != c->tune_cache.end()) { best.block = it->second.first; best.chunk = it->second.second; return AE_OK; }
   int maxslots = 0;
   for (int g : ids) maxslots = std::max(maxslots, c->graphs[g].dev.nslots);
+  // trial set: up to six graphs spanning the tape lengths (longest, shortest,
+  // quantiles), so tuning costs a fraction of a second even for 269 graphs
+  std::vector<int> byl = ids;
+  std::sort(byl.begin(), byl.end(), [&](int a, int b) { return c->graphs[a].dev.ntape > c->graphs[b].dev.ntape; });
+  std::vector<int> trial;
+  for (int q = 0; q < 6 && q < (int)byl.size(); ++q) {
+    int k = (int)((size_t)q * (byl.size() - 1) / 5);
+    if (std::find(trial.begin(), trial.end(), byl[k]) == trial.end()) trial.push_back(byl[k]);
+  }
   double best_rate = 0;
   for (int bs : {64, 128, 256}) {
     if ((size_t)bs * maxslots * 8 > 200 * 1024) continue;
-    for (unsigned long long ch : {4096ull, 16384ull, 65536ull}) {
-      uint64_t per = std::max<uint64_t>(ch * 2, (uint64_t)(c->sm_count * bs * 4 / std::max<size_t>(1, ids.size())));
-      std::vector<uint64_t> ns(ids.size(), per), fs(ids.size(), 1ull << 44);
+    for (unsigned long long ch : {1024ull, 4096ull, 16384ull}) {
+      uint64_t per = std::max<uint64_t>(ch * 4, (uint64_t)c->sm_count * bs * 8 / trial.size());
+      std::vector<uint64_t> ns(trial.size(), per), fs(trial.size(), 1ull << 44);
       std::vector<ae_graph_result> res;
       double secs = 0;
-      int rc = run_batched(c, ids, ns, fs, 0x5eed, bs, ch, false, res, &secs);
+      int rc = run_batched(c, trial, ns, fs, 0x5eed, bs, ch, false, res, &secs);
       if (rc) return rc;
-      double rate = (double)(per * ids.size()) / std::max(secs, 1e-9);
+      double fl = 0;
+      for (int g : trial) fl += c->graphs[g].tape.flops * (double)per;
+      double rate = fl / std::max(secs, 1e-9);   // tape flops per second
       if (rate > best_rate) { best_rate = rate; best.block = bs; best.chunk = ch; }
     }
   }

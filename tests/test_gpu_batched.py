@@ -23,6 +23,7 @@ def test_batched_matches_per_graph(ctx):
     ids = list(range(28))
     ns = [200000 + 3001 * i for i in ids]          # uneven counts, ragged chunks
     vb, sb, pb = ctx.integrate_batched(ids, ns, seed=8)
+    assert sum(p["seconds"] for p in pb) > 0 and sum(p["kernel_seconds"] for p in pb) > 0
     for i in (0, 5, 13, 22, 27):
         _, _, pg = ctx.integrate([i], ns[i], seed=8)
         assert pb[i]["n"] == ns[i]
