@@ -64,12 +64,25 @@ const char *ae_last_error(const ae_ctx *ctx);
  * loaded set.  1 <= loops <= 5. */
 int ae_load_graphs(ae_ctx *ctx, int loops, int *n_graphs_out);
 
+/* Load only the listed graphs (indices into the canonical list of `loops`
+ * loops); the loaded graphs get ids 0..n_ids-1 in the given order, and each
+ * keeps its canonical index as its Philox stream (graph word of the counter),
+ * so a graph draws the same samples whichever set it is loaded with. */
+int ae_load_graph_subset(ae_ctx *ctx, int loops, const int *canonical_ids, int n_ids, int *n_graphs_out);
+
+/* Seeded choice of k graph indices out of n_total (Fisher-Yates driven by
+ * Philox4x32-10, key = seed): the "seeded random subsets" of graphs used by
+ * the 4- and 5-loop workloads.  Ascending output; returns 0, or -1 on bad
+ * arguments.  No context needed. */
+int ae_seeded_subset(uint64_t n_total, int k, uint64_t seed, int *out);
+
 typedef struct ae_graph_meta {
   int loops, M, mult;
   int klass[3];          /* (k, m, m') of Sec. V, Table I */
   int word[11];          /* path word, -1 = external vertex; 2n+1 entries */
   int n_subgraphs, n_terms, tape_len, nslots, n_monomials;
   double flops;          /* FP64 flops of one tape evaluation (FMA = 2) */
+  int canonical_id;      /* index in the full canonical list */
 } ae_graph_meta;
 int ae_graph_info(ae_ctx *ctx, int graph_id, ae_graph_meta *out);
 
@@ -98,6 +111,13 @@ typedef struct ae_graph_result {
  * launch per graph.  Deterministic for given (ids, n_samples, seed, opts). */
 int ae_integrate(ae_ctx *ctx, const int *graph_ids, int n_ids, uint64_t n_samples,
                  uint64_t seed, double *value, double *sigma, ae_graph_result *per_graph);
+
+/* Samples first .. first+count-1 of one graph (the same Philox stream as
+ * ae_integrate): resuming a run or sharding a graph by counter range.  The
+ * sums of consecutive ranges add up to the sums of the whole range (up to
+ * summation order). */
+int ae_integrate_range(ae_ctx *ctx, int graph_id, uint64_t first, uint64_t count, uint64_t seed,
+                       ae_graph_result *out);
 
 /* Batched form: all listed graphs with their own sample counts in ONE
  * persistent launch: a work queue of (graph, counter range) chunks, longest

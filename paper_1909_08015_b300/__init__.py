@@ -78,6 +78,8 @@ def lib():
                                    dp, dp, P(AeGraphResult)]
         L.ae_integrate_batched.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_uint64),
                                            ctypes.c_uint64, dp, dp, P(AeGraphResult)]
+        L.ae_integrate_range.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                         P(AeGraphResult)]
         L.ae_allocate.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
                                   ctypes.c_uint64, ctypes.c_int, P(ctypes.c_uint64), dp]
         L.ae_train_proposal.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
@@ -189,6 +191,11 @@ class Context:
                                                _ptr(ns, ctypes.c_uint64), int(seed),
                                                ctypes.byref(v), ctypes.byref(s), res))
         return v.value, s.value, [r.as_dict() for r in res]
+
+    def integrate_range(self, gid, first, count, seed=0):
+        r = AeGraphResult()
+        self._check(lib().ae_integrate_range(self._h, gid, int(first), int(count), int(seed), ctypes.byref(r)))
+        return r.as_dict()
 
     def allocate(self, ids, n_pilot, n_total, seed=0, mode=0):
         ids = np.ascontiguousarray(ids, dtype=np.int32)

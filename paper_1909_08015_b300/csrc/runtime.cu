@@ -184,6 +184,7 @@ struct Chunk {
 __global__ void batched_kernel(const GraphDev *graphs, const Chunk *chunks, int nchunks, uint64_t seed,
                                double dd_ratio, Partial *part, unsigned long long *queue_idx, int *queue_gi,
                                unsigned long long qcap, unsigned long long *qcount, int *next) {
+  // chunks/part point at this launch's slice of the chunk list
   extern __shared__ double slots[];
   __shared__ int cur, curg;
   __shared__ GraphDev G;     // descriptor of the current chunk's graph
@@ -228,16 +229,41 @@ __global__ void batched_kernel(const GraphDev *graphs, const Chunk *chunks, int 
   }
 }
 
+// Counting sort of the re-evaluation queue by graph (so that the warps of the
+// double-double pass run one tape each): histogram, exclusive scan, scatter.
+__global__ void queue_hist_kernel(const int *queue_gi, const unsigned long long *qcount, unsigned long long qcap,
+                                  const int *rank, unsigned int *hist) {
+  uint64_t nq = min(*qcount, qcap);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (uint64_t)gridDim.x * blockDim.x)
+    atomicAdd(hist + rank[queue_gi[i]], 1u);
+}
+__global__ void queue_scan_kernel(unsigned int *hist, int ngraphs) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    unsigned int acc = 0;
+    for (int g = 0; g < ngraphs; ++g) { unsigned int v = hist[g]; hist[g] = acc; acc += v; }
+  }
+}
+__global__ void queue_scatter_kernel(const unsigned long long *qi, const int *qg, const unsigned long long *qcount,
+                                     unsigned long long qcap, const int *rank, unsigned int *offs,
+                                     unsigned long long *qi2, int *qg2) {
+  uint64_t nq = min(*qcount, qcap);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (uint64_t)gridDim.x * blockDim.x) {
+    unsigned int pos = atomicAdd(offs + rank[qg[i]], 1u);
+    qi2[pos] = qi[i];
+    qg2[pos] = qg[i];
+  }
+}
+
 // Double-double re-evaluation of the batched queue (count read on the device,
 // so the launch shape is fixed and the pair can be captured in a graph).
 __global__ void batched_dd_kernel(const GraphDev *graphs, uint64_t seed, const unsigned long long *queue_idx,
-                                  const int *queue_gi, const unsigned long long *qcount, unsigned long long qcap,
+                                  const int *queue_gi, const unsigned int *beg, const unsigned int *end,
                                   double *y_out, int *status) {
   extern __shared__ dd bdsl[];
   dd *S = bdsl + threadIdx.x;
   const int stride = blockDim.x;
-  uint64_t nq = min(*qcount, qcap);
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (uint64_t)gridDim.x * blockDim.x) {
+  uint64_t i0 = beg ? *beg : 0, i1 = *end;
+  for (uint64_t i = i0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < i1; i += (uint64_t)gridDim.x * blockDim.x) {
     const GraphDev &G = graphs[queue_gi[i]];
     double z[14], lz[14], lg;
     draw_any(G, queue_idx[i], seed, z, lz, lg);
@@ -503,15 +529,35 @@ extern "C" int ae_graph_info(ae_ctx *c, int id, ae_graph_meta *o) {
   return AE_OK;
 }
 
-static int pick_block(const ae_ctx *c, int nslots, size_t elem) {
+// Block size for a kernel whose dynamic shared memory is bs * nslots * elem:
+// the candidate with the most resident warps per SM (the slot file, not the
+// register file, is what limits residency for long tapes), ties to the
+// larger block.
+static int pick_block_for(const ae_ctx *c, const void *kernel, int nslots, size_t elem) {
   const size_t smem_cap = 200 * 1024;
-  int bs = c->opts.block_size;
-  if (bs <= 0) {
-    bs = 256;
-    while (bs > 32 && (size_t)bs * nslots * elem > smem_cap) bs /= 2;
+  if (c->opts.block_size > 0) {
+    int bs = c->opts.block_size;
+    return (size_t)bs * nslots * elem > smem_cap ? -1 : bs;
   }
-  if ((size_t)bs * nslots * elem > smem_cap) return -1;
-  return bs;
+  int best = -1, best_warps = 0;
+  for (int bs : {256, 128, 64, 32}) {
+    size_t smem = (size_t)bs * nslots * elem;
+    if (smem > smem_cap) continue;
+    int per_sm = 0;
+    if (kernel) {
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, bs, smem) != cudaSuccess) per_sm = 0;
+    } else {
+      per_sm = (int)std::min<size_t>(32, (228 * 1024) / (smem + 3072));
+    }
+    int warps = per_sm * bs / 32;
+    if (warps > best_warps) { best_warps = warps; best = bs; }
+  }
+  return best;
+}
+
+static int pick_block(const ae_ctx *c, int nslots, size_t elem) {
+  return pick_block_for(c, nullptr, nslots, elem);
 }
 
 static int ensure_scratch(ae_ctx *c, size_t nparts, size_t qcap) {
@@ -549,7 +595,7 @@ static void host_dd_add(double &hi, double &lo, double x) {
 static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_graph_result *res) {
   LoadedGraph &lg = c->graphs[gid];
   GraphDev &G = lg.dev;
-  int bs = pick_block(c, G.nslots, 8);
+  int bs = pick_block_for(c, (const void *)integrate_kernel, G.nslots, 8);
   if (bs < 0) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
   size_t smem = (size_t)bs * G.nslots * 8;
   CUDA_TRY(c, cudaFuncSetAttribute(integrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -586,7 +632,7 @@ static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_g
       return fail(c, AE_ERR_STATE, "double-double queue overflow");
     }
     if (nq) {
-      int bsd = pick_block(c, G.nslots, 16);
+      int bsd = pick_block_for(c, (const void *)dd_kernel, G.nslots, 16);
       if (bsd < 0) return fail(c, AE_ERR_STATE, "double-double slot file does not fit in shared memory");
       size_t sm2 = (size_t)bsd * G.nslots * 16;
       CUDA_TRY(c, cudaFuncSetAttribute(dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
@@ -650,6 +696,31 @@ static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_g
   return AE_OK;
 }
 
+static int run_batched(ae_ctx *c, const std::vector<int> &ids, const std::vector<uint64_t> &ns,
+                       const std::vector<uint64_t> &firsts, uint64_t seed, int bs, uint64_t chunk,
+                       bool use_graph, std::vector<ae_graph_result> &res, double *secs_out);
+
+// Samples [first, first + count) of one graph (resume / sharding by counter
+// range): the same Philox stream as ae_integrate, so ranges concatenate.
+extern "C" int ae_integrate_range(ae_ctx *c, int gid, uint64_t first, uint64_t count, uint64_t seed,
+                                  ae_graph_result *out) {
+  if (!c || !out) return AE_ERR_ARG;
+  if (c->device < 0) return fail(c, AE_ERR_NODEV, "integration needs a CUDA device");
+  if (gid < 0 || gid >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
+  if (count == 0) return fail(c, AE_ERR_ARG, "zero samples");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  std::vector<int> ids = {gid};
+  std::vector<uint64_t> ns = {count}, fs = {first};
+  std::vector<ae_graph_result> res;
+  double secs = 0;
+  int bs = pick_block(c, c->graphs[gid].dev.nslots, 8);
+  if (bs < 0) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
+  int rc = run_batched(c, ids, ns, fs, seed, bs, 16384, false, res, &secs);
+  if (rc) return rc;
+  *out = res[0];
+  return AE_OK;
+}
+
 extern "C" int ae_integrate(ae_ctx *c, const int *ids, int n_ids, uint64_t nsamp, uint64_t seed,
                             double *value, double *sigma, ae_graph_result *per) {
   if (!c) return AE_ERR_ARG;
@@ -700,16 +771,21 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
                          bool use_graph, std::vector<ae_graph_result> &res, double *secs_out, bool full_queue) {
   int maxslots = 0;
   for (int g : ids) maxslots = std::max(maxslots, c->graphs[g].dev.nslots);
-  size_t smem = (size_t)bs * maxslots * 8;
-  if (smem > 200 * 1024) return fail(c, AE_ERR_STATE, "batched slot file does not fit in shared memory");
-  CUDA_TRY(c, cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, bs, smem));
-  if (per_sm < 1) per_sm = 1;
-  // chunks: graphs by decreasing tape length (longest first balances the tail)
+  int per_sm = 1;
+  // Buckets of similar slot-file size, one persistent launch each (a launch
+  // sized for the largest tape would cut the occupancy of all the others);
+  // inside a bucket, graphs by decreasing tape length (balances the tail).
   std::vector<int> order(ids.size());
   for (size_t i = 0; i < ids.size(); ++i) order[i] = (int)i;
+  auto bucket_of = [&](int oi) {
+    int ns_ = c->graphs[ids[oi]].dev.nslots;
+    int b = 0;
+    for (int lim : {40, 56, 72, 96, 128, 176, 256, 512}) { if (ns_ <= lim) return b; ++b; }
+    return b;
+  };
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    int ba = bucket_of(a), bb = bucket_of(b);
+    if (ba != bb) return ba < bb;
     return c->graphs[ids[a]].dev.ntape > c->graphs[ids[b]].dev.ntape;
   });
   // Chunks graph by graph.  A graph gets at least ~2 chunks per resident CTA
@@ -717,19 +793,47 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   // the tape stays in L2 (many different tapes in flight thrash it).
   uint64_t resident = (uint64_t)c->sm_count * per_sm;
   std::vector<Chunk> chunks;
-  for (int oi : order) {
-    uint64_t cg = std::min<uint64_t>(chunk, std::max<uint64_t>((ns[oi] + 2 * resident - 1) / (2 * resident), (uint64_t)bs));
-    for (uint64_t s0 = 0; s0 < ns[oi]; s0 += cg)
-      chunks.push_back(Chunk{oi, 0, firsts[oi] + s0, std::min<uint64_t>(cg, ns[oi] - s0)});
+  struct Launch { size_t c0, c1; int bs; size_t smem; unsigned grid; };
+  std::vector<Launch> launches;
+  for (size_t k = 0; k < order.size();) {
+    int b = bucket_of(order[k]);
+    size_t k1 = k;
+    int bslots = 0;
+    while (k1 < order.size() && bucket_of(order[k1]) == b) { bslots = std::max(bslots, c->graphs[ids[order[k1]]].dev.nslots); ++k1; }
+    Launch L;
+    L.c0 = chunks.size();
+    // block size: the tuned one if it fits, else the occupancy choice for this bucket
+    L.bs = ((size_t)bs * bslots * 8 <= 200 * 1024) ? bs : pick_block_for(c, (const void *)batched_kernel, bslots, 8);
+    if (L.bs < 0) return fail(c, AE_ERR_STATE, "batched slot file does not fit in shared memory");
+    L.smem = (size_t)L.bs * bslots * 8;
+    int pm = 0;
+    CUDA_TRY(c, cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+    CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pm, batched_kernel, L.bs, L.smem));
+    if (pm < 1) pm = 1;
+    L.grid = (unsigned)(c->sm_count * pm);
+    uint64_t res_b = (uint64_t)L.grid;
+    for (size_t t = k; t < k1; ++t) {
+      int oi = order[t];
+      uint64_t cg = std::min<uint64_t>(chunk, std::max<uint64_t>((ns[oi] + 2 * res_b - 1) / (2 * res_b), (uint64_t)L.bs));
+      for (uint64_t s0 = 0; s0 < ns[oi]; s0 += cg)
+        chunks.push_back(Chunk{oi, 0, firsts[oi] + s0, std::min<uint64_t>(cg, ns[oi] - s0)});
+    }
+    L.c1 = chunks.size();
+    launches.push_back(L);
+    k = k1;
   }
+  (void)resident;
+  size_t smax = 0;
+  for (const Launch &L : launches) smax = std::max(smax, L.smem);
+  CUDA_TRY(c, cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
   uint64_t total = 0;
   for (uint64_t x : ns) total += x;
   size_t nch = chunks.size();
   size_t qcap = (size_t)std::max<uint64_t>(full_queue ? total : total / 4, 65536);
   // device buffers (graph descriptors, chunks, partials, queue), kept in the
   // context and grown when a larger batch arrives
-  size_t need = ids.size() * sizeof(GraphDev) + nch * sizeof(Chunk) + nch * sizeof(Partial) + qcap * (8 + 4 + 8 + 4) +
-                64 + 8 * 256;
+  size_t need = ids.size() * sizeof(GraphDev) + nch * sizeof(Chunk) + nch * sizeof(Partial) +
+                qcap * (8 + 4 + 8 + 4 + 8 + 4) + ids.size() * 8 + 64 * 4 + 8 * 768;
   if (need > c->bbuf_bytes) {
     if (c->bbuf) cudaFree(c->bbuf);
     c->bbuf = nullptr;
@@ -747,16 +851,48 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   int *qg = (int *)p; p += al(qcap * 4);
   double *qy = (double *)p; p += al(qcap * 8);
   int *qs = (int *)p; p += al(qcap * 4);
-  unsigned long long *qcount = (unsigned long long *)p; p += 64;
-  int *next = (int *)(qcount + 1);
+  unsigned long long *qi2 = (unsigned long long *)p; p += al(qcap * 8);
+  int *qg2 = (int *)p; p += al(qcap * 4);
+  unsigned int *hist = (unsigned int *)p; p += al(ids.size() * 4);
+  int *drank = (int *)p; p += al(ids.size() * 4);
+  unsigned long long *qcount = (unsigned long long *)p; p += 256;
+  int *next = (int *)(qcount + 1);   // one counter per launch (up to 32)
   std::vector<GraphDev> hg;
   for (int g : ids) hg.push_back(c->graphs[g].dev);
+  // rank of each graph in bucket order; last rank of each bucket
+  std::vector<int> hrank(ids.size());
+  for (size_t r = 0; r < order.size(); ++r) hrank[order[r]] = (int)r;
+  std::vector<int> bucket_last;   // rank of the last graph of each launch's bucket
+  {
+    size_t r = 0;
+    for (const Launch &L : launches) {
+      (void)L;
+      int b = bucket_of(order[r]);
+      while (r < order.size() && bucket_of(order[r]) == b) ++r;
+      bucket_last.push_back((int)r - 1);
+    }
+  }
   cudaError_t e = cudaMemcpyAsync(dG, hg.data(), hg.size() * sizeof(GraphDev), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(drank, hrank.data(), hrank.size() * 4, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dC, chunks.data(), nch * sizeof(Chunk), cudaMemcpyHostToDevice, c->stream);
-  int bsd = pick_block(c, maxslots, 16);
-  if (bsd < 0) bsd = 32;
-  size_t sm2 = (size_t)bsd * maxslots * 16;
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+  // one double-double launch per bucket, shaped for that bucket's slots
+  std::vector<int> dd_bs(launches.size());
+  std::vector<size_t> dd_sm(launches.size());
+  size_t ddmax = 0;
+  {
+    size_t r = 0;
+    for (size_t l = 0; l < launches.size(); ++l) {
+      int bslots = 0;
+      int b = bucket_of(order[r]);
+      while (r < order.size() && bucket_of(order[r]) == b) { bslots = std::max(bslots, c->graphs[ids[order[r]]].dev.nslots); ++r; }
+      int b16 = pick_block_for(c, (const void *)batched_dd_kernel, bslots, 16);
+      if (b16 < 0) b16 = 32;
+      dd_bs[l] = b16;
+      dd_sm[l] = (size_t)b16 * bslots * 16;
+      ddmax = std::max(ddmax, dd_sm[l]);
+    }
+  }
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ddmax);
   unsigned grid = (unsigned)(c->sm_count * per_sm);
   unsigned grid2 = (unsigned)(c->sm_count * 4);
   cudaEvent_t e0 = nullptr, e1 = nullptr, ek = nullptr;
@@ -768,11 +904,23 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   };
   auto enqueue = [&]() {
     rec(e0);
-    cudaMemsetAsync(qcount, 0, 16, c->stream);
-    batched_kernel<<<grid, bs, smem, c->stream>>>(dG, dC, (int)nch, seed, c->opts.dd_ratio, dP, qi, qg, qcap, qcount,
-                                                   next);
+    cudaMemsetAsync(qcount, 0, 256, c->stream);
+    cudaMemsetAsync(hist, 0, ids.size() * 4, c->stream);
+    for (size_t l = 0; l < launches.size(); ++l) {
+      const Launch &L = launches[l];
+      batched_kernel<<<L.grid, L.bs, L.smem, c->stream>>>(dG, dC + L.c0, (int)(L.c1 - L.c0), seed, c->opts.dd_ratio,
+                                                          dP + L.c0, qi, qg, qcap, qcount, next + l);
+    }
     rec(ek);
-    batched_dd_kernel<<<grid2, bsd, sm2, c->stream>>>(dG, seed, qi, qg, qcount, qcap, qy, qs);
+    queue_hist_kernel<<<grid2, 256, 0, c->stream>>>(qg, qcount, qcap, drank, hist);
+    queue_scan_kernel<<<1, 32, 0, c->stream>>>(hist, (int)ids.size());
+    queue_scatter_kernel<<<grid2, 256, 0, c->stream>>>(qi, qg, qcount, qcap, drank, hist, qi2, qg2);
+    // after the scatter hist[r] is the end of bin r: bucket l spans
+    // [hist[last of l-1], hist[last of l])
+    for (size_t l = 0; l < launches.size(); ++l) {
+      const unsigned int *bg = l == 0 ? nullptr : hist + bucket_last[l - 1];
+      batched_dd_kernel<<<grid2, dd_bs[l], dd_sm[l], c->stream>>>(dG, seed, qi2, qg2, bg, hist + bucket_last[l], qy, qs);
+    }
     rec(e1);
   };
   cudaGraph_t graph = nullptr;
@@ -808,8 +956,8 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   std::vector<int> hgq(nq), hs(nq);
   std::vector<double> hy(nq);
   if (e == cudaSuccess && nq) {
-    e = cudaMemcpy(hq.data(), qi, nq * 8, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(hgq.data(), qg, nq * 4, cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(hq.data(), qi2, nq * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hgq.data(), qg2, nq * 4, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(hy.data(), qy, nq * 8, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(hs.data(), qs, nq * 4, cudaMemcpyDeviceToHost);
   }
@@ -866,7 +1014,7 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     r.sigma = mult * r.sigma1;
     r.seconds = ms * 1e-3 * (double)ns[gi] / (double)total;   // share of the launch by samples
     r.kernel_seconds = mk * 1e-3 * (double)ns[gi] / (double)total;
-    r.launches = gi == 0 ? 2 : 0;
+    r.launches = gi == 0 ? (uint64_t)(2 * launches.size() + 3) : 0;
     r.d2h_bytes = gi == 0 ? (8 + nch * sizeof(Partial) + nq * 24) : 0;
     r.h2d_bytes = gi == 0 ? (ids.size() * sizeof(GraphDev) + nch * sizeof(Chunk)) : 0;
   }

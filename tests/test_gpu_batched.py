@@ -57,3 +57,17 @@ def test_four_loop_batched_runs(ctx):
     for i in (0, 134, 268):
         _, _, pg = ctx.integrate([i], 1 << 14, seed=1)
         assert abs(pb[i]["sum_y"] - pg[0]["sum_y"]) <= 1e-9 * abs(pg[0]["sum_y"]) + 1e-300
+
+
+def test_resume_by_counter_range(ctx):
+    """Two consecutive counter ranges add up to the whole range (resume and
+    sharding by range draw exactly the samples of an uninterrupted run)."""
+    ctx.load_graphs(2)
+    whole = ctx.integrate_range(3, 0, 400000, seed=4)
+    a = ctx.integrate_range(3, 0, 150000, seed=4)
+    b = ctx.integrate_range(3, 150000, 250000, seed=4)
+    assert a["n"] + b["n"] == whole["n"]
+    assert abs(a["sum_y"] + b["sum_y"] - whole["sum_y"]) <= 1e-12 * abs(whole["sum_y"]) + 1e-12
+    assert abs(a["sum_y2"] + b["sum_y2"] - whole["sum_y2"]) <= 1e-12 * whole["sum_y2"]
+    _, _, per = ctx.integrate([3], 400000, seed=4)
+    assert abs(per[0]["sum_y"] - whole["sum_y"]) <= 1e-9 * abs(whole["sum_y"])
