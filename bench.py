@@ -230,6 +230,7 @@ def main():
     clocks = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
         os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv")
     clocks.start()
+    torch.cuda.nvtx.range_push("timed")
     dev_ms = 0.0
     e2e_s = 0.0
     per_all = []
@@ -246,6 +247,7 @@ def main():
         e2e_s += time.perf_counter() - t0
         dev_ms += ev0.elapsed_time(ev1)
         per_all.append(per)
+    torch.cuda.nvtx.range_pop()
     ck = clocks.stop(local)
     t_dev = dev_ms / 1e3
     if dist:

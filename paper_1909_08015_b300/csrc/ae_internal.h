@@ -104,7 +104,19 @@ enum TapeOp : uint8_t {
   T_RFMAC = 14,  // r = r + K[b] * a
   T_RFMA = 15,   // r = r + a * b
   T_RST = 16,    // d = r
+  // Horner form of a sum of monomials: a stack of register accumulators
+  // R[0..kHLevels-1]; the level k of an instruction is op - base.  Each op is
+  // one FMA; "first" ops start R[k] from the node's own coefficient K[d].
+  T_HFL = 32,    // R[k] = a * K[b] + K[d]      (first edge, leaf child)
+  T_HL = 48,     // R[k] = a * K[b] + R[k]      (leaf child)
+  T_HFU = 64,    // R[k] = a * R[k+1] + K[d]    (first edge, inner child)
+  T_HU = 80,     // R[k] = a * R[k+1] + R[k]    (inner child)
+  T_HST = 96,    // d = R[0]
 };
+constexpr int kHLevels = 12;   // register accumulators of the Horner stack
+inline bool is_horner(int op) { return op >= T_HFL && op < T_HST; }
+inline int horner_kind(int op) { return op & ~15; }
+inline int horner_level(int op) { return op & 15; }
 struct Ins {
   uint8_t op;
   uint8_t pad;

@@ -27,6 +27,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <climits>
 #include <numeric>
 #include <stdexcept>
 #include <unordered_map>
@@ -519,7 +520,7 @@ static std::vector<Mono> expand_factor(const Factor &f, int chan, const std::vec
 
 // ========================================================== tape builder ==
 struct Builder {
-  struct SIns { uint8_t op; int d, a, b; };   // value ids; b may be a constant index
+  struct SIns { uint8_t op; int d, a, b; int c = -1; };   // value ids; b (and c) may be constant indices
   std::vector<SIns> prog;
   std::vector<double> khi, klo;
   std::map<std::pair<double, double>, int> kidx;
@@ -527,6 +528,7 @@ struct Builder {
   int M = 0;
   std::map<std::tuple<int, int, int>, int> cse;
   double flops = 0;
+  bool horner = true;   // Horner trees for sums of monomials (else monomial chains)
 
   int newval() { return nvals++; }
   int konst(double hi, double lo = 0.0) {
@@ -590,9 +592,80 @@ static int stack_product(Builder &B, ProdStack &ps, const std::vector<int> &v) {
   return ps.vals.back();
 }
 
+// ------------------------------------------------------------ Horner --
+// A sum of monomials  sum_m K[k_m] prod(vars_m)  evaluated by greedy
+// multivariate Horner factorisation: at every node the variable that occurs
+// in most of the node's monomials is factored out,
+//     q = x * q_x + q_rest,
+// recursively, so that every edge of the resulting tree costs one FMA into
+// the register accumulator of its depth and no monomial is multiplied out.
+// Returns false (emitting nothing) when the tree is deeper than the register
+// stack.
+struct HMono { std::vector<int> v; int k; };   // sorted variable multiset, constant index
+
+static int horner_depth(const std::vector<HMono> &ms) {
+  size_t d = 0;
+  for (auto &m : ms) d = std::max(d, m.v.size());
+  return (int)d;
+}
+
+static void horner_node(Builder &B, std::vector<HMono> &ms, int lvl, int coef, int zero_k) {
+  // ms: monomials of this node with at least one variable each; coef: the
+  // node's own constant index or -1.
+  bool first = true;
+  std::vector<HMono> rest;
+  rest.swap(ms);
+  while (!rest.empty()) {
+    std::map<int, int> cnt;
+    for (auto &m : rest) {
+      int prev = -1;
+      for (int x : m.v) if (x != prev) { cnt[x]++; prev = x; }
+    }
+    int best = -1, bc = -1;
+    for (auto &kv : cnt) if (kv.second > bc) { bc = kv.second; best = kv.first; }
+    std::vector<HMono> grp, oth;
+    int leaf_k = -1;
+    for (auto &m : rest) {
+      auto it = std::find(m.v.begin(), m.v.end(), best);
+      if (it == m.v.end()) { oth.push_back(std::move(m)); continue; }
+      m.v.erase(it);
+      if (m.v.empty()) leaf_k = m.k;
+      else grp.push_back(std::move(m));
+    }
+    rest.swap(oth);
+    int addend = first ? (coef >= 0 ? coef : zero_k) : -1;
+    if (grp.empty()) {
+      // x * K[leaf] (+ accumulator or node coefficient)
+      B.prog.push_back({(uint8_t)((first ? T_HFL : T_HL) + lvl), -1, best, leaf_k, addend});
+    } else {
+      horner_node(B, grp, lvl + 1, leaf_k, zero_k);
+      B.prog.push_back({(uint8_t)((first ? T_HFU : T_HU) + lvl), -1, best, -1, addend});
+    }
+    B.flops += (first && addend == zero_k) ? 1 : 2;
+    first = false;
+  }
+}
+
+// Emits the Horner evaluation of ms into a fresh value; monomials must have
+// distinct variable lists.  Returns -1 if it does not fit the register stack.
+static int emit_horner(Builder &B, std::vector<HMono> ms) {
+  if (horner_depth(ms) >= kHLevels) return -1;
+  int coef = -1;
+  std::vector<HMono> inner;
+  for (auto &m : ms) {
+    std::sort(m.v.begin(), m.v.end());
+    if (m.v.empty()) coef = m.k;
+    else inner.push_back(std::move(m));
+  }
+  if (inner.empty()) return coef >= 0 ? B.cval(coef) : B.zero();
+  horner_node(B, inner, 0, coef, B.konst(0.0));
+  int d = B.newval();
+  B.prog.push_back({T_HST, d, -1, -1});
+  return d;
+}
+
 // polynomial in z evaluated into a fresh accumulator
 static int emit_poly(Builder &B, const Poly &p) {
-  int acc = B.zero();
   std::vector<std::pair<std::vector<int>, double>> ms;
   for (auto &kv : p.t) {
     std::vector<int> vars;
@@ -603,6 +676,13 @@ static int emit_poly(Builder &B, const Poly &p) {
     ms.push_back({vars, kv.second});
   }
   std::sort(ms.begin(), ms.end());
+  if (B.horner) {
+    std::vector<HMono> hm;
+    for (auto &m : ms) hm.push_back({m.first, B.konst(m.second)});
+    int v = emit_horner(B, hm);
+    if (v >= 0) return v;
+  }
+  int acc = B.zero();
   ProdStack ps;
   int one = -1;
   for (auto &m : ms) {
@@ -730,8 +810,47 @@ static std::vector<int> emit_numerator(Builder &B, const FactorVals &fv, const s
     if (x.second->j != y.second->j) return x.second->j < y.second->j;
     return x.first < y.first;
   });
-  ProdStack ps;
   B.clear_cse();
+  if (B.horner) {
+    // one Horner tree per Wick order j; equal variable lists merged exactly
+    std::vector<int> res(jmax + 1, -1);
+    bool ok = true;
+    for (int j = 0; j <= jmax && ok; ++j) {
+      std::map<std::vector<int>, std::pair<long long, long long>> merged;
+      for (auto &o : order) {
+        if (o.second->j != j) continue;
+        auto it = merged.find(o.first);
+        if (it == merged.end()) { merged[o.first] = {o.second->num, o.second->den}; continue; }
+        long long n1 = it->second.first, d1 = it->second.second;
+        long long n2 = o.second->num, d2 = o.second->den;
+        long long g = gcdll(d1, d2);
+        __int128 num = (__int128)n1 * (d2 / g) + (__int128)n2 * (d1 / g), den = (__int128)(d1 / g) * d2;
+        __int128 h = num, b2 = den;
+        if (h < 0) h = -h;
+        while (b2) { __int128 t = h % b2; h = b2; b2 = t; }
+        if (h == 0) h = 1;
+        num /= h; den /= h;
+        if (num > LLONG_MAX || num < -LLONG_MAX || den > LLONG_MAX) ok = false;
+        it->second = {(long long)num, (long long)den};
+      }
+      if (merged.empty()) continue;
+      std::vector<HMono> hm;
+      for (auto &kv : merged)
+        if (kv.second.first != 0) hm.push_back({kv.first, B.konst_rat(kv.second.first, kv.second.second)});
+      if (hm.empty()) { res[j] = B.zero(); continue; }
+      int v = emit_horner(B, hm);
+      if (v < 0) ok = false;
+      res[j] = v;
+    }
+    if (ok) {
+      int rU2 = B.bin(T_MUL, fv.rU, fv.rU);
+      for (auto &a : res)
+        if (a >= 0) a = B.bin(T_MUL, a, rU2);
+      B.clear_cse();
+      return res;
+    }
+  }
+  ProdStack ps;
   for (auto &o : order) {
     const Mono &m = *o.second;
     int mv;
@@ -887,8 +1006,16 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
     std::vector<char> live(B.nvals, 0);
     live[outI] = live[outK] = 1;
     std::vector<char> keep(B.prog.size(), 0);
+    bool hlive = false;   // the Horner ops before an HST live with it
     for (int i = (int)B.prog.size() - 1; i >= 0; --i) {
       auto &in = B.prog[i];
+      if (is_horner(in.op)) {
+        if (!hlive) continue;
+        keep[i] = 1;
+        live[in.a] = 1;
+        continue;
+      }
+      if (in.op == T_HST) hlive = live[in.d] != 0;
       if (!live[in.d]) continue;
       keep[i] = 1;
       if (in.a >= 0) live[in.a] = 1;
@@ -897,11 +1024,17 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
     }
     std::vector<Builder::SIns> np;
     double fl = 0;
+    const int zk = B.konst(0.0);
     for (size_t i = 0; i < B.prog.size(); ++i)
       if (keep[i]) {
         np.push_back(B.prog[i]);
         uint8_t op = B.prog[i].op;
-        fl += (op == T_FMA || op == T_FMAC) ? 2 : (op == T_CONST || op == T_ZERO) ? 0 : 1;
+        if (is_horner(op)) {
+          int kind = horner_kind(op);
+          fl += ((kind == T_HFL || kind == T_HFU) && B.prog[i].c == zk) ? 1 : 2;
+          continue;
+        }
+        fl += (op == T_FMA || op == T_FMAC) ? 2 : (op == T_CONST || op == T_ZERO || op == T_HST) ? 0 : 1;
       }
     B.prog.swap(np);
     B.flops = fl;
@@ -979,6 +1112,16 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
     bool b_is_val = bval(in.op);
     int sa = in.a >= 0 ? slot[in.a] : 0;
     int sb = b_is_val ? slot[in.b] : in.b;
+    if (is_horner(in.op)) {
+      if (in.a >= B.M && last[in.a] == (int)i) freelist.push_back(slot[in.a]);
+      Ins ins;
+      ins.op = in.op; ins.pad = 0;
+      ins.d = (uint16_t)(in.c >= 0 ? in.c : 0);
+      ins.a = (uint16_t)sa;
+      ins.b = (uint16_t)(in.b >= 0 ? in.b : 0);
+      tp.code.push_back(ins);
+      continue;
+    }
     if (in.op == T_RZERO || in.op == T_RFMAC || in.op == T_RFMA) {
       // register ops: no destination slot; release operands at their last use
       std::vector<int> rel2;
@@ -1013,6 +1156,7 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
     ins.d = (uint16_t)sd; ins.a = (uint16_t)sa; ins.b = (uint16_t)sb;
     tp.code.push_back(ins);
   }
+  if (B.khi.size() > 65535) throw std::runtime_error("constant pool exceeds 16-bit indices");
   tp.khi = B.khi; tp.klo = B.klo;
   tp.nslots = nslots;
   tp.out_I = slot[outI]; tp.out_K = slot[outK];
@@ -1027,8 +1171,20 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
 void tape_replay(const Tape &t, const double *z, double *I, double *K) {
   std::vector<double> s(t.nslots, 0.0);
   double r = 0.0;
+  double R[kHLevels + 1] = {0};
   for (int i = 0; i < t.M; ++i) s[i] = z[i];
   for (const Ins &in : t.code) {
+    if (is_horner(in.op)) {
+      int k = horner_level(in.op);
+      switch (horner_kind(in.op)) {
+        case T_HFL: R[k] = std::fma(s[in.a], t.khi[in.b], t.khi[in.d]); break;
+        case T_HL: R[k] = std::fma(s[in.a], t.khi[in.b], R[k]); break;
+        case T_HFU: R[k] = std::fma(s[in.a], R[k + 1], t.khi[in.d]); break;
+        case T_HU: R[k] = std::fma(s[in.a], R[k + 1], R[k]); break;
+      }
+      continue;
+    }
+    if (in.op == T_HST) { s[in.d] = R[0]; continue; }
     double &d = s[in.d];
     switch (in.op) {
       case T_ADD: d = s[in.a] + s[in.b]; break;

@@ -266,14 +266,29 @@ __device__ __forceinline__ void draw_any(const GraphDev &G, uint64_t idx, uint64
   else draw_sample(G, idx, seed, z, lz, lg);
 }
 
+// Horner-stack cases of the interpreters: level k accumulates into R##k and
+// reads its child level from R##k1.
+#define AE_HCASES(k, k1)                                                             \
+  case T_HFL + k: R##k = __fma_rn(S[a * stride], __ldg(K + b), __ldg(K + d)); break; \
+  case T_HL + k: R##k = __fma_rn(S[a * stride], __ldg(K + b), R##k); break;          \
+  case T_HFU + k: R##k = __fma_rn(S[a * stride], R##k1, __ldg(K + d)); break;        \
+  case T_HU + k: R##k = __fma_rn(S[a * stride], R##k1, R##k); break;
+#define AE_HCASES_ALL                                                                \
+  AE_HCASES(0, 1) AE_HCASES(1, 2) AE_HCASES(2, 3) AE_HCASES(3, 4) AE_HCASES(4, 5)     \
+  AE_HCASES(5, 6) AE_HCASES(6, 7) AE_HCASES(7, 8) AE_HCASES(8, 9) AE_HCASES(9, 10)    \
+  AE_HCASES(10, 11)
+static_assert(kHLevels == 12, "interpreter cases cover Horner levels 0..10 (degree <= 11)");
+
 // FP64 tape interpreter.  S points at this thread's column of the slot file
-// (stride = blockDim.x); r is the register accumulator.  The next
-// instruction word is fetched while the current one executes.
+// (stride = blockDim.x); r is the register accumulator of monomial chains and
+// R0..R11 the Horner stack.  The next instruction word is fetched while the
+// current one executes.
 __device__ __forceinline__ void run_tape(const GraphDev &G, double *S, int stride) {
   const uint2 *code = G.code;
   const double *K = G.khi;
   const int n = G.ntape;
   double r = 0.0;
+  double R0 = 0, R1 = 0, R2 = 0, R3 = 0, R4 = 0, R5 = 0, R6 = 0, R7 = 0, R8 = 0, R9 = 0, R10 = 0, R11 = 0;
   uint2 w = __ldg(code);
   for (int pc = 0; pc < n; ++pc) {
     uint2 wn = __ldg(code + min(pc + 1, n - 1));
@@ -299,6 +314,8 @@ __device__ __forceinline__ void run_tape(const GraphDev &G, double *S, int strid
       case T_NEG: *D = -S[a * stride]; break;
       case T_ZERO: *D = 0.0; break;
       case T_ADDABS: *D = __dadd_rn(*D, fabs(S[a * stride])); break;
+      AE_HCASES_ALL
+      case T_HST: *D = R0; break;
       default: break;
     }
     w = wn;
@@ -308,9 +325,28 @@ __device__ __forceinline__ void run_tape(const GraphDev &G, double *S, int strid
 // Double-double twin of run_tape (slot file holds hi/lo pairs).
 static __device__ void run_tape_dd(const GraphDev &G, dd *S, int stride) {
   dd r = {0.0, 0.0};
+  dd R[kHLevels];
+#pragma unroll
+  for (int k = 0; k < kHLevels; ++k) R[k] = {0.0, 0.0};
   for (int pc = 0; pc < G.ntape; ++pc) {
     uint2 w = __ldg(G.code + pc);
     int op = w.x & 0xff, d = w.x >> 16, a = w.y & 0xffff, b = w.y >> 16;
+    if (op >= T_HFL && op < T_HST) {
+      // Horner stack: unrolled over the levels so that R stays in registers
+      const int kind = op & ~15, lvl = op & 15;
+      dd x = S[a * stride];
+      dd kb = {0, 0}, kd = {0, 0};
+      if (kind == T_HFL || kind == T_HL) kb = {__ldg(G.khi + b), __ldg(G.klo + b)};
+      if (kind == T_HFL || kind == T_HFU) kd = {__ldg(G.khi + d), __ldg(G.klo + d)};
+#pragma unroll
+      for (int k = 0; k < kHLevels - 1; ++k) {
+        if (k != lvl) continue;
+        dd m = (kind == T_HFL || kind == T_HL) ? kb : R[k + 1];
+        dd acc = (kind == T_HFL || kind == T_HFU) ? kd : R[k];
+        R[k] = dd_fma_fast(acc, m, x);
+      }
+      continue;
+    }
     dd *D = S + d * stride;
     dd kb = {0, 0};
     if (op == T_FMAC || op == T_MULC || op == T_CONST || op == T_RFMAC) kb = {__ldg(G.khi + b), __ldg(G.klo + b)};
@@ -331,6 +367,7 @@ static __device__ void run_tape_dd(const GraphDev &G, dd *S, int stride) {
       case T_NEG: { dd t = S[a * stride]; *D = {-t.hi, -t.lo}; } break;
       case T_ZERO: *D = {0.0, 0.0}; break;
       case T_ADDABS: *D = dd_add_fast(*D, dd_abs(S[a * stride])); break;
+      case T_HST: *D = R[0]; break;
       default: break;
     }
   }
