@@ -29,12 +29,27 @@ sys.path.insert(0, ROOT)
 METRIC = "MC samples/s and 1/(σ²·s) per graph set, learned+batched vs plain pdf, 1 B300"
 
 
-def sampler_flops(M):
+def sampler_flops(M, learned=False):
     """FP64 operations of one draw of the sampler and density (FMA = 2),
-    counted from the steps of the walk: uniforms (4 ops each, 2M of them),
-    M-1 walk steps (product, |T| additions, one series log2 of 42 ops, a
-    quotient and a sum), M series exp2 (76 ops) with normalisation, and the
-    density of three sector components plus the mixture (4 exp2, 1 log2)."""
+    counted from the steps of the walk.
+
+    Plain density (series log2/exp2, bit-reproducible on the host): uniforms
+    (4 ops each, 2M of them), M-1 walk steps (product, |T| additions, one
+    series log2 of 42 ops, a quotient and a sum), M series exp2 (76 ops) with
+    normalisation, and the density of three sector components plus the
+    mixture (4 exp2, 1 log2).
+
+    Learned mixture: the same uniforms; M-1 walk steps of |T| additions, one
+    log2, a product and a sum; normalisation (M exp2, M sums, one log2, one
+    reciprocal, 2M products/differences); three sector densities (3 ops per
+    level); the learned density (5 ops per level); one five-term log-sum-exp.
+    Each call of the device's exp2/log2 counts as ONE operation here, so the
+    learned count is a lower bound."""
+    if learned:
+        walk = sum((M - l) + 3 for l in range(M - 1))
+        norm = 4 * M + 2
+        pdf = 9 * (M - 1) + 14 + 5 * (M - 1) + 2 + 17
+        return 8 * M + walk + norm + pdf
     walk = sum(1 + (M - l) + 42 + 2 for l in range(M - 1))
     norm = M * 76 + M + 42 + 2 * M
     pdf = M + 3 * (M - 1) * 3 + 9 + 4 * (2 + 76) + 42 + 2
@@ -264,7 +279,7 @@ def main():
     rate = total / t_dev
     # roofline of the dominant kernel: FP64 integrand kernel (sampler + tape)
     kern_s = sum(p["kernel_seconds"] for per in per_all for p in per)
-    flops_per = [info[i]["flops"] + sampler_flops(M) for i in ids]
+    flops_per = [info[i]["flops"] + sampler_flops(M, learned) for i in ids]
     fl_total = sum(flops_per[i] * alloc[i] for i in ids) * args.steps
     achieved = fl_total / kern_s / 1e12
     launches = sum(p["launches"] for per in per_all for p in per)

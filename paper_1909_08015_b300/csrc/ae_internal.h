@@ -83,8 +83,9 @@ double ae_log2(double x);
 double ae_exp2(double x);
 
 // ------------------------------------------------------------- tapes -----
-// One tape instruction (8 bytes).  Slots hold FP64 values; z occupies slots
-// 0..M-1 on entry.  Constants live in a per-graph pool (hi, lo) pairs.
+// Operations of the integrand compiler's intermediate program (value ids,
+// constants in a per-graph pool).  They are lowered to the device instruction
+// format Ins below.
 enum TapeOp : uint8_t {
   T_ADD = 1,   // d = a + b
   T_SUB = 2,   // d = a - b
@@ -98,36 +99,38 @@ enum TapeOp : uint8_t {
   T_NEG = 10,  // d = -a
   T_ZERO = 11, // d = 0
   T_ADDABS = 12, // d = d + |a|
-  // register accumulator r (one per thread): accumulation chains without a
-  // shared-memory round trip per step
-  T_RZERO = 13,  // r = 0
-  T_RFMAC = 14,  // r = r + K[b] * a
-  T_RFMA = 15,   // r = r + a * b
-  T_RST = 16,    // d = r
-  // Horner form of a sum of monomials: a stack of register accumulators
-  // R[0..kHLevels-1]; the level k of an instruction is op - base.  Each op is
-  // one FMA; "first" ops start R[k] from the node's own coefficient K[d].
-  T_HFL = 32,    // R[k] = a * K[b] + K[d]      (first edge, leaf child)
-  T_HL = 48,     // R[k] = a * K[b] + R[k]      (leaf child)
-  T_HFU = 64,    // R[k] = a * R[k+1] + K[d]    (first edge, inner child)
-  T_HU = 80,     // R[k] = a * R[k+1] + R[k]    (inner child)
-  T_HST = 96,    // d = R[0]
+  T_G = 13,    // d = a * (b or K[b]) + (c or K[c]); flags G_BK, G_CK
 };
-constexpr int kHLevels = 12;   // register accumulators of the Horner stack
-inline bool is_horner(int op) { return op >= T_HFL && op < T_HST; }
-inline int horner_kind(int op) { return op & ~15; }
-inline int horner_level(int op) { return op & 15; }
+enum : uint8_t { G_BK = 1, G_CK = 2 };
+
+// One device instruction (32 bytes).  Almost every instruction is the same
+// fused multiply-add
+//     S[d] = S[a] * (I_BK ? kb : S[b]) + (I_CK ? kc : S[c]),
+// so the interpreter needs no dispatch beyond one test of the special code
+// (division, absolute value, accumulated absolute value).  Slot fields are
+// byte offsets (slot * 8) into the thread's row of the slot file; a field
+// that names an immediate holds 0 (a valid slot).  kbi/kci index the
+// constant pool (hi, lo) so that the double-double evaluation can use the
+// constants' low parts.
 struct Ins {
-  uint8_t op;
-  uint8_t pad;
-  uint16_t d, a, b;
+  uint16_t op;          // flags I_* | special code << 8
+  uint16_t d, a, b, c;  // byte offsets in the slot row
+  uint16_t kbi, kci;    // constant-pool indices of kb, kc
+  uint16_t pad;
+  double kb, kc;
 };
-static_assert(sizeof(Ins) == 8, "Ins must be 8 bytes");
+static_assert(sizeof(Ins) == 32, "Ins must be 32 bytes");
+enum : uint16_t {
+  I_BK = 1, I_CK = 2,
+  I_DIV = 1 << 8,     // S[d] = S[a] / S[b]
+  I_ABS = 2 << 8,     // S[d] = |S[a]|
+  I_ADDABS = 3 << 8,  // S[d] = S[c] + |S[a]|
+};
 
 struct Tape {
   std::vector<Ins> code;
   std::vector<double> khi, klo;  // constant pool
-  int nslots = 0;
+  int nslots = 0;                 // row pitch of the slot file (odd: conflict-free rows)
   int out_I = -1, out_K = -1;     // output slots
   double flops = 0;               // FP64 flops per evaluation (FMA = 2)
   int M = 0;

@@ -520,7 +520,9 @@ static std::vector<Mono> expand_factor(const Factor &f, int chan, const std::vec
 
 // ========================================================== tape builder ==
 struct Builder {
-  struct SIns { uint8_t op; int d, a, b; int c = -1; };   // value ids; b (and c) may be constant indices
+  // value ids; b may be a constant index (T_FMAC, T_MULC, T_CONST, or T_G
+  // with G_BK), c a value id or (T_G with G_CK) a constant index
+  struct SIns { uint8_t op; int d, a, b; int c = -1; uint8_t fl = 0; };
   std::vector<SIns> prog;
   std::vector<double> khi, klo;
   std::map<std::pair<double, double>, int> kidx;
@@ -597,22 +599,17 @@ static int stack_product(Builder &B, ProdStack &ps, const std::vector<int> &v) {
 // multivariate Horner factorisation: at every node the variable that occurs
 // in most of the node's monomials is factored out,
 //     q = x * q_x + q_rest,
-// recursively, so that every edge of the resulting tree costs one FMA into
-// the register accumulator of its depth and no monomial is multiplied out.
-// Returns false (emitting nothing) when the tree is deeper than the register
-// stack.
+// recursively, so that every edge of the resulting tree costs one fused
+// multiply-add and no monomial is multiplied out.  The running sums are
+// ordinary values (SSA); the slot allocator gives each update the slot of the
+// sum it replaces.
 struct HMono { std::vector<int> v; int k; };   // sorted variable multiset, constant index
 
-static int horner_depth(const std::vector<HMono> &ms) {
-  size_t d = 0;
-  for (auto &m : ms) d = std::max(d, m.v.size());
-  return (int)d;
-}
-
-static void horner_node(Builder &B, std::vector<HMono> &ms, int lvl, int coef, int zero_k) {
+// Returns the value id of the node's polynomial  K[coef] + sum over ms.
+static int horner_node(Builder &B, std::vector<HMono> &ms, int coef, int zero_k) {
   // ms: monomials of this node with at least one variable each; coef: the
   // node's own constant index or -1.
-  bool first = true;
+  int acc = -1;
   std::vector<HMono> rest;
   rest.swap(ms);
   while (!rest.empty()) {
@@ -633,23 +630,25 @@ static void horner_node(Builder &B, std::vector<HMono> &ms, int lvl, int coef, i
       else grp.push_back(std::move(m));
     }
     rest.swap(oth);
-    int addend = first ? (coef >= 0 ? coef : zero_k) : -1;
-    if (grp.empty()) {
-      // x * K[leaf] (+ accumulator or node coefficient)
-      B.prog.push_back({(uint8_t)((first ? T_HFL : T_HL) + lvl), -1, best, leaf_k, addend});
-    } else {
-      horner_node(B, grp, lvl + 1, leaf_k, zero_k);
-      B.prog.push_back({(uint8_t)((first ? T_HFU : T_HU) + lvl), -1, best, -1, addend});
-    }
-    B.flops += (first && addend == zero_k) ? 1 : 2;
-    first = false;
+    // multiplicand: the leaf's coefficient, or the child's polynomial
+    int mul = -1;
+    uint8_t fl = 0;
+    if (grp.empty()) { mul = leaf_k; fl |= G_BK; }
+    else mul = horner_node(B, grp, leaf_k, zero_k);
+    // addend: the running sum, else the node's own coefficient (or zero)
+    int add = acc;
+    if (acc < 0) { add = coef >= 0 ? coef : zero_k; fl |= G_CK; }
+    int d = B.newval();
+    B.prog.push_back({T_G, d, best, mul, add, fl});
+    B.flops += (acc < 0 && coef < 0) ? 1 : 2;
+    acc = d;
   }
+  return acc;
 }
 
 // Emits the Horner evaluation of ms into a fresh value; monomials must have
-// distinct variable lists.  Returns -1 if it does not fit the register stack.
+// distinct variable lists.
 static int emit_horner(Builder &B, std::vector<HMono> ms) {
-  if (horner_depth(ms) >= kHLevels) return -1;
   int coef = -1;
   std::vector<HMono> inner;
   for (auto &m : ms) {
@@ -658,10 +657,7 @@ static int emit_horner(Builder &B, std::vector<HMono> ms) {
     else inner.push_back(std::move(m));
   }
   if (inner.empty()) return coef >= 0 ? B.cval(coef) : B.zero();
-  horner_node(B, inner, 0, coef, B.konst(0.0));
-  int d = B.newval();
-  B.prog.push_back({T_HST, d, -1, -1});
-  return d;
+  return horner_node(B, inner, coef, B.konst(0.0));
 }
 
 // polynomial in z evaluated into a fresh accumulator
@@ -1000,148 +996,76 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
   int zK = B.bin(T_MUL, Ktot, 0);
   int outK = B.mulc(zK, B.konst(std::fabs(pref)));
   // ------------------------------------------------ dead code removal --
+  // value operands of an intermediate instruction
+  auto b_is_val = [](const Builder::SIns &in) {
+    return in.op == T_ADD || in.op == T_SUB || in.op == T_MUL || in.op == T_DIV || in.op == T_FMA ||
+           (in.op == T_G && !(in.fl & G_BK));
+  };
+  auto c_is_val = [](const Builder::SIns &in) { return in.op == T_G && !(in.fl & G_CK); };
+  auto accum = [](uint8_t op) { return op == T_FMA || op == T_FMAC || op == T_ADDABS; };
+  const int zk = B.konst(0.0);
   {
-    auto b_val = [](uint8_t op) { return op == T_ADD || op == T_SUB || op == T_MUL || op == T_DIV || op == T_FMA; };
-    auto accum = [](uint8_t op) { return op == T_FMA || op == T_FMAC || op == T_ADDABS; };
     std::vector<char> live(B.nvals, 0);
     live[outI] = live[outK] = 1;
     std::vector<char> keep(B.prog.size(), 0);
-    bool hlive = false;   // the Horner ops before an HST live with it
     for (int i = (int)B.prog.size() - 1; i >= 0; --i) {
       auto &in = B.prog[i];
-      if (is_horner(in.op)) {
-        if (!hlive) continue;
-        keep[i] = 1;
-        live[in.a] = 1;
-        continue;
-      }
-      if (in.op == T_HST) hlive = live[in.d] != 0;
       if (!live[in.d]) continue;
       keep[i] = 1;
       if (in.a >= 0) live[in.a] = 1;
-      if (b_val(in.op) && in.b >= 0) live[in.b] = 1;
+      if (b_is_val(in) && in.b >= 0) live[in.b] = 1;
+      if (c_is_val(in) && in.c >= 0) live[in.c] = 1;
       if (accum(in.op)) live[in.d] = 1;
     }
     std::vector<Builder::SIns> np;
     double fl = 0;
-    const int zk = B.konst(0.0);
     for (size_t i = 0; i < B.prog.size(); ++i)
       if (keep[i]) {
-        np.push_back(B.prog[i]);
-        uint8_t op = B.prog[i].op;
-        if (is_horner(op)) {
-          int kind = horner_kind(op);
-          fl += ((kind == T_HFL || kind == T_HFU) && B.prog[i].c == zk) ? 1 : 2;
-          continue;
-        }
-        fl += (op == T_FMA || op == T_FMAC) ? 2 : (op == T_CONST || op == T_ZERO || op == T_HST) ? 0 : 1;
+        const auto &in = B.prog[i];
+        np.push_back(in);
+        if (in.op == T_G) fl += ((in.fl & G_CK) && in.c == zk) ? 1 : 2;
+        else fl += (in.op == T_FMA || in.op == T_FMAC) ? 2 : (in.op == T_CONST || in.op == T_ZERO) ? 0 : 1;
       }
     B.prog.swap(np);
     B.flops = fl;
   }
-  // ------------------------------------------- register accumulators --
-  // A chain ZERO d; {FMAC|FMA} d ...; (first plain read of d) becomes
-  // RZERO; {RFMAC|RFMA} ...; RST d when no other register chain is open.
-  {
-    std::vector<Builder::SIns> np;
-    np.reserve(B.prog.size() + 16);
-    size_t i = 0;
-    const size_t N = B.prog.size();
-    auto reads_plain = [&](const Builder::SIns &in, int v) {
-      bool b_val = in.op == T_ADD || in.op == T_SUB || in.op == T_MUL || in.op == T_DIV || in.op == T_FMA;
-      return in.a == v || (b_val && in.b == v);
-    };
-    while (i < N) {
-      const auto &z = B.prog[i];
-      if (z.op != T_ZERO) { np.push_back(z); ++i; continue; }
-      int d = z.d;
-      // find the extent: accumulations into d up to the first other use of d
-      size_t last = i;
-      bool other = false;
-      for (size_t k = i + 1; k < N; ++k) {
-        const auto &in = B.prog[k];
-        bool acc_d = (in.op == T_FMAC || in.op == T_FMA) && in.d == d && !(in.op == T_FMA && (in.a == d || in.b == d));
-        if (acc_d) { last = k; continue; }
-        if (reads_plain(in, d) || in.d == d) break;
-        if (in.op == T_ZERO) { other = true; break; }   // another chain would start inside
-      }
-      (void)other;
-      // only worth it when the chain has at least two steps
-      size_t nacc = 0;
-      for (size_t k = i + 1; k <= last; ++k)
-        if ((B.prog[k].op == T_FMAC || B.prog[k].op == T_FMA) && B.prog[k].d == d) ++nacc;
-      bool clean = nacc >= 2;
-      for (size_t k = i + 1; k <= last && clean; ++k) {
-        const auto &in = B.prog[k];
-        if (in.op == T_ZERO || in.op == T_ADDABS) clean = false;
-        if ((in.op == T_FMAC || in.op == T_FMA) && in.d != d) clean = false;
-      }
-      if (!clean) { np.push_back(z); ++i; continue; }
-      np.push_back({T_RZERO, -1, -1, -1});
-      for (size_t k = i + 1; k <= last; ++k) {
-        const auto &in = B.prog[k];
-        if (in.op == T_FMAC && in.d == d) np.push_back({T_RFMAC, -1, in.a, in.b});
-        else if (in.op == T_FMA && in.d == d) np.push_back({T_RFMA, -1, in.a, in.b});
-        else np.push_back(in);
-      }
-      np.push_back({T_RST, d, -1, -1});
-      i = last + 1;
-    }
-    B.prog.swap(np);
-  }
   // ---------------------------------------------------- slot allocation --
   std::vector<int> last(B.nvals, -1);
-  auto bval = [](uint8_t op) {
-    return op == T_ADD || op == T_SUB || op == T_MUL || op == T_DIV || op == T_FMA || op == T_RFMA;
-  };
   for (size_t i = 0; i < B.prog.size(); ++i) {
     auto &in = B.prog[i];
     if (in.a >= 0) last[in.a] = (int)i;
-    if (bval(in.op) && in.b >= 0) last[in.b] = (int)i;
-    if (in.op == T_FMA || in.op == T_FMAC || in.op == T_ADDABS) last[in.d] = (int)i;
+    if (b_is_val(in) && in.b >= 0) last[in.b] = (int)i;
+    if (c_is_val(in) && in.c >= 0) last[in.c] = (int)i;
+    if (accum(in.op)) last[in.d] = (int)i;
   }
   last[outI] = last[outK] = (int)B.prog.size();
   std::vector<int> slot(B.nvals, -1);
   std::vector<int> freelist;
   int nslots = B.M;
   for (int i = 0; i < B.M; ++i) slot[i] = i;   // z slots stay reserved
-  Tape tp;
-  tp.M = B.M;
+  struct Low { const Builder::SIns *in; int sd, sa, sb, sc; };
+  std::vector<Low> low;
+  low.reserve(B.prog.size());
   for (size_t i = 0; i < B.prog.size(); ++i) {
-    auto in = B.prog[i];
-    bool b_is_val = bval(in.op);
+    const auto &in = B.prog[i];
     int sa = in.a >= 0 ? slot[in.a] : 0;
-    int sb = b_is_val ? slot[in.b] : in.b;
-    if (is_horner(in.op)) {
-      if (in.a >= B.M && last[in.a] == (int)i) freelist.push_back(slot[in.a]);
-      Ins ins;
-      ins.op = in.op; ins.pad = 0;
-      ins.d = (uint16_t)(in.c >= 0 ? in.c : 0);
-      ins.a = (uint16_t)sa;
-      ins.b = (uint16_t)(in.b >= 0 ? in.b : 0);
-      tp.code.push_back(ins);
-      continue;
-    }
-    if (in.op == T_RZERO || in.op == T_RFMAC || in.op == T_RFMA) {
-      // register ops: no destination slot; release operands at their last use
-      std::vector<int> rel2;
-      if (in.a >= B.M && last[in.a] == (int)i) rel2.push_back(in.a);
-      if (b_is_val && in.b >= B.M && last[in.b] == (int)i && in.b != in.a) rel2.push_back(in.b);
-      for (int v : rel2) freelist.push_back(slot[v]);
-      Ins ins;
-      ins.op = in.op; ins.pad = 0; ins.d = 0; ins.a = (uint16_t)sa; ins.b = (uint16_t)sb;
-      tp.code.push_back(ins);
-      continue;
-    }
-    // release operands whose last use is here (before allocating d, so d may reuse)
-    bool accum = (in.op == T_FMA || in.op == T_FMAC || in.op == T_ADDABS);
+    int sb = b_is_val(in) ? slot[in.b] : -1;
+    int sc = c_is_val(in) ? slot[in.c] : -1;
+    // release operands whose last use is here (before allocating d, so that
+    // d may take the slot of the value it replaces)
+    bool acc = accum(in.op);
     std::vector<int> rel;
-    if (in.a >= B.M && last[in.a] == (int)i && !(accum && in.a == in.d)) rel.push_back(in.a);
-    if (b_is_val && in.b >= B.M && last[in.b] == (int)i && in.b != in.a && !(accum && in.b == in.d)) rel.push_back(in.b);
+    auto release = [&](int v) {
+      if (v >= B.M && last[v] == (int)i && !(acc && v == in.d) &&
+          std::find(rel.begin(), rel.end(), v) == rel.end()) rel.push_back(v);
+    };
+    if (in.a >= 0) release(in.a);
+    if (b_is_val(in) && in.b >= 0) release(in.b);
+    if (c_is_val(in) && in.c >= 0) release(in.c);
     int sd;
-    if (accum) sd = slot[in.d];
+    if (acc) sd = slot[in.d];
     else {
-      for (int v : rel) { freelist.push_back(slot[v]); }
+      for (int v : rel) freelist.push_back(slot[v]);
       rel.clear();
       if (!freelist.empty()) { sd = freelist.back(); freelist.pop_back(); }
       else sd = nslots++;
@@ -1149,16 +1073,49 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
       if (last[in.d] <= (int)i) freelist.push_back(sd);   // never read
     }
     for (int v : rel) freelist.push_back(slot[v]);
-    if (accum && last[in.d] == (int)i && in.d != outI && in.d != outK) freelist.push_back(sd);
-    if (nslots > 65000) throw std::runtime_error("tape needs too many slots");
-    Ins ins;
-    ins.op = in.op; ins.pad = 0;
-    ins.d = (uint16_t)sd; ins.a = (uint16_t)sa; ins.b = (uint16_t)sb;
-    tp.code.push_back(ins);
+    if (acc && last[in.d] == (int)i && in.d != outI && in.d != outK) freelist.push_back(sd);
+    low.push_back({&in, sd, sa, sb, sc});
   }
+  if (nslots > 8191) throw std::runtime_error("tape needs more than 8191 slots");
+  // ------------------------------------------- lowering to instructions --
+  // every arithmetic operation becomes  d = a * (b | kb) + (c | kc)
+  const int k_one = B.konst(1.0), k_mone = B.konst(-1.0);
   if (B.khi.size() > 65535) throw std::runtime_error("constant pool exceeds 16-bit indices");
+  Tape tp;
+  tp.M = B.M;
+  for (const Low &l : low) {
+    const auto &in = *l.in;
+    Ins o{};
+    auto setb = [&](int k) { o.op |= I_BK; o.kbi = (uint16_t)k; o.kb = B.khi[k]; };
+    auto setc = [&](int k) { o.op |= I_CK; o.kci = (uint16_t)k; o.kc = B.khi[k]; };
+    int a = l.sa, bb = 0, cc = 0;
+    switch (in.op) {
+      case T_ADD: bb = 0; setb(k_one); cc = l.sb; break;                 // a * 1 + b
+      case T_SUB: a = l.sb; setb(k_mone); cc = l.sa; break;              // b * -1 + a
+      case T_MUL: bb = l.sb; setc(zk); break;                            // a * b + 0
+      case T_DIV: bb = l.sb; o.op = I_DIV; break;
+      case T_FMA: bb = l.sb; cc = l.sd; break;                           // a * b + d
+      case T_FMAC: setb(in.b); cc = l.sd; break;                         // a * K + d
+      case T_MULC: setb(in.b); setc(zk); break;                          // a * K + 0
+      case T_CONST: a = 0; setb(zk); setc(in.b); break;                  // z0 * 0 + K
+      case T_ABS: o.op = I_ABS; break;
+      case T_NEG: setb(k_mone); setc(zk); break;                         // a * -1 + 0
+      case T_ZERO: a = 0; setb(zk); setc(zk); break;                     // z0 * 0 + 0
+      case T_ADDABS: o.op = I_ADDABS; cc = l.sd; break;                  // d + |a|
+      case T_G:
+        if (in.fl & G_BK) setb(in.b); else bb = l.sb;
+        if (in.fl & G_CK) setc(in.c); else cc = l.sc;
+        break;
+      default: throw std::runtime_error("unknown intermediate operation");
+    }
+    o.d = (uint16_t)(l.sd * 8);
+    o.a = (uint16_t)(a * 8);
+    o.b = (uint16_t)(bb * 8);
+    o.c = (uint16_t)(cc * 8);
+    tp.code.push_back(o);
+  }
   tp.khi = B.khi; tp.klo = B.klo;
-  tp.nslots = nslots;
+  tp.nslots = nslots | 1;   // odd row pitch: the rows of a warp fall in distinct banks
   tp.out_I = slot[outI]; tp.out_K = slot[outK];
   tp.flops = B.flops;
   tp.n_terms = (int)terms.size();
@@ -1167,44 +1124,24 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
 }
 
 // Host replay of a tape: used only by the test suite to check the compiler
-// against the oracle without a GPU.
+// against the oracle without a GPU.  Same operations as the device
+// interpreter.
 void tape_replay(const Tape &t, const double *z, double *I, double *K) {
   std::vector<double> s(t.nslots, 0.0);
-  double r = 0.0;
-  double R[kHLevels + 1] = {0};
   for (int i = 0; i < t.M; ++i) s[i] = z[i];
   for (const Ins &in : t.code) {
-    if (is_horner(in.op)) {
-      int k = horner_level(in.op);
-      switch (horner_kind(in.op)) {
-        case T_HFL: R[k] = std::fma(s[in.a], t.khi[in.b], t.khi[in.d]); break;
-        case T_HL: R[k] = std::fma(s[in.a], t.khi[in.b], R[k]); break;
-        case T_HFU: R[k] = std::fma(s[in.a], R[k + 1], t.khi[in.d]); break;
-        case T_HU: R[k] = std::fma(s[in.a], R[k + 1], R[k]); break;
-      }
-      continue;
-    }
-    if (in.op == T_HST) { s[in.d] = R[0]; continue; }
-    double &d = s[in.d];
-    switch (in.op) {
-      case T_ADD: d = s[in.a] + s[in.b]; break;
-      case T_SUB: d = s[in.a] - s[in.b]; break;
-      case T_MUL: d = s[in.a] * s[in.b]; break;
-      case T_DIV: d = s[in.a] / s[in.b]; break;
-      case T_FMA: d = std::fma(s[in.a], s[in.b], d); break;
-      case T_FMAC: d = std::fma(t.khi[in.b], s[in.a], d); break;
-      case T_MULC: d = t.khi[in.b] * s[in.a]; break;
-      case T_CONST: d = t.khi[in.b]; break;
-      case T_ABS: d = std::fabs(s[in.a]); break;
-      case T_NEG: d = -s[in.a]; break;
-      case T_ZERO: d = 0.0; break;
-      case T_ADDABS: d = d + std::fabs(s[in.a]); break;
-      case T_RZERO: r = 0.0; break;
-      case T_RFMAC: r = std::fma(t.khi[in.b], s[in.a], r); break;
-      case T_RFMA: r = std::fma(s[in.a], s[in.b], r); break;
-      case T_RST: d = r; break;
+    const double a = s[in.a / 8];
+    const double b = (in.op & I_BK) ? in.kb : s[in.b / 8];
+    const double c = (in.op & I_CK) ? in.kc : s[in.c / 8];
+    double r;
+    switch (in.op >> 8) {   // special code
+      case 0: r = std::fma(a, b, c); break;
+      case I_DIV >> 8: r = a / b; break;
+      case I_ABS >> 8: r = std::fabs(a); break;
+      case I_ADDABS >> 8: r = c + std::fabs(a); break;
       default: throw std::runtime_error("bad opcode");
     }
+    s[in.d / 8] = r;
   }
   *I = s[t.out_I];
   *K = s[t.out_K];

@@ -16,7 +16,7 @@ struct GraphDev {
   const double *deg;      // 3 * 2^M
   const double *phi;      // 3 * 2^M
   const double *wt;       // 3 * 2^M: phi/deg (same IEEE quotient as the walk's definition)
-  const uint2 *code;      // tape
+  const Ins *code;       // tape (32-byte instructions)
   const double *khi, *klo;
   int M, ntape, nslots, outI, outK;
   int graph_id;
@@ -28,7 +28,9 @@ struct GraphDev {
   const double *lP2 = nullptr;   // log2 P(j | T)
   const double *lD = nullptr;    // Deg_theta(T)
   const double *lD2 = nullptr;   // log2 Deg_theta(T)
+  const double *lDi = nullptr;   // 1 / Deg_theta(T)
   double beta = 0.1;             // weight of the plain density in the mixture
+  double l2beta = 0, l2nbeta = 0;   // log2 beta, log2 (1 - beta)
 };
 
 struct Partial {
@@ -139,7 +141,12 @@ __device__ __forceinline__ double weight(double I, double lg) {
 
 // Defensive mixture q = (1-beta) q_theta + beta g.  u[0] < beta selects the
 // plain density (its component pick rescaled to u[0]/beta), otherwise the
-// learned walk; the returned log2 density is that of the mixture.
+// learned walk; the returned log2 density is that of the mixture,
+//   log2 q = log2( (1-beta) 2^{log2 q_theta} + sum_k beta C_k 2^{log2 g_k} ),
+// one log-sum-exp over five terms.  This path is checked statistically
+// (normalisation, unbiasedness), not operation by operation against the
+// host, so it uses the device's own exp2/log2 and reciprocal tables of the
+// exponents instead of the series and quotients of draw_sample.
 static __device__ void draw_mix(const GraphDev &G, uint64_t idx, uint64_t seed, double *z, double *lz, double &log2q) {
   const int M = G.M;
   double u[2 * 14 + 2];
@@ -179,11 +186,11 @@ static __device__ void draw_mix(const GraphDev &G, uint64_t idx, uint64_t seed, 
         if (chosen < 0) chosen = last;
         lz[chosen] = cur;
         T ^= 1u << chosen;
-        cur += dlog2(u[2 + 2 * l]) / __ldg(deg + T);
+        cur += log2(u[2 + 2 * l]) / __ldg(deg + T);
       }
       lz[__ffs(T) - 1] = cur;
     } else {
-      for (int i = 0; i < M; ++i) lz[i] = dlog2(-dlog2(u[1 + i]));
+      for (int i = 0; i < M; ++i) lz[i] = log2(-log2(u[1 + i]));
     }
   } else {
     uint32_t T = full;
@@ -201,16 +208,16 @@ static __device__ void draw_mix(const GraphDev &G, uint64_t idx, uint64_t seed, 
       if (chosen < 0) chosen = last;
       lz[chosen] = cur;
       T ^= 1u << chosen;
-      cur += dlog2(u[2 + 2 * l]) / __ldg(G.lD + T);
+      cur += log2(u[2 + 2 * l]) * __ldg(G.lDi + T);
     }
     lz[__ffs(T) - 1] = cur;
   }
   // normalise: z = 2^lz / sum, log2 z = lz - log2 sum
   double ssum = 0.0;
-  for (int i = 0; i < M; ++i) { z[i] = dexp2(lz[i]); ssum += z[i]; }
-  double ls = dlog2(ssum);
-  for (int i = 0; i < M; ++i) { z[i] = z[i] / ssum; lz[i] = lz[i] - ls; }
-  // densities at z
+  for (int i = 0; i < M; ++i) { z[i] = exp2(lz[i]); ssum += z[i]; }
+  const double ls = log2(ssum), rs = 1.0 / ssum;
+  for (int i = 0; i < M; ++i) { z[i] = z[i] * rs; lz[i] = lz[i] - ls; }
+  // sector order at z (descending log2 z, ties by lower index)
   int ord[14];
   for (int i = 0; i < M; ++i) {
     int p = i;
@@ -219,7 +226,8 @@ static __device__ void draw_mix(const GraphDev &G, uint64_t idx, uint64_t seed, 
   }
   double sumlz = 0.0;
   for (int i = 0; i < M; ++i) sumlz += lz[i];
-  double t[4];
+  // five log2 terms: beta C_k g_k (k = g1, g2, g3, g4) and (1 - beta) q_theta
+  double t[5];
   for (int k = 0; k < 3; ++k) {
     const double *deg = G.deg + ((size_t)k << M);
     double acc = 0.0;
@@ -232,18 +240,12 @@ static __device__ void draw_mix(const GraphDev &G, uint64_t idx, uint64_t seed, 
       T ^= 1u << ord[l];
     }
     int slot = k == 0 ? 0 : k + 1;
-    t[slot] = G.log2C[slot] - G.log2phi_full[k] + acc - sumlz;
+    t[slot] = G.log2C[slot] - G.log2phi_full[k] + acc - sumlz + G.l2beta;
   }
-  t[1] = G.log2C[1] + G.log2_fact;
-  double m = fmax(fmax(t[0], t[1]), fmax(t[2], t[3]));
-  double rel = 0.0;
-  for (int k = 0; k < 4; ++k) rel += dexp2(t[k] - m);
-  double lg = m + dlog2(rel);
-  // learned density along the same order
-  double lq = 0.0;
+  t[1] = G.log2C[1] + G.log2_fact + G.l2beta;
   {
     uint32_t T = full;
-    double prev = 0.0;
+    double lq = 0.0, prev = 0.0;
     for (int l = 0; l < M - 1; ++l) {
       int j = ord[l];
       lq += __ldg(G.lP2 + (size_t)T * 16 + j);
@@ -253,11 +255,12 @@ static __device__ void draw_mix(const GraphDev &G, uint64_t idx, uint64_t seed, 
       lq += __ldg(G.lD2 + T) + __ldg(G.lD + T) * (cv - pv);
       prev = cv;
     }
-    lq -= sumlz;
+    t[4] = lq - sumlz + G.l2nbeta;
   }
-  double a = dlog2(1.0 - G.beta) + lq, b = dlog2(G.beta) + lg;
-  double mm = fmax(a, b);
-  log2q = mm + dlog2(dexp2(a - mm) + dexp2(b - mm));
+  double m = fmax(fmax(fmax(t[0], t[1]), fmax(t[2], t[3])), t[4]);
+  double rel = 0.0;
+  for (int k = 0; k < 5; ++k) rel += exp2(t[k] - m);
+  log2q = m + log2(rel);
 }
 
 __device__ __forceinline__ void draw_any(const GraphDev &G, uint64_t idx, uint64_t seed, double *z, double *lz,
@@ -266,110 +269,164 @@ __device__ __forceinline__ void draw_any(const GraphDev &G, uint64_t idx, uint64
   else draw_sample(G, idx, seed, z, lz, lg);
 }
 
-// Horner-stack cases of the interpreters: level k accumulates into R##k and
-// reads its child level from R##k1.
-#define AE_HCASES(k, k1)                                                             \
-  case T_HFL + k: R##k = __fma_rn(S[a * stride], __ldg(K + b), __ldg(K + d)); break; \
-  case T_HL + k: R##k = __fma_rn(S[a * stride], __ldg(K + b), R##k); break;          \
-  case T_HFU + k: R##k = __fma_rn(S[a * stride], R##k1, __ldg(K + d)); break;        \
-  case T_HU + k: R##k = __fma_rn(S[a * stride], R##k1, R##k); break;
-#define AE_HCASES_ALL                                                                \
-  AE_HCASES(0, 1) AE_HCASES(1, 2) AE_HCASES(2, 3) AE_HCASES(3, 4) AE_HCASES(4, 5)     \
-  AE_HCASES(5, 6) AE_HCASES(6, 7) AE_HCASES(7, 8) AE_HCASES(8, 9) AE_HCASES(9, 10)    \
-  AE_HCASES(10, 11)
-static_assert(kHLevels == 12, "interpreter cases cover Horner levels 0..10 (degree <= 11)");
+// x if flag != 0, else y
+__device__ __forceinline__ double sel64(uint32_t flag, double x, double y) {
+  double r;
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\tselp.f64 %0, %1, %2, q;\n\t}"
+      : "=d"(r) : "d"(x), "d"(y), "r"(flag));
+  return r;
+}
 
-// FP64 tape interpreter.  S points at this thread's column of the slot file
-// (stride = blockDim.x); r is the register accumulator of monomial chains and
-// R0..R11 the Horner stack.  The next instruction word is fetched while the
-// current one executes.
-__device__ __forceinline__ void run_tape(const GraphDev &G, double *S, int stride) {
-  const uint2 *code = G.code;
-  const double *K = G.khi;
+// The rare instructions (division, |a|, c + |a|), kept out of the loop body.
+static __device__ __noinline__ double special_op(uint32_t sp, double va, double vb, double vc) {
+  if (sp == I_DIV) return __ddiv_rn(va, vb);
+  if (sp == I_ABS) return fabs(va);
+  return __dadd_rn(vc, fabs(va));   // I_ADDABS
+}
+
+// One tape instruction on this thread's slot row Sb:
+//   S[d] = S[a] * (kb | S[b]) + (kc | S[c])   or a special operation.
+__device__ __forceinline__ void tape_step(const uint4 &w0, const uint4 &w1, char *Sb) {
+  const uint32_t op = w0.x & 0xffffu, d = w0.x >> 16, a = w0.y & 0xffffu, b = w0.y >> 16, c = w0.z & 0xffffu;
+  const double va = *reinterpret_cast<const double *>(Sb + a);
+  const double vb = sel64(op & I_BK, __hiloint2double((int)w1.y, (int)w1.x), *reinterpret_cast<const double *>(Sb + b));
+  const double vc = sel64(op & I_CK, __hiloint2double((int)w1.w, (int)w1.z), *reinterpret_cast<const double *>(Sb + c));
+  const uint32_t sp = op & 0xff00u;
+  *reinterpret_cast<double *>(Sb + d) = sp == 0 ? __fma_rn(va, vb, vc) : special_op(sp, va, vb, vc);
+}
+
+// FP64 tape interpreter reading instructions from global memory (next one
+// prefetched).  Used by the kernels whose threads do not run the tape in step
+// (parity dumps, training samples); the integration kernels stream the tape
+// through shared memory instead (run_tape_staged).
+__device__ __forceinline__ void run_tape(const GraphDev &G, double *S) {
+  char *Sb = reinterpret_cast<char *>(S);
+  const uint4 *code = reinterpret_cast<const uint4 *>(G.code);
   const int n = G.ntape;
-  double r = 0.0;
-  double R0 = 0, R1 = 0, R2 = 0, R3 = 0, R4 = 0, R5 = 0, R6 = 0, R7 = 0, R8 = 0, R9 = 0, R10 = 0, R11 = 0;
-  uint2 w = __ldg(code);
+  uint4 w0 = __ldg(code), w1 = __ldg(code + 1);
+#pragma unroll 1
   for (int pc = 0; pc < n; ++pc) {
-    uint2 wn = __ldg(code + min(pc + 1, n - 1));
-    int op = w.x & 0xff;
-    int d = w.x >> 16;
-    int a = w.y & 0xffff;
-    int b = w.y >> 16;
-    double *D = S + d * stride;
-    switch (op) {
-      case T_RFMAC: r = __fma_rn(__ldg(K + b), S[a * stride], r); break;
-      case T_MUL: *D = __dmul_rn(S[a * stride], S[b * stride]); break;
-      case T_RFMA: r = __fma_rn(S[a * stride], S[b * stride], r); break;
-      case T_RZERO: r = 0.0; break;
-      case T_RST: *D = r; break;
-      case T_ADD: *D = __dadd_rn(S[a * stride], S[b * stride]); break;
-      case T_SUB: *D = __dadd_rn(S[a * stride], -S[b * stride]); break;
-      case T_DIV: *D = __ddiv_rn(S[a * stride], S[b * stride]); break;
-      case T_FMA: *D = __fma_rn(S[a * stride], S[b * stride], *D); break;
-      case T_FMAC: *D = __fma_rn(__ldg(K + b), S[a * stride], *D); break;
-      case T_MULC: *D = __dmul_rn(__ldg(K + b), S[a * stride]); break;
-      case T_CONST: *D = __ldg(K + b); break;
-      case T_ABS: *D = fabs(S[a * stride]); break;
-      case T_NEG: *D = -S[a * stride]; break;
-      case T_ZERO: *D = 0.0; break;
-      case T_ADDABS: *D = __dadd_rn(*D, fabs(S[a * stride])); break;
-      AE_HCASES_ALL
-      case T_HST: *D = R0; break;
-      default: break;
-    }
-    w = wn;
+    const int nx = 2 * min(pc + 1, n - 1);
+    const uint4 n0 = __ldg(code + nx), n1 = __ldg(code + nx + 1);
+    tape_step(w0, w1, Sb);
+    w0 = n0; w1 = n1;
   }
 }
 
-// Double-double twin of run_tape (slot file holds hi/lo pairs).
-static __device__ void run_tape_dd(const GraphDev &G, dd *S, int stride) {
-  dd r = {0.0, 0.0};
-  dd R[kHLevels];
-#pragma unroll
-  for (int k = 0; k < kHLevels; ++k) R[k] = {0.0, 0.0};
+// ------------------------------------------------ tape staging (TMA) ----
+// The integration kernels run the tape CTA-synchronously: every thread of a
+// CTA evaluates its own sample, all of them step through the same tape
+// segment by segment, and the segments are copied global -> shared memory by
+// the bulk-copy engine (cp.async.bulk, completion on an mbarrier), two
+// buffers deep, so that instruction fetch is a shared-memory broadcast
+// instead of a per-warp L1/L2 round trip.
+constexpr int kSeg = 128;                               // instructions per segment
+constexpr int kSegBytes = kSeg * (int)sizeof(Ins);      // 4 KB
+constexpr int kStageBytes = 2 * kSegBytes;              // both buffers
+constexpr long long kWaitCycles = 4000000000ll;         // bound of one wait (~2 s)
+
+struct Stage {
+  Ins *buf;             // 2 x kSeg instructions, shared memory
+  uint64_t *bar;        // 2 mbarriers, shared memory
+  uint32_t issued;      // segments issued (thread 0's view)
+  uint32_t used;        // segments consumed (identical in every thread)
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// thread 0; the caller synchronises the CTA afterwards
+__device__ __forceinline__ void stage_init(Stage &st) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(st.bar)) : "memory");
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(st.bar + 1)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// thread 0: copy segment seg of G's tape into the next buffer.  The buffer's
+// previous contents must have been consumed by every thread (the caller
+// issues after a CTA barrier).
+__device__ __forceinline__ void stage_issue(Stage &st, const GraphDev &G, int seg) {
+  const int k = st.issued & 1;
+  const int cnt = min(kSeg, G.ntape - seg * kSeg);
+  const uint32_t bytes = (uint32_t)cnt * (uint32_t)sizeof(Ins);
+  const uint32_t bar = smem_addr(st.bar + k), dst = smem_addr(st.buf + k * kSeg);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(dst), "l"(G.code + (size_t)seg * kSeg), "r"(bytes), "r"(bar) : "memory");
+  ++st.issued;
+}
+
+// every thread: wait until the next segment to consume has landed; false if
+// the bounded wait ran out
+__device__ __forceinline__ bool stage_wait(const Stage &st) {
+  const uint32_t bar = smem_addr(st.bar + (st.used & 1)), parity = (st.used >> 1) & 1;
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+
+// All threads of the CTA together: run G's tape on this thread's row (only
+// if active).  Segment 0 must have been issued; if `again` the tape is
+// rerun next (the next round of samples), and its segment 0 is issued while
+// the last segment executes.  Returns false (in every thread) if a wait ran
+// out; *err is set and the caller must leave the kernel.
+static __device__ bool run_tape_staged(Stage &st, const GraphDev &G, double *S, bool active, bool again, int *err) {
+  char *Sb = reinterpret_cast<char *>(S);
+  const int nseg = (G.ntape + kSeg - 1) / kSeg;
+  for (int s = 0; s < nseg; ++s) {
+    const bool ok = stage_wait(st);
+    // after this barrier every thread has finished segment s-1: its buffer
+    // may be refilled
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(err, 1);
+      return false;
+    }
+    if (threadIdx.x == 0) {
+      if (s + 1 < nseg) stage_issue(st, G, s + 1);
+      else if (again) stage_issue(st, G, 0);
+    }
+    const uint4 *code = reinterpret_cast<const uint4 *>(st.buf + (st.used & 1) * kSeg);
+    const int cnt = min(kSeg, G.ntape - s * kSeg);
+    ++st.used;
+    if (!active) continue;
+    uint4 w0 = code[0], w1 = code[1];
+#pragma unroll 1
+    for (int k = 0; k < cnt; ++k) {
+      const int nx = 2 * min(k + 1, cnt - 1);
+      const uint4 n0 = code[nx], n1 = code[nx + 1];
+      tape_step(w0, w1, Sb);
+      w0 = n0; w1 = n1;
+    }
+  }
+  return true;
+}
+
+// Double-double twin of run_tape (rows of hi/lo pairs; offsets scaled by 2;
+// constants with their low parts from the pool).  Every result is stored at
+// once, so forwarded operands are read from their slots and I_NOST is
+// ignored.
+static __device__ void run_tape_dd(const GraphDev &G, dd *S) {
+  char *Sb = reinterpret_cast<char *>(S);
+  const uint4 *code = reinterpret_cast<const uint4 *>(G.code);
   for (int pc = 0; pc < G.ntape; ++pc) {
-    uint2 w = __ldg(G.code + pc);
-    int op = w.x & 0xff, d = w.x >> 16, a = w.y & 0xffff, b = w.y >> 16;
-    if (op >= T_HFL && op < T_HST) {
-      // Horner stack: unrolled over the levels so that R stays in registers
-      const int kind = op & ~15, lvl = op & 15;
-      dd x = S[a * stride];
-      dd kb = {0, 0}, kd = {0, 0};
-      if (kind == T_HFL || kind == T_HL) kb = {__ldg(G.khi + b), __ldg(G.klo + b)};
-      if (kind == T_HFL || kind == T_HFU) kd = {__ldg(G.khi + d), __ldg(G.klo + d)};
-#pragma unroll
-      for (int k = 0; k < kHLevels - 1; ++k) {
-        if (k != lvl) continue;
-        dd m = (kind == T_HFL || kind == T_HL) ? kb : R[k + 1];
-        dd acc = (kind == T_HFL || kind == T_HFU) ? kd : R[k];
-        R[k] = dd_fma_fast(acc, m, x);
-      }
-      continue;
-    }
-    dd *D = S + d * stride;
-    dd kb = {0, 0};
-    if (op == T_FMAC || op == T_MULC || op == T_CONST || op == T_RFMAC) kb = {__ldg(G.khi + b), __ldg(G.klo + b)};
-    switch (op) {
-      case T_RZERO: r = {0.0, 0.0}; break;
-      case T_RFMAC: r = dd_fma_fast(r, kb, S[a * stride]); break;
-      case T_RFMA: r = dd_fma_fast(r, S[a * stride], S[b * stride]); break;
-      case T_RST: *D = r; break;
-      case T_ADD: *D = dd_add_fast(S[a * stride], S[b * stride]); break;
-      case T_SUB: { dd t = S[b * stride]; *D = dd_add_fast(S[a * stride], {-t.hi, -t.lo}); } break;
-      case T_MUL: *D = dd_mul_fast(S[a * stride], S[b * stride]); break;
-      case T_DIV: *D = dd_div(S[a * stride], S[b * stride]); break;
-      case T_FMA: *D = dd_fma_fast(*D, S[a * stride], S[b * stride]); break;
-      case T_FMAC: *D = dd_fma_fast(*D, kb, S[a * stride]); break;
-      case T_MULC: *D = dd_mul_fast(kb, S[a * stride]); break;
-      case T_CONST: *D = kb; break;
-      case T_ABS: *D = dd_abs(S[a * stride]); break;
-      case T_NEG: { dd t = S[a * stride]; *D = {-t.hi, -t.lo}; } break;
-      case T_ZERO: *D = {0.0, 0.0}; break;
-      case T_ADDABS: *D = dd_add_fast(*D, dd_abs(S[a * stride])); break;
-      case T_HST: *D = R[0]; break;
-      default: break;
-    }
+    const uint4 w0 = __ldg(code + 2 * pc);
+    const uint32_t op = w0.x & 0xffffu, d = (w0.x >> 16) * 2, a = (w0.y & 0xffffu) * 2, b = (w0.y >> 16) * 2,
+                   c = (w0.z & 0xffffu) * 2, kbi = w0.z >> 16, kci = w0.w & 0xffffu;
+    const dd va = *reinterpret_cast<const dd *>(Sb + a);
+    const dd vb = (op & I_BK) ? dd{__ldg(G.khi + kbi), __ldg(G.klo + kbi)} : *reinterpret_cast<const dd *>(Sb + b);
+    const dd vc = (op & I_CK) ? dd{__ldg(G.khi + kci), __ldg(G.klo + kci)} : *reinterpret_cast<const dd *>(Sb + c);
+    dd r;
+    const uint32_t sp = op & 0xff00u;
+    if (sp == 0) r = dd_fma_fast(vc, vb, va);
+    else if (sp == I_DIV) r = dd_div(va, vb);
+    else if (sp == I_ABS) r = dd_abs(va);
+    else r = dd_add_fast(vc, dd_abs(va));   // I_ADDABS
+    *reinterpret_cast<dd *>(Sb + d) = r;
   }
 }
 

@@ -166,9 +166,10 @@ __global__ void mlp_fwd_kernel(int M, const __nv_bfloat16 *Wbf, const float *P, 
 
 // Tables of the learned walk for every state T.
 //   lp[T*16+j]  = P(j | T) (0 for j not in T), lp2 = log2 of it;
-//   ld[T] = Deg_theta(T), ld2 = log2 Deg_theta(T) (proper nonempty T).
+//   ld[T] = Deg_theta(T), ld2 = log2 Deg_theta(T), ldi = 1 / Deg_theta(T)
+//   (proper nonempty T).
 __global__ void tables_kernel(int M, const float *O, const double *deg, const double *wplain, double *lp,
-                              double *lp2, double *ld, double *ld2) {
+                              double *lp2, double *ld, double *ld2, double *ldi) {
   uint32_t S = 1u << M, full = S - 1;
   for (uint32_t T = blockIdx.x * blockDim.x + threadIdx.x; T < S; T += gridDim.x * blockDim.x) {
     const float *o = O + (size_t)T * OUT;
@@ -196,9 +197,11 @@ __global__ void tables_kernel(int M, const float *O, const double *deg, const do
       double dth = deg[T] * exp(KAP * tanh((double)o[15] / KAP));
       ld[T] = dth;
       ld2[T] = log2(dth);
+      ldi[T] = 1.0 / dth;
     } else {
       ld[T] = 1.0;
       ld2[T] = 0.0;
+      ldi[T] = 1.0;
     }
   }
 }
@@ -208,16 +211,15 @@ __global__ void tables_kernel(int M, const float *O, const double *deg, const do
 __global__ void train_gen_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t seed, uint8_t *order,
                                  float *lt, double *w) {
   extern __shared__ double slots[];
-  double *Sl = slots + threadIdx.x;
-  const int stride = blockDim.x;
+  double *Sl = slots + threadIdx.x * G.nslots;   // this thread's row of the slot file
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < count; base += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t i = base + threadIdx.x;
     if (i >= count) continue;
     double z[14], lz[14], lg;
     draw_sample(G, first + i, seed, z, lz, lg);
-    for (int k = 0; k < G.M; ++k) Sl[k * stride] = z[k];
-    run_tape(G, Sl, stride);
-    double y = weight(Sl[G.outI * stride], lg);
+    for (int k = 0; k < G.M; ++k) Sl[k] = z[k];
+    run_tape(G, Sl);
+    double y = weight(Sl[G.outI], lg);
     w[i] = isfinite(y) ? fabs(y) : 0.0;
     int ord[14];
     for (int a = 0; a < G.M; ++a) {
@@ -445,7 +447,7 @@ __global__ void to_bf16_kernel(const float *src, __nv_bfloat16 *dst, int n) {
 struct Net {
   __nv_bfloat16 *Wbf, *H1, *H2, *H3;
   float *P, *master, *m, *v, *grad, *O, *dO, *part;
-  double *lp, *lp2, *ld, *ld2, *deg, *wplain, *wsum_part, *loss_part;
+  double *lp, *lp2, *ld, *ld2, *ldi, *deg, *wplain, *wsum_part, *loss_part;
   unsigned long long *acc;
   int M;
   int ntiles;
@@ -456,7 +458,7 @@ size_t net_bytes(int M) {
   size_t nt = (S + 63) / 64;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   return al(NPARAM * 2) + 3 * al(S * HID * 2) + al(NPARAM * 4) * 5 + al(S * OUT * 4) * 2 + al(nt * NPARAM * 4) +
-         al(S * 16 * 8) * 2 + al(S * 8) * 4 + al(1024 * 8) * 2 + al(S * 16 * 8);
+         al(S * 16 * 8) * 2 + al(S * 8) * 5 + al(1024 * 8) * 2 + al(S * 16 * 8);
 }
 
 void carve(Net &n, void *mem, int M) {
@@ -482,6 +484,7 @@ void carve(Net &n, void *mem, int M) {
   n.lp2 = (double *)take(S * 16 * 8);
   n.ld = (double *)take(S * 8);
   n.ld2 = (double *)take(S * 8);
+  n.ldi = (double *)take(S * 8);
   n.deg = (double *)take(S * 8);
   n.wplain = (double *)take(S * 8);
   n.wsum_part = (double *)take(1024 * 8);
@@ -493,7 +496,8 @@ void carve(Net &n, void *mem, int M) {
 cudaError_t net_forward(Net &n, cudaStream_t st) {
   size_t S = (size_t)1 << n.M;
   mlp_fwd_kernel<<<n.ntiles, 128, 0, st>>>(n.M, n.Wbf, n.P, n.H1, n.H2, n.H3, n.O);
-  tables_kernel<<<(unsigned)((S + 127) / 128), 128, 0, st>>>(n.M, n.O, n.deg, n.wplain, n.lp, n.lp2, n.ld, n.ld2);
+  tables_kernel<<<(unsigned)((S + 127) / 128), 128, 0, st>>>(n.M, n.O, n.deg, n.wplain, n.lp, n.lp2, n.ld, n.ld2,
+                                                             n.ldi);
   return cudaGetLastError();
 }
 
@@ -547,6 +551,7 @@ static void attach_tables(LoadedGraph &lg, Net &n) {
   lg.dev.lP2 = n.lp2;
   lg.dev.lD = n.ld;
   lg.dev.lD2 = n.ld2;
+  lg.dev.lDi = n.ldi;
 }
 
 extern "C" int ae_train_proposal(ae_ctx *c, int gid, uint64_t n_train, uint64_t seed, int steps, double lr,
@@ -626,6 +631,8 @@ extern "C" int ae_train_proposal(ae_ctx *c, int gid, uint64_t n_train, uint64_t 
   cudaMemcpy(lg.learned.master.data(), n.master, NPARAM * 4, cudaMemcpyDeviceToHost);
   attach_tables(lg, n);
   lg.dev.beta = beta;
+  lg.dev.l2beta = std::log2(beta);
+  lg.dev.l2nbeta = beta < 1 ? std::log2(1.0 - beta) : -1e300;
   lg.learned.beta = beta;
   lg.learned.active = true;
   if (rep) {
@@ -650,6 +657,8 @@ extern "C" int ae_set_proposal(ae_ctx *c, int gid, int mode, double beta) {
   carve(n, lg.learned.mem, lg.g.M());
   attach_tables(lg, n);
   lg.dev.beta = beta;
+  lg.dev.l2beta = std::log2(beta);
+  lg.dev.l2nbeta = beta < 1 ? std::log2(1.0 - beta) : -1e300;
   lg.learned.beta = beta;
   lg.learned.active = true;
   return AE_OK;

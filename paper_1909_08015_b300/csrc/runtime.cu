@@ -44,25 +44,36 @@ static int fail(ae_ctx *c, int code, const std::string &msg) { return ae_fail(c,
   } while (0)
 
 // Process samples [first, first + count) of one graph; CTA b takes a
-// contiguous chunk, thread t its strided share.
-__global__ void integrate_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t seed,
+// contiguous chunk in rounds of blockDim.x samples (one per thread), each
+// round's tapes run together, staged through shared memory.
+__global__ void integrate_kernel(GraphDev Gp, uint64_t first, uint64_t count, uint64_t seed,
                                  double dd_ratio, Partial *part, unsigned long long *queue,
-                                 unsigned long long qcap, unsigned long long *qcount) {
-  extern __shared__ double slots[];
-  double *S = slots + threadIdx.x;
-  const int stride = blockDim.x;
+                                 unsigned long long qcap, unsigned long long *qcount, int *err) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ GraphDev G;
+  __shared__ uint64_t bars[2];
+  Stage st{reinterpret_cast<Ins *>(dsm), bars, 0, 0};
+  if (threadIdx.x == 0) { G = Gp; stage_init(st); }
+  __syncthreads();
+  double *S = reinterpret_cast<double *>(dsm + kStageBytes) + threadIdx.x * G.nslots;   // this thread's row
   uint64_t chunk = (count + gridDim.x - 1) / gridDim.x;
   uint64_t lo = (uint64_t)blockIdx.x * chunk;
   uint64_t hi = min(count, lo + chunk);
   Partial p = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   double z[14], lz[14];
-  for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    uint64_t idx = first + i;
-    double lg;
-    draw_any(G, idx, seed, z, lz, lg);
-    for (int k = 0; k < G.M; ++k) S[k * stride] = z[k];
-    run_tape(G, S, stride);
-    double I = S[G.outI * stride], Kv = S[G.outK * stride];
+  if (threadIdx.x == 0 && lo < hi) stage_issue(st, G, 0);
+  for (uint64_t base = lo; base < hi; base += blockDim.x) {
+    const uint64_t i = base + threadIdx.x;
+    const bool active = i < hi;
+    const uint64_t idx = first + i;
+    double lg = 0.0;
+    if (active) {
+      draw_any(G, idx, seed, z, lz, lg);
+      for (int k = 0; k < G.M; ++k) S[k] = z[k];
+    }
+    if (!run_tape_staged(st, G, S, active, base + blockDim.x < hi, err)) return;
+    if (!active) continue;
+    double I = S[G.outI], Kv = S[G.outK];
     double y = weight(I, lg);
     bool bad = !isfinite(I) || !isfinite(Kv) || !isfinite(y) ||
                (dd_ratio > 0 && Kv > dd_ratio * fabs(I));
@@ -87,15 +98,14 @@ __global__ void integrate_kernel(GraphDev G, uint64_t first, uint64_t count, uin
 __global__ void dd_kernel(GraphDev G, uint64_t seed, const unsigned long long *queue, uint64_t nq,
                           double dd_ratio, double *y_out, int *status) {
   extern __shared__ dd dslots[];
-  dd *S = dslots + threadIdx.x;
-  const int stride = blockDim.x;
+  dd *S = dslots + threadIdx.x * G.nslots;   // this thread's row of the slot file
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
        i += (uint64_t)gridDim.x * blockDim.x) {
     double z[14], lz[14], lg;
     draw_any(G, queue[i], seed, z, lz, lg);
-    for (int k = 0; k < G.M; ++k) S[k * stride] = {z[k], 0.0};
-    run_tape_dd(G, S, stride);
-    dd I = S[G.outI * stride], K = S[G.outK * stride];
+    for (int k = 0; k < G.M; ++k) S[k] = {z[k], 0.0};
+    run_tape_dd(G, S);
+    dd I = S[G.outI], K = S[G.outK];
     double y = weight(I.hi + I.lo, lg);
     // accepted when the double-double result keeps ~8 significant digits
     // (2^-104 K / |I| below 1e-8)
@@ -110,17 +120,16 @@ __global__ void dd_kernel(GraphDev G, uint64_t seed, const unsigned long long *q
 __global__ void eval_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t seed, double *z_out,
                             double *lg_out, double *I_out, double *K_out, double *y_out) {
   extern __shared__ double slots[];
-  double *S = slots + threadIdx.x;
-  const int stride = blockDim.x;
+  double *S = slots + threadIdx.x * G.nslots;   // this thread's row of the slot file
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < count;
        base += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t i = base + threadIdx.x;
     if (i >= count) continue;
     double z[14], lz[14], lg;
     draw_any(G, first + i, seed, z, lz, lg);
-    for (int k = 0; k < G.M; ++k) { S[k * stride] = z[k]; z_out[i * G.M + k] = z[k]; }
-    run_tape(G, S, stride);
-    double I = S[G.outI * stride], Kv = S[G.outK * stride];
+    for (int k = 0; k < G.M; ++k) { S[k] = z[k]; z_out[i * G.M + k] = z[k]; }
+    run_tape(G, S);
+    double I = S[G.outI], Kv = S[G.outK];
     lg_out[i] = lg; I_out[i] = I; K_out[i] = Kv; y_out[i] = weight(I, lg);
   }
 }
@@ -129,17 +138,16 @@ __global__ void eval_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t
 __global__ void eval_dd_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t seed,
                                double *I_out, double *K_out, double *y_out) {
   extern __shared__ dd dslots2[];
-  dd *S = dslots2 + threadIdx.x;
-  const int stride = blockDim.x;
+  dd *S = dslots2 + threadIdx.x * G.nslots;   // this thread's row of the slot file
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < count;
        base += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t i = base + threadIdx.x;
     if (i >= count) continue;
     double z[14], lz[14], lg;
     draw_any(G, first + i, seed, z, lz, lg);
-    for (int k = 0; k < G.M; ++k) S[k * stride] = {z[k], 0.0};
-    run_tape_dd(G, S, stride);
-    dd I = S[G.outI * stride], K = S[G.outK * stride];
+    for (int k = 0; k < G.M; ++k) S[k] = {z[k], 0.0};
+    run_tape_dd(G, S);
+    dd I = S[G.outI], K = S[G.outK];
     double Iv = I.hi + I.lo;
     I_out[i] = Iv; K_out[i] = K.hi + K.lo; y_out[i] = weight(Iv, lg);
   }
@@ -183,32 +191,41 @@ struct Chunk {
 // (graph, sample index).
 __global__ void batched_kernel(const GraphDev *graphs, const Chunk *chunks, int nchunks, uint64_t seed,
                                double dd_ratio, Partial *part, unsigned long long *queue_idx, int *queue_gi,
-                               unsigned long long qcap, unsigned long long *qcount, int *next) {
+                               unsigned long long qcap, unsigned long long *qcount, int *next, int *err) {
   // chunks/part point at this launch's slice of the chunk list
-  extern __shared__ double slots[];
+  extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ int cur, curg;
   __shared__ GraphDev G;     // descriptor of the current chunk's graph
-  double *S = slots + threadIdx.x;
-  const int stride = blockDim.x;
+  __shared__ uint64_t bars[2];
+  Stage st{reinterpret_cast<Ins *>(dsm), bars, 0, 0};
   double z[14], lz[14];
-  if (threadIdx.x == 0) curg = -1;
+  if (threadIdx.x == 0) { curg = -1; stage_init(st); }
   for (;;) {
     if (threadIdx.x == 0) {
       cur = atomicAdd(next, 1);
       if (cur < nchunks && chunks[cur].gi != curg) { curg = chunks[cur].gi; G = graphs[curg]; }
+      if (cur < nchunks && chunks[cur].count > 0) stage_issue(st, G, 0);
     }
     __syncthreads();
     int c = cur;
     if (c >= nchunks) break;
     const Chunk ch = chunks[c];
+    // this thread's row of the slot file (pitch of the current graph; the
+    // launch reserves the largest pitch of its bucket)
+    double *S = reinterpret_cast<double *>(dsm + kStageBytes) + threadIdx.x * G.nslots;
     Partial p = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (uint64_t i = threadIdx.x; i < ch.count; i += blockDim.x) {
-      uint64_t idx = ch.first + i;
-      double lg;
-      draw_any(G, idx, seed, z, lz, lg);
-      for (int k = 0; k < G.M; ++k) S[k * stride] = z[k];
-      run_tape(G, S, stride);
-      double I = S[G.outI * stride], Kv = S[G.outK * stride];
+    for (uint64_t base = 0; base < ch.count; base += blockDim.x) {
+      const uint64_t i = base + threadIdx.x;
+      const bool active = i < ch.count;
+      const uint64_t idx = ch.first + i;
+      double lg = 0.0;
+      if (active) {
+        draw_any(G, idx, seed, z, lz, lg);
+        for (int k = 0; k < G.M; ++k) S[k] = z[k];
+      }
+      if (!run_tape_staged(st, G, S, active, base + blockDim.x < ch.count, err)) return;
+      if (!active) continue;
+      double I = S[G.outI], Kv = S[G.outK];
       double y = weight(I, lg);
       bool bad = !isfinite(I) || !isfinite(Kv) || !isfinite(y) || (dd_ratio > 0 && Kv > dd_ratio * fabs(I));
       p.n += 1;
@@ -256,20 +273,21 @@ __global__ void queue_scatter_kernel(const unsigned long long *qi, const int *qg
 
 // Double-double re-evaluation of the batched queue (count read on the device,
 // so the launch shape is fixed and the pair can be captured in a graph).
+// The threads of a CTA may work on different graphs: every row has the pitch
+// of the launch (the largest of its bucket), not that of the thread's graph.
 __global__ void batched_dd_kernel(const GraphDev *graphs, uint64_t seed, const unsigned long long *queue_idx,
                                   const int *queue_gi, const unsigned int *beg, const unsigned int *end,
-                                  double *y_out, int *status) {
+                                  double *y_out, int *status, int pitch) {
   extern __shared__ dd bdsl[];
-  dd *S = bdsl + threadIdx.x;
-  const int stride = blockDim.x;
+  dd *S = bdsl + threadIdx.x * pitch;   // this thread's row of the slot file
   uint64_t i0 = beg ? *beg : 0, i1 = *end;
   for (uint64_t i = i0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < i1; i += (uint64_t)gridDim.x * blockDim.x) {
     const GraphDev &G = graphs[queue_gi[i]];
     double z[14], lz[14], lg;
     draw_any(G, queue_idx[i], seed, z, lz, lg);
-    for (int k = 0; k < G.M; ++k) S[k * stride] = {z[k], 0.0};
-    run_tape_dd(G, S, stride);
-    dd I = S[G.outI * stride], K = S[G.outK * stride];
+    for (int k = 0; k < G.M; ++k) S[k] = {z[k], 0.0};
+    run_tape_dd(G, S);
+    dd I = S[G.outI], K = S[G.outK];
     double y = weight(I.hi + I.lo, lg);
     bool bad = !isfinite(I.hi) || !isfinite(K.hi) || !isfinite(y) || K.hi > 2.0e23 * fabs(I.hi);
     y_out[i] = bad ? 0.0 : y;
@@ -299,17 +317,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes
 __global__ void dd_dense_kernel(GraphDev G, uint64_t first, uint64_t seed, const unsigned long long *queue,
                                 const unsigned long long *qcount, double *y_off, unsigned char *flag) {
   extern __shared__ dd dsl3[];
-  dd *S = dsl3 + threadIdx.x;
-  const int stride = blockDim.x;
+  dd *S = dsl3 + threadIdx.x * G.nslots;   // this thread's row of the slot file
   uint64_t nq = *qcount;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
        i += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t idx = queue[i];
     double z[14], lz[14], lg;
     draw_any(G, idx, seed, z, lz, lg);
-    for (int k = 0; k < G.M; ++k) S[k * stride] = {z[k], 0.0};
-    run_tape_dd(G, S, stride);
-    dd I = S[G.outI * stride], K = S[G.outK * stride];
+    for (int k = 0; k < G.M; ++k) S[k] = {z[k], 0.0};
+    run_tape_dd(G, S);
+    dd I = S[G.outI], K = S[G.outK];
     double y = weight(I.hi + I.lo, lg);
     bool bad = !isfinite(I.hi) || !isfinite(K.hi) || !isfinite(y) || K.hi > 2.0e23 * fabs(I.hi);
     y_off[idx - first] = bad ? 0.0 : y;
@@ -477,7 +494,7 @@ static int load_impl(ae_ctx *c, int loops, const int *subset, int n_subset, int 
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     for (auto &lg : c->graphs) {
       size_t T = (size_t)1 << lg.g.M();
-      bytes += al(3 * T * 8) * 3 + al(lg.tape.khi.size() * 8) * 2 + al(lg.tape.code.size() * 8);
+      bytes += al(3 * T * 8) * 3 + al(lg.tape.khi.size() * 8) * 2 + al(lg.tape.code.size() * sizeof(Ins));
     }
     CUDA_TRY(c, cudaMalloc(&c->arena, bytes));
     c->arena_bytes = bytes;
@@ -498,9 +515,9 @@ static int load_impl(ae_ctx *c, int loops, const int *subset, int n_subset, int 
       size_t nk = lg.tape.khi.size();
       G.khi = (double *)p; if (nk) CUDA_TRY(c, cudaMemcpy(p, lg.tape.khi.data(), nk * 8, cudaMemcpyHostToDevice)); p += al(nk * 8);
       G.klo = (double *)p; if (nk) CUDA_TRY(c, cudaMemcpy(p, lg.tape.klo.data(), nk * 8, cudaMemcpyHostToDevice)); p += al(nk * 8);
-      G.code = (const uint2 *)p;
-      CUDA_TRY(c, cudaMemcpy(p, lg.tape.code.data(), lg.tape.code.size() * 8, cudaMemcpyHostToDevice));
-      p += al(lg.tape.code.size() * 8);
+      G.code = (const Ins *)p;
+      CUDA_TRY(c, cudaMemcpy(p, lg.tape.code.data(), lg.tape.code.size() * sizeof(Ins), cudaMemcpyHostToDevice));
+      p += al(lg.tape.code.size() * sizeof(Ins));
       G.M = lg.g.M(); G.ntape = (int)lg.tape.code.size(); G.nslots = lg.tape.nslots;
       G.outI = lg.tape.out_I; G.outK = lg.tape.out_K; G.graph_id = canon[gi];   // Philox stream of the graph
       lg.canonical_id = canon[gi];
@@ -533,15 +550,15 @@ extern "C" int ae_graph_info(ae_ctx *c, int id, ae_graph_meta *o) {
 // the candidate with the most resident warps per SM (the slot file, not the
 // register file, is what limits residency for long tapes), ties to the
 // larger block.
-static int pick_block_for(const ae_ctx *c, const void *kernel, int nslots, size_t elem) {
-  const size_t smem_cap = 200 * 1024;
+static int pick_block_for(const ae_ctx *c, const void *kernel, int nslots, size_t elem, size_t extra = 0) {
+  const size_t smem_cap = 224 * 1024;
   if (c->opts.block_size > 0) {
     int bs = c->opts.block_size;
-    return (size_t)bs * nslots * elem > smem_cap ? -1 : bs;
+    return extra + (size_t)bs * nslots * elem > smem_cap ? -1 : bs;
   }
   int best = -1, best_warps = 0;
-  for (int bs : {256, 128, 64, 32}) {
-    size_t smem = (size_t)bs * nslots * elem;
+  for (int bs : {1024, 768, 512, 384, 256, 128, 64, 32}) {
+    size_t smem = extra + (size_t)bs * nslots * elem;
     if (smem > smem_cap) continue;
     int per_sm = 0;
     if (kernel) {
@@ -566,7 +583,7 @@ static int ensure_scratch(ae_ctx *c, size_t nparts, size_t qcap) {
     CUDA_TRY(c, cudaMalloc(&c->d_part, nparts * sizeof(Partial)));
     c->part_cap = nparts;
   }
-  if (!c->d_qcount) CUDA_TRY(c, cudaMalloc(&c->d_qcount, sizeof(unsigned long long)));
+  if (!c->d_qcount) CUDA_TRY(c, cudaMalloc(&c->d_qcount, 2 * sizeof(unsigned long long)));
   if (qcap > c->queue_cap) {
     if (c->d_queue) cudaFree(c->d_queue);
     if (c->d_yq) cudaFree(c->d_yq);
@@ -595,9 +612,9 @@ static void host_dd_add(double &hi, double &lo, double x) {
 static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_graph_result *res) {
   LoadedGraph &lg = c->graphs[gid];
   GraphDev &G = lg.dev;
-  int bs = pick_block_for(c, (const void *)integrate_kernel, G.nslots, 8);
+  int bs = pick_block_for(c, (const void *)integrate_kernel, G.nslots, 8, kStageBytes);
   if (bs < 0) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
-  size_t smem = (size_t)bs * G.nslots * 8;
+  size_t smem = kStageBytes + (size_t)bs * G.nslots * 8;
   CUDA_TRY(c, cudaFuncSetAttribute(integrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = c->opts.ctas_per_sm;
   if (per_sm <= 0) {
@@ -615,18 +632,25 @@ static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_g
     size_t qcap = (size_t)std::max<uint64_t>(len, 65536);   // every sample may need re-evaluation
     int rc = ensure_scratch(c, grid, qcap);
     if (rc) return rc;
-    CUDA_TRY(c, cudaMemsetAsync(c->d_qcount, 0, sizeof(unsigned long long), c->stream));
+    // d_qcount[0]: queue length, d_qcount[1]: wait-timeout flag
+    CUDA_TRY(c, cudaMemsetAsync(c->d_qcount, 0, 2 * sizeof(unsigned long long), c->stream));
     cudaEvent_t e0, e1, ek;
     cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&ek);
     cudaEventRecord(e0, c->stream);
     integrate_kernel<<<(unsigned)grid, bs, smem, c->stream>>>(G, start, len, seed, c->opts.dd_ratio, c->d_part,
-                                                              c->d_queue, c->queue_cap, c->d_qcount);
+                                                              c->d_queue, c->queue_cap, c->d_qcount,
+                                                              (int *)(c->d_qcount + 1));
     CUDA_TRY(c, cudaGetLastError());
     cudaEventRecord(ek, c->stream);
     ++launches;
-    unsigned long long nq = 0;
-    CUDA_TRY(c, cudaMemcpyAsync(&nq, c->d_qcount, sizeof(nq), cudaMemcpyDeviceToHost, c->stream));
+    unsigned long long hq[2] = {0, 0};
+    CUDA_TRY(c, cudaMemcpyAsync(hq, c->d_qcount, sizeof(hq), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    unsigned long long nq = hq[0];
+    if (hq[1]) {
+      cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(ek);
+      return fail(c, AE_ERR_TIMEOUT, "integrate: a tape-staging wait ran out");
+    }
     if (nq > c->queue_cap) {
       cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(ek);
       return fail(c, AE_ERR_STATE, "double-double queue overflow");
@@ -803,9 +827,10 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     Launch L;
     L.c0 = chunks.size();
     // block size: the tuned one if it fits, else the occupancy choice for this bucket
-    L.bs = ((size_t)bs * bslots * 8 <= 200 * 1024) ? bs : pick_block_for(c, (const void *)batched_kernel, bslots, 8);
+    L.bs = (kStageBytes + (size_t)bs * bslots * 8 <= 224 * 1024)
+               ? bs : pick_block_for(c, (const void *)batched_kernel, bslots, 8, kStageBytes);
     if (L.bs < 0) return fail(c, AE_ERR_STATE, "batched slot file does not fit in shared memory");
-    L.smem = (size_t)L.bs * bslots * 8;
+    L.smem = kStageBytes + (size_t)L.bs * bslots * 8;
     int pm = 0;
     CUDA_TRY(c, cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
     CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pm, batched_kernel, L.bs, L.smem));
@@ -857,6 +882,7 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   int *drank = (int *)p; p += al(ids.size() * 4);
   unsigned long long *qcount = (unsigned long long *)p; p += 256;
   int *next = (int *)(qcount + 1);   // one counter per launch (up to 32)
+  int *derr = (int *)((char *)qcount + 192);   // wait-timeout flag
   std::vector<GraphDev> hg;
   for (int g : ids) hg.push_back(c->graphs[g].dev);
   // rank of each graph in bucket order; last rank of each bucket
@@ -876,7 +902,7 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   if (e == cudaSuccess) e = cudaMemcpyAsync(drank, hrank.data(), hrank.size() * 4, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dC, chunks.data(), nch * sizeof(Chunk), cudaMemcpyHostToDevice, c->stream);
   // one double-double launch per bucket, shaped for that bucket's slots
-  std::vector<int> dd_bs(launches.size());
+  std::vector<int> dd_bs(launches.size()), dd_pitch(launches.size());
   std::vector<size_t> dd_sm(launches.size());
   size_t ddmax = 0;
   {
@@ -888,6 +914,7 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
       int b16 = pick_block_for(c, (const void *)batched_dd_kernel, bslots, 16);
       if (b16 < 0) b16 = 32;
       dd_bs[l] = b16;
+      dd_pitch[l] = bslots;
       dd_sm[l] = (size_t)b16 * bslots * 16;
       ddmax = std::max(ddmax, dd_sm[l]);
     }
@@ -909,7 +936,7 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     for (size_t l = 0; l < launches.size(); ++l) {
       const Launch &L = launches[l];
       batched_kernel<<<L.grid, L.bs, L.smem, c->stream>>>(dG, dC + L.c0, (int)(L.c1 - L.c0), seed, c->opts.dd_ratio,
-                                                          dP + L.c0, qi, qg, qcap, qcount, next + l);
+                                                          dP + L.c0, qi, qg, qcap, qcount, next + l, derr);
     }
     rec(ek);
     queue_hist_kernel<<<grid2, 256, 0, c->stream>>>(qg, qcount, qcap, drank, hist);
@@ -919,7 +946,8 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     // [hist[last of l-1], hist[last of l])
     for (size_t l = 0; l < launches.size(); ++l) {
       const unsigned int *bg = l == 0 ? nullptr : hist + bucket_last[l - 1];
-      batched_dd_kernel<<<grid2, dd_bs[l], dd_sm[l], c->stream>>>(dG, seed, qi2, qg2, bg, hist + bucket_last[l], qy, qs);
+      batched_dd_kernel<<<grid2, dd_bs[l], dd_sm[l], c->stream>>>(dG, seed, qi2, qg2, bg, hist + bucket_last[l], qy, qs,
+                                                                  dd_pitch[l]);
     }
     rec(e1);
   };
@@ -942,8 +970,10 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     }
   }
   unsigned long long nq = 0;
+  int herr = 0;
   std::vector<Partial> parts(nch);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nq, qcount, 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(parts.data(), dP, nch * sizeof(Partial), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   float ms = 0, mk = 0;
@@ -967,6 +997,7 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   if (e1) cudaEventDestroy(e1);
   if (ek) cudaEventDestroy(ek);
   if (e != cudaSuccess) return fail(c, AE_ERR_CUDA, std::string("batched: ") + cudaGetErrorString(e));
+  if (herr) return fail(c, AE_ERR_TIMEOUT, "batched: a tape-staging wait ran out");
   for (auto &pp : parts)
     if (pp.n_overflow) return fail(c, AE_ERR_STATE, "double-double queue overflow");
   (void)buf;
@@ -1041,8 +1072,8 @@ static int autotune_batched(ae_ctx *c, const std::vector<int> &ids, BatchTune &b
     if (std::find(trial.begin(), trial.end(), byl[k]) == trial.end()) trial.push_back(byl[k]);
   }
   double best_rate = 0;
-  for (int bs : {64, 128, 256}) {
-    if ((size_t)bs * maxslots * 8 > 200 * 1024) continue;
+  for (int bs : {128, 256, 512}) {
+    if (kStageBytes + (size_t)bs * maxslots * 8 > 224 * 1024) continue;
     for (unsigned long long ch : {1024ull, 4096ull, 16384ull}) {
       uint64_t per = std::max<uint64_t>(ch * 4, (uint64_t)c->sm_count * bs * 8 / trial.size());
       std::vector<uint64_t> ns(trial.size(), per), fs(trial.size(), 1ull << 44);
@@ -1207,9 +1238,9 @@ extern "C" int ae_integrate_noalloc(ae_ctx *c, int gid, uint64_t nsamp, uint64_t
   double *y_off = (double *)(scr + kNaYOff);
   unsigned char *flag = scr + kNaFlagOff;
   GraphDev &G = c->graphs[gid].dev;
-  int bs = pick_block(c, G.nslots, 8);
+  int bs = pick_block_for(c, (const void *)integrate_kernel, G.nslots, 8, kStageBytes);
   if (bs < 0) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
-  size_t smem = (size_t)bs * G.nslots * 8;
+  size_t smem = kStageBytes + (size_t)bs * G.nslots * 8;
   CUDA_TRY(c, cudaFuncSetAttribute(integrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = c->opts.ctas_per_sm;
   if (per_sm <= 0) {
@@ -1218,11 +1249,13 @@ extern "C" int ae_integrate_noalloc(ae_ctx *c, int gid, uint64_t nsamp, uint64_t
   }
   uint64_t grid = std::min<uint64_t>((uint64_t)c->sm_count * per_sm, (uint64_t)kNaMaxGrid);
   if (grid * bs > nsamp) grid = std::max<uint64_t>(1, (nsamp + bs - 1) / bs);
-  // what must start at zero: the queue counter and the per-sample flags
-  CUDA_TRY(c, cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), c->stream));
+  int *werr = (int *)(qcount + 1);   // wait-timeout flag
+  // what must start at zero: the queue counter, the timeout flag and the
+  // per-sample flags
+  CUDA_TRY(c, cudaMemsetAsync(qcount, 0, 2 * sizeof(unsigned long long), c->stream));
   CUDA_TRY(c, cudaMemsetAsync(flag, 0, nsamp, c->stream));
   integrate_kernel<<<(unsigned)grid, bs, smem, c->stream>>>(G, 0, nsamp, seed, c->opts.dd_ratio, part, queue,
-                                                            kNaMaxSamples, qcount);
+                                                            kNaMaxSamples, qcount, werr);
   CUDA_TRY(c, cudaGetLastError());
   int bsd = pick_block(c, G.nslots, 16);
   if (bsd < 0) return fail(c, AE_ERR_STATE, "double-double slot file does not fit in shared memory");
@@ -1233,8 +1266,11 @@ extern "C" int ae_integrate_noalloc(ae_ctx *c, int gid, uint64_t nsamp, uint64_t
   noalloc_reduce_kernel<<<1, 256, 0, c->stream>>>(part, (int)grid, y_off, flag, nsamp, result);
   CUDA_TRY(c, cudaGetLastError());
   Partial r;
+  int herr = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&r, result, sizeof(Partial), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&herr, werr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (herr) return fail(c, AE_ERR_TIMEOUT, "integrate_noalloc: a tape-staging wait ran out");
   std::memset(out, 0, sizeof(*out));
   out->sum_y = r.sy_hi + r.sy_lo;
   out->sum_y2 = r.sy2_hi + r.sy2_lo;
