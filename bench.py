@@ -29,30 +29,37 @@ sys.path.insert(0, ROOT)
 METRIC = "MC samples/s and 1/(σ²·s) per graph set, learned+batched vs plain pdf, 1 B300"
 
 
+# FP64 operations of the table-driven elementary functions (one division
+# counted as one operation): exp2 = range reduction (10) + degree-7 Horner
+# (14) + table product; log2 = reduction (9) + 3-step Horner (6) + 5.
+EXP2_OPS = 25
+LOG2_OPS = 20
+
+
 def sampler_flops(M, learned=False):
     """FP64 operations of one draw of the sampler and density (FMA = 2),
-    counted from the steps of the walk.
+    counted from the steps of the code.
 
-    Plain density (series log2/exp2, bit-reproducible on the host): uniforms
-    (4 ops each, 2M of them), M-1 walk steps (product, |T| additions, one
-    series log2 of 42 ops, a quotient and a sum), M series exp2 (76 ops) with
-    normalisation, and the density of three sector components plus the
-    mixture (4 exp2, 1 log2).
+    Plain density: uniforms (4 ops each, 2M of them); M-1 walk steps
+    (product, |T| additions, one log2, a quotient and a sum); normalisation
+    (M exp2 and sums, one log2, M quotients and differences); three sector
+    densities (3 ops per level) and the four-component mixture (4 exp2,
+    one log2).
 
     Learned mixture: the same uniforms; M-1 walk steps of |T| additions, one
     log2, a product and a sum; normalisation (M exp2, M sums, one log2, one
-    reciprocal, 2M products/differences); three sector densities (3 ops per
-    level); the learned density (5 ops per level); one five-term log-sum-exp.
-    Each call of the device's exp2/log2 counts as ONE operation here, so the
-    learned count is a lower bound."""
+    reciprocal, 2M products/differences); three sector densities; the
+    learned density (5 ops per level); one five-term log-sum-exp (5 exp2, one
+    log2).  This path calls the device's exp2/log2; each call is counted at
+    the operation count of the table-driven form of the same function."""
     if learned:
-        walk = sum((M - l) + 3 for l in range(M - 1))
-        norm = 4 * M + 2
-        pdf = 9 * (M - 1) + 14 + 5 * (M - 1) + 2 + 17
+        walk = sum((M - l) + 2 + LOG2_OPS for l in range(M - 1))
+        norm = M * EXP2_OPS + M + LOG2_OPS + 1 + 2 * M
+        pdf = 9 * (M - 1) + 14 + 5 * (M - 1) + 2 + 5 * (EXP2_OPS + 2) + LOG2_OPS + 1
         return 8 * M + walk + norm + pdf
-    walk = sum(1 + (M - l) + 42 + 2 for l in range(M - 1))
-    norm = M * 76 + M + 42 + 2 * M
-    pdf = M + 3 * (M - 1) * 3 + 9 + 4 * (2 + 76) + 42 + 2
+    walk = sum(1 + (M - l) + LOG2_OPS + 2 for l in range(M - 1))
+    norm = M * EXP2_OPS + M + LOG2_OPS + 2 * M
+    pdf = M + 3 * (M - 1) * 3 + 9 + 4 * (2 + EXP2_OPS) + LOG2_OPS + 2
     return 8 * M + 2 + walk + norm + pdf
 
 
@@ -176,6 +183,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--loops", type=int, default=3)
+    ap.add_argument("--graphs", type=int, default=0,
+                    help="seeded subset of this many graphs of the loop order (0: all of them)")
     ap.add_argument("--samples", type=int, default=1 << 24, help="samples per graph per step")
     ap.add_argument("--train", type=int, default=1 << 20, help="training samples per graph")
     ap.add_argument("--train-steps", type=int, default=150)
@@ -206,7 +215,13 @@ def main():
     opts.stream = stream.cuda_stream
     ctx = ae.Context(local, opts)
     t0 = time.perf_counter()
-    ngr = ctx.load_graphs(args.loops)
+    canon = None
+    if args.graphs > 0:
+        total_graphs = {1: 1, 2: 4, 3: 28, 4: 269, 5: 3213}[args.loops]
+        canon = ae.seeded_subset(total_graphs, min(args.graphs, total_graphs), 0)
+        ngr = ctx.load_graph_subset(args.loops, canon)
+    else:
+        ngr = ctx.load_graphs(args.loops)
     compile_s = time.perf_counter() - t0
     ids = list(range(ngr))
     info = [ctx.graph_info(i) for i in ids]
@@ -315,17 +330,19 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        crate, cores, evals, wall = oracle_rate(args.loops, [0, ngr // 2, ngr - 1], args.oracle_samples)
+        cids = [0, ngr // 2, ngr - 1] if canon is None else [canon[0], canon[len(canon) // 2], canon[-1]]
+        crate, cores, evals, wall = oracle_rate(args.loops, cids, args.oracle_samples)
         cpu = {"value": crate, "unit": "samples/s", "cores": cores, "kind": "oracle",
-               "sample": "graphs 0, %d, %d of the set, %d samples each, plain density (evaluation after "
-                         "per-graph setup, %.1f s on %d processes)" % (ngr // 2, ngr - 1, args.oracle_samples, wall, cores)}
+               "sample": "canonical graphs %s of the %d-loop list, %d samples each, plain density (evaluation "
+                         "after per-graph setup, %.1f s on %d processes)" % (cids, args.loops, args.oracle_samples,
+                                                                             wall, cores)}
     isps = 1.0 / (sigma ** 2 * t_dev) if sigma > 0 else None
     line = {
         "metric": METRIC, "value": rate, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "all %d %d-loop vertex graphs without lepton loops, %s" % (
-                       len(ids), args.loops,
+        "config": {"workload": "%s %d %d-loop vertex graphs without lepton loops, %s" % (
+                       "all" if canon is None else "seeded subset of", len(ids), args.loops,
                        "learned mixture density, one batched persistent launch per step" if learned
                        else "plain density, one launch per graph"),
                    "samples_per_graph_per_step": args.samples, "seed": "step index (+ rank offset)",

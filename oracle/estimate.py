@@ -17,12 +17,12 @@ import numpy as np
 from .graphs import enumerate_graphs
 from .integrand import Integrand
 from .philox import uniforms
-from .sampler import Density, sample, exp2_series
+from .sampler import Density, sample, exp2_tab
 
 
 def weight(I, lg):
     kf = math.floor(lg)
-    s = float(exp2_series(kf - lg))
+    s = float(exp2_tab(kf - lg))
     kc = min(max(kf, -100000.0), 100000.0)
     return math.ldexp(I * s, -int(kc))
 

@@ -81,6 +81,60 @@ def exp2_series(x):
     return np.ldexp(p, k.astype(np.int64))
 
 
+# Table-driven log2 / exp2 (Tang's method: reduce the argument to a short
+# interval around a table point, evaluate a short series there).  The tables
+# are the series functions above evaluated at the table points, so they are
+# fixed by the same definitions.
+#   exp2: x = k/32 + d, |d| <= 1/64:  2^x = 2^(k div 32) * 2^((k mod 32)/32) * exp(d ln 2),
+#         exp by its Taylor polynomial of degree 7 (remainder < 5e-21).
+#   log2: x = F 2^E with F in [3/4, 3/2); c = j/32 nearest to F (j = 24..48):
+#         log2 x = E + log2 c + 2 atanh(s)/ln 2, s = (F - c)/(F + c), |s| <= 1/96,
+#         atanh by s (1 + s^2/3 + s^4/5 + s^6/7) (remainder < 2e-19 s).  The
+#         interval around 1 keeps log2 x accurate relative to itself near x = 1.
+EXP2_TAB = np.array([float(exp2_series(j / 32.0)) for j in range(32)])
+LOG2_TAB = np.array([float(log2_series(j / 32.0)) for j in range(24, 49)])
+
+
+def exp2_tab(x):
+    """2^x (numpy array), table-driven; 0 below -1100, inf above 1100, NaN
+    for NaN."""
+    x0 = np.asarray(x, dtype=np.float64)
+    ok = (x0 >= -1100.0) & (x0 <= 1100.0)
+    x = np.where(ok, x0, 0.0)
+    k = np.floor(x * 32.0 + 0.5)
+    m = np.floor(k * 0.03125)
+    j = (k - m * 32.0).astype(np.int64)
+    r = (x - k * 0.03125) * LN2
+    p = 1.0 / 5040.0
+    for c in (1.0 / 720.0, 1.0 / 120.0, 1.0 / 24.0, 1.0 / 6.0, 0.5, 1.0, 1.0):
+        p = p * r + c
+    v = np.ldexp(EXP2_TAB[j] * p, m.astype(np.int64))
+    return np.where(ok, v, np.where(x0 > 1100.0, np.inf, np.where(x0 < -1100.0, 0.0, x0)))
+
+
+def log2_tab(x):
+    """log2 (numpy array), table-driven; -inf at 0, inf at inf, NaN for
+    negative or NaN arguments."""
+    x0 = np.asarray(x, dtype=np.float64)
+    ok = (x0 > 0.0) & (x0 < np.inf)
+    x = np.where(ok, x0, 1.0)
+    f, e = np.frexp(x)                     # x = f * 2^e, f in [0.5, 1)
+    low = f < 0.75
+    F = np.where(low, f * 2.0, f)
+    E = np.where(low, e - 1, e).astype(np.float64)
+    jf = np.floor(F * 32.0 + 0.5)
+    c = jf * 0.03125
+    s = (F - c) / (F + c)
+    s2 = s * s
+    p = 1.0 / 7.0
+    p = p * s2 + 1.0 / 5.0
+    p = p * s2 + 1.0 / 3.0
+    p = p * s2 + 1.0
+    t = ((s + s) * p) * INV_LN2
+    v = (E + LOG2_TAB[jf.astype(np.int64) - 24]) + t
+    return np.where(ok, v, np.where(x0 == 0.0, -np.inf, np.where(x0 == np.inf, np.inf, np.nan)))
+
+
 class LineSets:
     """Line structure of one graph in the merged (M = 3n-1) numbering."""
 
@@ -177,7 +231,7 @@ class Density:
         self.C = [1.0 - C2 - C3 - C4, C3, C4]      # mixture weights of g1, g3, g4
         self.C2 = C2
         self.full = (1 << M) - 1
-        self.log2_fact = float(log2_series(float(math.factorial(M - 1))))  # log2 (M-1)!
+        self.log2_fact = float(log2_tab(float(math.factorial(M - 1))))  # log2 (M-1)!
 
 
 def sample(dens, u):
@@ -221,26 +275,26 @@ def sample(dens, u):
             chosen = np.where(chosen < 0, last, chosen)
             lz[sel, chosen] = cur
             T = T ^ (np.int64(1) << chosen)
-            cur = cur + log2_series(ut) / deg[T]
+            cur = cur + log2_tab(ut) / deg[T]
         # the last remaining line
         lastj = np.zeros(sel.size, dtype=np.int64)
         for j in range(M):
             lastj = np.where(T >> j & 1 == 1, j, lastj)
         lz[sel, lastj] = cur
-        e = exp2_series(lz[sel])
+        e = exp2_tab(lz[sel])
         ssum = np.zeros(sel.size)
         for i in range(M):
             ssum = ssum + e[:, i]
         zz[sel] = e / ssum[:, None]
-        lz[sel] = lz[sel] - log2_series(ssum)[:, None]
+        lz[sel] = lz[sel] - log2_tab(ssum)[:, None]
     sel = np.nonzero(comp == 1)[0]
     if sel.size:
-        L = -log2_series(u[sel, 1:1 + M])
+        L = -log2_tab(u[sel, 1:1 + M])
         ssum = np.zeros(sel.size)
         for i in range(M):
             ssum = ssum + L[:, i]
         zz[sel] = L / ssum[:, None]
-        lz[sel] = log2_series(L) - log2_series(ssum)[:, None]
+        lz[sel] = log2_tab(L) - log2_tab(ssum)[:, None]
     return zz, log2_density(dens, lz), comp
 
 
@@ -270,11 +324,11 @@ def log2_density(dens, lz):
             acc = acc + deg[T] * (cur - prev)
             prev = cur
             T = T ^ (np.int64(1) << order[:, l])
-        terms.append(log2_series(dens.C[k]) - log2_series(phi[dens.full]) + acc - sumlz)
-    terms.insert(1, np.full(S, log2_series(dens.C2) + dens.log2_fact))
+        terms.append(log2_tab(dens.C[k]) - log2_tab(phi[dens.full]) + acc - sumlz)
+    terms.insert(1, np.full(S, log2_tab(dens.C2) + dens.log2_fact))
     terms = np.stack(terms, 1)
     m = terms.max(1)
     rel = np.zeros(S)
     for k in range(4):
-        rel = rel + exp2_series(terms[:, k] - m)
-    return m + log2_series(rel)
+        rel = rel + exp2_tab(terms[:, k] - m)
+    return m + log2_tab(rel)

@@ -81,6 +81,11 @@ DensityTables build_density(const Graph &g, const DensityConsts &c);
 // plain IEEE add/multiply, series from their published definitions.
 double ae_log2(double x);
 double ae_exp2(double x);
+// table-driven forms used by the sampler and density (tables from the series)
+double ae_log2t(double x);
+double ae_exp2t(double x);
+const double *ae_exp2_table();   // 2^(j/32), j = 0..31
+const double *ae_log2_table();   // log2(j/32), j = 24..48
 
 // ------------------------------------------------------------- tapes -----
 // Operations of the integrand compiler's intermediate program (value ids,

@@ -62,3 +62,5 @@ struct ae_ctx {
 
 
 int ae_fail(ae_ctx *c, int code, const std::string &msg);
+// uploads the sampler's log2/exp2 tables into learned.cu's constant memory
+cudaError_t ae_learned_upload_tables();

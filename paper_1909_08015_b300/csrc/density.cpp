@@ -18,6 +18,8 @@
 #include <cstdint>
 #include <vector>
 
+#include <array>
+
 #include "ae_internal.h"
 
 namespace ae {
@@ -49,6 +51,66 @@ double ae_exp2(double x) {
     p = p * r + 1.0 / fact;
   }
   return std::ldexp(p, (int)std::max(-100000.0, std::min(100000.0, k)));
+}
+
+// Table-driven log2 / exp2 (Tang's method): the argument is reduced to a
+// short interval around a table point and a short series is evaluated there.
+//   exp2: x = k/32 + d, |d| <= 1/64: 2^x = 2^(k div 32) 2^((k mod 32)/32) exp(d ln 2),
+//         exp by its Taylor polynomial of degree 7.
+//   log2: x = F 2^E, F in [3/4, 3/2), c = j/32 nearest to F (j = 24..48):
+//         log2 x = E + log2 c + 2 atanh(s)/ln 2, s = (F - c)/(F + c), |s| <= 1/96,
+//         atanh s by s (1 + s^2/3 + s^4/5 + s^6/7).
+// The tables are ae_exp2 / ae_log2 at the table points.  The device's
+// dexp2/dlog2 perform the same IEEE operations on the same tables.
+// (function-local statics: initialised once, thread-safe; the graphs are
+// compiled on several host threads)
+const double *ae_exp2_table() {
+  static const std::array<double, 32> t = [] {
+    std::array<double, 32> a{};
+    for (int j = 0; j < 32; ++j) a[j] = ae_exp2((double)j / 32.0);
+    return a;
+  }();
+  return t.data();
+}
+const double *ae_log2_table() {
+  static const std::array<double, 25> t = [] {
+    std::array<double, 25> a{};
+    for (int j = 24; j <= 48; ++j) a[j - 24] = ae_log2((double)j / 32.0);
+    return a;
+  }();
+  return t.data();
+}
+
+double ae_exp2t(double x) {
+  if (!(x >= -1100.0 && x <= 1100.0)) return x > 1100.0 ? HUGE_VAL : (x < -1100.0 ? 0.0 : x);
+  const double *T = ae_exp2_table();
+  double k = std::floor(x * 32.0 + 0.5);
+  double m = std::floor(k * 0.03125);
+  int j = (int)(k - m * 32.0);
+  double r = (x - k * 0.03125) * 0.6931471805599453;
+  double p = 1.0 / 5040.0;
+  const double c[7] = {1.0 / 720.0, 1.0 / 120.0, 1.0 / 24.0, 1.0 / 6.0, 0.5, 1.0, 1.0};
+  for (int i = 0; i < 7; ++i) p = p * r + c[i];
+  return std::ldexp(T[j] * p, (int)m);
+}
+
+double ae_log2t(double x) {
+  if (!(x > 0.0 && x < HUGE_VAL)) return x == 0.0 ? -HUGE_VAL : (x == HUGE_VAL ? HUGE_VAL : NAN);
+  const double *T = ae_log2_table();
+  int e;
+  double f = std::frexp(x, &e);
+  double F = f, E = (double)e;
+  if (f < 0.75) { F = f * 2.0; E = (double)(e - 1); }
+  double jf = std::floor(F * 32.0 + 0.5);
+  double c = jf * 0.03125;
+  double s = (F - c) / (F + c);
+  double s2 = s * s;
+  double p = 1.0 / 7.0;
+  p = p * s2 + 1.0 / 5.0;
+  p = p * s2 + 1.0 / 3.0;
+  p = p * s2 + 1.0;
+  double t = ((s + s) * p) * 1.4426950408889634;
+  return (E + T[(int)jf - 24]) + t;
 }
 
 DensityTables build_density(const Graph &g, const DensityConsts &c) {
@@ -120,7 +182,7 @@ DensityTables build_density(const Graph &g, const DensityConsts &c) {
   t.C[0] = C1; t.C[1] = c.C2; t.C[2] = c.C3; t.C[3] = c.C4;
   double f = 1.0;
   for (int i = 2; i <= M - 1; ++i) f = f * (double)i;
-  t.log2_fact = ae_log2(f);
+  t.log2_fact = ae_log2t(f);
   return t;
 }
 

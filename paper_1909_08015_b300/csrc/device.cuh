@@ -1,6 +1,8 @@
 // Device building blocks for sm_103a: Philox4x32-10, the Hepp-sector
 // sampler and density, the FP64 tape interpreter and its double-double twin.
 #pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
 #include <cstdint>
 
 namespace aedev {
@@ -63,6 +65,64 @@ __device__ __forceinline__ double dexp2(double x) {
   for (int i = 1; i < 19; ++i) p = __dadd_rn(__dmul_rn(p, r), kInvFact[i]);
   double kc = fmin(fmax(k, -100000.0), 100000.0);
   return ldexp(p, (int)kc);
+}
+
+// --------------------------------------- log2 / exp2 (table-driven) ----
+// Tang's table-driven method, the same IEEE operations as the host's
+// ae_log2t / ae_exp2t on the same tables (2^(j/32) and log2(j/32), the series
+// above at the table points, computed by the host and uploaded when a
+// context is created).
+//   exp2: x = k/32 + d, |d| <= 1/64; Taylor polynomial of degree 7 for exp(d ln 2).
+//   log2: x = F 2^E, F in [3/4, 3/2), c = j/32; 2 atanh((F-c)/(F+c))/ln 2, 4 terms.
+// Outside [-1100, 1100] exp2 is 0 or inf; log2 0 = -inf; NaN stays NaN (so a
+// table index is always in range).
+// (global memory read through L1: each lane indexes its own entry, which the
+// constant cache would serialise)
+__device__ double kExp2Tab[32];
+__device__ double kLog2Tab[25];
+
+// Each translation unit that launches sampling kernels holds its own copy of
+// the tables and uploads it with this function.
+static inline cudaError_t upload_elem_tables(const double *exp2_tab, const double *log2_tab) {
+  cudaError_t e = cudaMemcpyToSymbol(kExp2Tab, exp2_tab, 32 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(kLog2Tab, log2_tab, 25 * sizeof(double));
+  return e;
+}
+
+__device__ __forceinline__ double dexp2t(double x) {
+  if (!(x >= -1100.0 && x <= 1100.0)) return x > 1100.0 ? CUDART_INF : (x < -1100.0 ? 0.0 : x);
+  const double k = floor(__dadd_rn(__dmul_rn(x, 32.0), 0.5));
+  const double m = floor(__dmul_rn(k, 0.03125));
+  const int j = (int)__dadd_rn(k, -__dmul_rn(m, 32.0));
+  const double r = __dmul_rn(__dadd_rn(x, -__dmul_rn(k, 0.03125)), 0.6931471805599453);
+  double p = 1.0 / 5040.0;
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 720.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 120.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 24.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0 / 6.0);
+  p = __dadd_rn(__dmul_rn(p, r), 0.5);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0);
+  return ldexp(__dmul_rn(__ldg(kExp2Tab + j), p), (int)m);
+}
+
+__device__ __forceinline__ double dlog2t(double x) {
+  if (!(x > 0.0 && x < CUDART_INF)) return x == 0.0 ? -CUDART_INF : (x == CUDART_INF ? CUDART_INF : CUDART_NAN);
+  int e;
+  const double f = frexp(x, &e);
+  const bool low = f < 0.75;
+  const double F = low ? __dmul_rn(f, 2.0) : f;
+  const double E = (double)(low ? e - 1 : e);
+  const double jf = floor(__dadd_rn(__dmul_rn(F, 32.0), 0.5));
+  const double c = __dmul_rn(jf, 0.03125);
+  const double s = __ddiv_rn(__dadd_rn(F, -c), __dadd_rn(F, c));
+  const double s2 = __dmul_rn(s, s);
+  double p = 1.0 / 7.0;
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 5.0);
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 3.0);
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0);
+  const double t = __dmul_rn(__dmul_rn(__dadd_rn(s, s), p), 1.4426950408889634);
+  return __dadd_rn(__dadd_rn(E, __ldg(kLog2Tab + (int)jf - 24)), t);
 }
 
 // ---------------------------------------------------- double-double ----

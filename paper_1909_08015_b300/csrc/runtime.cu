@@ -385,6 +385,10 @@ extern "C" int ae_create(ae_ctx **out, int dev, const ae_opts *opts) {
     cudaError_t e = cudaSetDevice(dev);
     if (e != cudaSuccess) { delete c; return AE_ERR_CUDA; }
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    // tables of the sampler's log2/exp2, in both units that launch sampling kernels
+    e = upload_elem_tables(ae_exp2_table(), ae_log2_table());
+    if (e == cudaSuccess) e = ae_learned_upload_tables();
+    if (e != cudaSuccess) { delete c; return AE_ERR_CUDA; }
     if (c->opts.stream) {
       c->stream = (cudaStream_t)c->opts.stream;
       c->own_stream = false;
@@ -523,8 +527,8 @@ static int load_impl(ae_ctx *c, int loops, const int *subset, int n_subset, int 
       lg.canonical_id = canon[gi];
       G.C1 = lg.dens.C[0]; G.C2 = lg.dens.C[1]; G.C3 = lg.dens.C[2]; G.C4 = lg.dens.C[3];
       G.log2_fact = lg.dens.log2_fact;
-      for (int k = 0; k < 4; ++k) G.log2C[k] = ae_log2(lg.dens.C[k]);
-      for (int k = 0; k < 3; ++k) G.log2phi_full[k] = ae_log2(lg.dens.phi[k][T - 1]);
+      for (int k = 0; k < 4; ++k) G.log2C[k] = ae_log2t(lg.dens.C[k]);
+      for (int k = 0; k < 3; ++k) G.log2phi_full[k] = ae_log2t(lg.dens.phi[k][T - 1]);
     }
   }
   if (n_out) *n_out = (int)c->graphs.size();
@@ -557,7 +561,7 @@ static int pick_block_for(const ae_ctx *c, const void *kernel, int nslots, size_
     return extra + (size_t)bs * nslots * elem > smem_cap ? -1 : bs;
   }
   int best = -1, best_warps = 0;
-  for (int bs : {1024, 768, 512, 384, 256, 128, 64, 32}) {
+  for (int bs : {1024, 768, 640, 512, 448, 384, 320, 256, 224, 192, 160, 128, 96, 64, 32}) {
     size_t smem = extra + (size_t)bs * nslots * elem;
     if (smem > smem_cap) continue;
     int per_sm = 0;
@@ -1072,7 +1076,13 @@ static int autotune_batched(ae_ctx *c, const std::vector<int> &ids, BatchTune &b
     if (std::find(trial.begin(), trial.end(), byl[k]) == trial.end()) trial.push_back(byl[k]);
   }
   double best_rate = 0;
-  for (int bs : {128, 256, 512}) {
+  // candidates: the block with the most resident warps for the largest slot
+  // row, and the usual sizes that fit
+  const int occ = pick_block_for(c, (const void *)batched_kernel, maxslots, 8, kStageBytes);
+  std::vector<int> cand;
+  for (int bs : {occ, 128, 256, 512})
+    if (bs > 0 && std::find(cand.begin(), cand.end(), bs) == cand.end()) cand.push_back(bs);
+  for (int bs : cand) {
     if (kStageBytes + (size_t)bs * maxslots * 8 > 224 * 1024) continue;
     for (unsigned long long ch : {1024ull, 4096ull, 16384ull}) {
       uint64_t per = std::max<uint64_t>(ch * 4, (uint64_t)c->sm_count * bs * 8 / trial.size());

@@ -1,0 +1,54 @@
+"""Writes tests/golden/oracle_samples_<n>loop.txt: per-sample values of the
+CPU oracle (and nothing else) for a few graphs whose oracle set-up takes
+minutes, so that the GPU parity tests can compare against them without
+rebuilding the oracle's coefficient tables on every run.
+
+    python tests/golden/make_oracle_samples.py 4 0 5 134 --count 12
+
+Each line: graph id, sample index, then z (M values), log2 g, I, K, all as
+hexadecimal floating-point literals (exact round trip).  Seed 0.
+"""
+import argparse
+import multiprocessing as mp
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+
+def one(args):
+    n, gi, count, seed = args
+    from oracle.estimate import GraphOracle
+    from oracle.graphs import enumerate_graphs
+    o = GraphOracle(enumerate_graphs(n)[gi], gi)
+    r = o.samples(0, count, seed)
+    lines = []
+    for k in range(count):
+        vals = list(r["z"][k]) + [r["log2g"][k], r["I"][k], r["K"][k]]
+        lines.append("%d %d %s" % (gi, k, " ".join(float(v).hex() for v in vals)))
+    return lines
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("loops", type=int)
+    ap.add_argument("ids", type=int, nargs="+")
+    ap.add_argument("--count", type=int, default=12)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args()
+    with mp.get_context("spawn").Pool(len(a.ids)) as pool:
+        res = pool.map(one, [(a.loops, gi, a.count, a.seed) for gi in a.ids])
+    path = os.path.join(HERE, "oracle_samples_%dloop.txt" % a.loops)
+    with open(path, "w") as f:
+        f.write("# CPU oracle per-sample values, %d-loop graphs %s, seed %d, samples 0..%d\n"
+                % (a.loops, a.ids, a.seed, a.count - 1))
+        f.write("# written by tests/golden/make_oracle_samples.py (calls oracle/ only)\n")
+        f.write("# columns: graph sample z[0..M-1] log2g I K (hex floats)\n")
+        for lines in res:
+            f.write("\n".join(lines) + "\n")
+    print(path)
+
+
+if __name__ == "__main__":
+    main()

@@ -16,7 +16,7 @@ from oracle.forest import divergent_subgraphs, terms as forest_terms
 from oracle.graphs import Graph, enumerate_graphs, class_counts, perfect_matchings, is_1pi, word_of
 from oracle.integrand import Integrand
 from oracle.philox import philox4x32_10, uniforms
-from oracle.sampler import Density, sample, log2_series, exp2_series, deg_table, phi_table
+from oracle.sampler import Density, sample, log2_series, exp2_series, log2_tab, exp2_tab, deg_table, phi_table
 from oracle.estimate import GraphOracle, summarize, weight
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
@@ -130,6 +130,21 @@ def test_log2_exp2_series_accuracy():
     assert np.all(np.abs(l - np.log2(x)) <= 4 * np.spacing(np.abs(np.log2(x))) + 1e-300)
     t = rng.uniform(-1000, 1000, 20000)
     assert np.all(np.abs(exp2_series(t) / np.exp2(t) - 1) < 4e-16)
+
+
+def test_log2_exp2_table_accuracy():
+    """The table-driven forms used by the sampler: within 4 ulp of libm for
+    log2 (including arguments next to 1, where the result is tiny) and 4e-16
+    relative for exp2; exact at powers of two."""
+    rng = np.random.default_rng(1)
+    for x in (np.exp(rng.uniform(-700, 700, 20000)), 1.0 + rng.uniform(-1e-3, 1e-3, 20000),
+              rng.uniform(0.3, 3.0, 20000)):
+        l = log2_tab(x)
+        assert np.all(np.abs(l - np.log2(x)) <= 4 * np.spacing(np.abs(np.log2(x))) + 1e-300)
+    assert list(log2_tab(np.array([0.25, 0.5, 1.0, 2.0, 1024.0]))) == [-2.0, -1.0, 0.0, 1.0, 10.0]
+    t = np.concatenate([rng.uniform(-1000, 1000, 20000), rng.uniform(-1, 1, 20000)])
+    assert np.all(np.abs(exp2_tab(t) / np.exp2(t) - 1) < 4e-16)
+    assert list(exp2_tab(np.array([-3.0, 0.0, 1.0, 10.0]))) == [0.125, 1.0, 2.0, 1024.0]
 
 
 # ---------------------------------------------------------------- pdf -----
