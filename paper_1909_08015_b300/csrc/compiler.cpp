@@ -531,6 +531,9 @@ struct Builder {
   std::map<std::tuple<int, int, int>, int> cse;
   double flops = 0;
   bool horner = true;   // Horner trees for sums of monomials (else monomial chains)
+  bool share = true;    // reuse identical Horner subtrees emitted recently
+  int share_window = 64;   // instructions
+  std::map<std::vector<long long>, std::pair<int, size_t>> hcse;   // value id, program size after it
 
   int newval() { return nvals++; }
   int konst(double hi, double lo = 0.0) {
@@ -566,7 +569,7 @@ struct Builder {
   void fma(int acc, int a, int b) { prog.push_back({T_FMA, acc, a, b}); flops += 2; }
   int mulc(int a, int k) { int d = newval(); prog.push_back({T_MULC, d, a, k}); flops += 1; return d; }
   void addabs(int acc, int a) { prog.push_back({T_ADDABS, acc, a, -1}); flops += 1; }
-  void clear_cse() { cse.clear(); }
+  void clear_cse() { cse.clear(); hcse.clear(); }
 };
 
 // Products of sorted variable lists evaluated in lexicographic order: the
@@ -608,7 +611,25 @@ struct HMono { std::vector<int> v; int k; };   // sorted variable multiset, cons
 // Returns the value id of the node's polynomial  K[coef] + sum over ms.
 static int horner_node(Builder &B, std::vector<HMono> &ms, int coef, int zero_k) {
   // ms: monomials of this node with at least one variable each; coef: the
-  // node's own constant index or -1.
+  // node's own constant index or -1.  A polynomial already emitted since the
+  // last clear_cse (same monomials, same coefficients) is reused.
+  std::vector<long long> key;
+  if (B.share && ms.size() >= 2) {
+    std::vector<std::pair<std::vector<int>, int>> srt;
+    srt.reserve(ms.size());
+    for (auto &m : ms) srt.push_back({m.v, m.k});
+    std::sort(srt.begin(), srt.end());
+    key.push_back(coef);
+    for (auto &p : srt) {
+      key.push_back(-1 - (long long)p.first.size());
+      for (int x : p.first) key.push_back(x);
+      key.push_back(p.second);
+    }
+    auto it = B.hcse.find(key);
+    // only recent subtrees: reusing one from far back would keep its value
+    // live (a slot occupied) across everything in between
+    if (it != B.hcse.end() && B.prog.size() - it->second.second <= (size_t)B.share_window) return it->second.first;
+  }
   int acc = -1;
   std::vector<HMono> rest;
   rest.swap(ms);
@@ -643,6 +664,7 @@ static int horner_node(Builder &B, std::vector<HMono> &ms, int coef, int zero_k)
     B.flops += (acc < 0 && coef < 0) ? 1 : 2;
     acc = d;
   }
+  if (!key.empty()) B.hcse[key] = {acc, B.prog.size()};
   return acc;
 }
 
