@@ -41,8 +41,9 @@ def sampler_flops(M, learned=False):
     counted from the steps of the code.
 
     Plain density: uniforms (4 ops each, 2M of them); M-1 walk steps
-    (product, |T| additions, one log2, a quotient and a sum); normalisation
-    (M exp2 and sums, one log2, M quotients and differences); three sector
+    (product, |T| additions, one log2, a product with 1/Deg and a sum);
+    normalisation (M exp2 and sums, one log2, one reciprocal, M products and
+    differences); three sector
     densities (3 ops per level) and the four-component mixture (4 exp2,
     one log2).
 
@@ -58,7 +59,7 @@ def sampler_flops(M, learned=False):
         pdf = 9 * (M - 1) + 14 + 5 * (M - 1) + 2 + 5 * (EXP2_OPS + 2) + LOG2_OPS + 1
         return 8 * M + walk + norm + pdf
     walk = sum(1 + (M - l) + LOG2_OPS + 2 for l in range(M - 1))
-    norm = M * EXP2_OPS + M + LOG2_OPS + 2 * M
+    norm = M * EXP2_OPS + M + LOG2_OPS + 1 + 2 * M
     pdf = M + 3 * (M - 1) * 3 + 9 + 4 * (2 + EXP2_OPS) + LOG2_OPS + 2
     return 8 * M + 2 + walk + norm + pdf
 

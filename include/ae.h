@@ -45,7 +45,17 @@ typedef struct ae_opts {
   int ctas_per_sm;                   /* CTAs per SM for the grid, 0 = automatic   */
   void *stream;                      /* cudaStream_t to launch on; NULL = a stream
                                         owned by the context                      */
+  int rng;                           /* 0 = Philox4x32-10 (Calc 2), 1 = MRG32k3a
+                                        (Calc 1, L'Ecuyer 1999): sample i of graph
+                                        g under seed s starts at output
+                                        s 2^96 + g 2^80 + 64 i of the stream from
+                                        the state (12345 x 6); set before loading */
 } ae_opts;
+
+/* The settings of the paper's second calculation (Sec. V, Calc 1):
+ * MRG32k3a, C2 = 0.03, C3 = 0.035, C4 = 0.035, D = 0.75; the rest as in
+ * ae_default_opts. */
+void ae_calc1_opts(ae_opts *opts);
 
 void ae_default_opts(ae_opts *opts);
 
@@ -207,6 +217,39 @@ int ae_proposal_nparams(void);
  * proportional to sigma_j^2.  sigma_out (nullable) receives the pilot sigmas. */
 int ae_allocate(ae_ctx *ctx, const int *graph_ids, int n_ids, uint64_t n_pilot, uint64_t n_total,
                 uint64_t seed, int mode, uint64_t *n_out, double *sigma_out);
+
+/* The paper's sampling probabilities of its integration controller
+ * (Sec. IV.C, "Monte Carlo integration: details"): with C_j = sigma_j sqrt(N_j)
+ * and t_j the time of one integrand evaluation, the total sigma^2 * time is
+ * smallest for p_j = (C_j / sqrt(t_j)) / sum_l (C_l / sqrt(t_l)).  p_floor in
+ * [0, 1] raises every p_j below p_floor / n to that value, then renormalises
+ * (the paper gives extra
+ * attention to graphs with a large sigma_up/sigma_down, a quantity this
+ * library does not estimate, so a floor is its stabilisation).  Graphs with
+ * no finite positive weight get the floor only; if no graph has one, p is
+ * uniform.  Pure host function: sigma, N, t, p are n-element host arrays. */
+int ae_schedule_probabilities(const double *sigma, const uint64_t *N, const double *t, int n,
+                              double p_floor, double *p);
+
+/* The paper's integration controller: rounds of blocks_per_round blocks of
+ * block_size samples; the graph of every block is drawn at random (a host
+ * Philox stream of `seed`) with ae_schedule_probabilities(p_floor) from the
+ * samples processed so far; round 0 gives each graph one block.  One batched
+ * launch per round; each graph continues its own Philox counter, so its
+ * samples are exactly those of ae_integrate over [0, N_j).  per_graph (n_ids
+ * entries, nullable) holds the accumulated per-graph results (n = N_j). */
+int ae_integrate_adaptive(ae_ctx *ctx, const int *graph_ids, int n_ids, uint64_t block_size,
+                          int n_rounds, int blocks_per_round, double p_floor, uint64_t seed,
+                          double *value, double *sigma, ae_graph_result *per_graph);
+
+/* Two independent calculations (e.g. Calc 1 and Calc 2) combined as in
+ * Sec. V: per graph by inverse-variance weighting (v = sum w v / sum w,
+ * w = 1/sigma^2, sigma = (sum w)^-1/2), then summed with Eq. eq_sigma_sum.
+ * v1, s1, v2, s2: per-graph values (multiplicity included) and sigmas;
+ * v_out, s_out (nullable): combined per graph; total, total_sigma
+ * (nullable): the sum.  A graph with one sigma 0 takes that exact value. */
+int ae_combine_runs(const double *v1, const double *s1, const double *v2, const double *s2, int n,
+                    double *v_out, double *s_out, double *total, double *total_sigma);
 
 /* Per-sample dump for parity tests: samples first .. first+count-1 of
  * graph_id under `seed`.  z: count*M, log2g, I, K, y: count each (any may be

@@ -17,7 +17,8 @@ import numpy as np
 from .graphs import enumerate_graphs
 from .integrand import Integrand
 from .philox import uniforms
-from .sampler import Density, sample, exp2_tab
+from . import mrg32k3a
+from .sampler import CALC1, CALC2, Density, sample, exp2_tab
 
 
 def weight(I, lg):
@@ -28,16 +29,31 @@ def weight(I, lg):
 
 
 class GraphOracle:
-    def __init__(self, g, graph_id):
+    """calc=2: Philox4x32-10 and the Calc 2 constants; calc=1: MRG32k3a and
+    the Calc 1 constants (Sec. V)."""
+
+    def __init__(self, g, graph_id, calc=2, integrand=True):
         self.g = g
         self.gid = graph_id
-        self.dens = Density(g)
-        self.integrand = Integrand(g)
+        self.calc = calc
+        self.dens = Density(g, **(CALC1 if calc == 1 else CALC2))
+        self.integrand = Integrand(g) if integrand else None
+
+    def uniforms(self, idx, seed):
+        if self.calc == 1:
+            return mrg32k3a.uniforms(idx, self.gid, seed, self.dens.M)
+        return uniforms(idx, self.gid, seed, self.dens.M)
+
+    def points(self, first, count, seed=0):
+        """Sample points and densities only (no integrand)."""
+        idx = np.arange(first, first + count, dtype=np.uint64)
+        z, lg, comp = sample(self.dens, self.uniforms(idx, seed))
+        return dict(z=z, log2g=lg, comp=comp)
 
     def samples(self, first, count, seed=0):
         """Per-sample (z, log2g, I, K, y) for samples first..first+count-1."""
         idx = np.arange(first, first + count, dtype=np.uint64)
-        u = uniforms(idx, self.gid, seed, self.dens.M)
+        u = self.uniforms(idx, seed)
         z, lg, comp = sample(self.dens, u)
         I = np.empty(count)
         K = np.empty(count)

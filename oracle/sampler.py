@@ -45,6 +45,7 @@ import numpy as np
 C_BIGZ, C_BIGF, C_ADD = 0.256, 0.839, 0.786
 C_SUBI, C_SUBSE, C_SUBO = 0.2, 0.0, 0.2
 CALC2 = dict(C2=0.03, C3=0.01, C4=0.06, D=0.75)
+CALC1 = dict(C2=0.03, C3=0.035, C4=0.035, D=0.75)   # the constants of Calc 1 (Sec. V)
 
 INV_LN2 = 1.4426950408889634
 LN2 = 0.6931471805599453
@@ -254,6 +255,8 @@ def sample(dens, u):
         if sel.size == 0:
             continue
         deg, phi = dens.deg[k], dens.phi[k]
+        with np.errstate(divide="ignore"):
+            dinv = 1.0 / deg    # the empty and the full set (Deg 0) are never used
         T = np.full(sel.size, dens.full, dtype=np.int64)
         cur = np.zeros(sel.size)
         for l in range(M - 1):
@@ -275,7 +278,7 @@ def sample(dens, u):
             chosen = np.where(chosen < 0, last, chosen)
             lz[sel, chosen] = cur
             T = T ^ (np.int64(1) << chosen)
-            cur = cur + log2_tab(ut) / deg[T]
+            cur = cur + log2_tab(ut) * dinv[T]   # log2 t = log2(u) * (1/Deg)
         # the last remaining line
         lastj = np.zeros(sel.size, dtype=np.int64)
         for j in range(M):
@@ -285,7 +288,7 @@ def sample(dens, u):
         ssum = np.zeros(sel.size)
         for i in range(M):
             ssum = ssum + e[:, i]
-        zz[sel] = e / ssum[:, None]
+        zz[sel] = e * (1.0 / ssum)[:, None]
         lz[sel] = lz[sel] - log2_tab(ssum)[:, None]
     sel = np.nonzero(comp == 1)[0]
     if sel.size:
@@ -293,7 +296,7 @@ def sample(dens, u):
         ssum = np.zeros(sel.size)
         for i in range(M):
             ssum = ssum + L[:, i]
-        zz[sel] = L / ssum[:, None]
+        zz[sel] = L * (1.0 / ssum)[:, None]
         lz[sel] = log2_tab(L) - log2_tab(ssum)[:, None]
     return zz, log2_density(dens, lz), comp
 

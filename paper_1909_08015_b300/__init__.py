@@ -24,7 +24,8 @@ class AeOpts(ctypes.Structure):
                 ("D", ctypes.c_double), ("C_subI", ctypes.c_double), ("C_subSE", ctypes.c_double),
                 ("C_subO", ctypes.c_double), ("C_bigZ", ctypes.c_double), ("C_bigF", ctypes.c_double),
                 ("C_add", ctypes.c_double), ("deg_max", ctypes.c_double), ("dd_ratio", ctypes.c_double),
-                ("block_size", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("block_size", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("rng", ctypes.c_int)]
 
 
 class AeGraphMeta(ctypes.Structure):
@@ -66,6 +67,7 @@ def lib():
         vp = ctypes.c_void_p
         dp = P(ctypes.c_double)
         L.ae_default_opts.argtypes = [P(AeOpts)]
+        L.ae_calc1_opts.argtypes = [P(AeOpts)]
         L.ae_create.argtypes = [P(vp), ctypes.c_int, P(AeOpts)]
         L.ae_destroy.argtypes = [vp]
         L.ae_last_error.argtypes = [vp]
@@ -80,6 +82,11 @@ def lib():
                                            ctypes.c_uint64, dp, dp, P(AeGraphResult)]
         L.ae_integrate_range.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                          P(AeGraphResult)]
+        L.ae_integrate_adaptive.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_uint64, dp, dp,
+                                            P(AeGraphResult)]
+        L.ae_schedule_probabilities.argtypes = [dp, P(ctypes.c_uint64), dp, ctypes.c_int, ctypes.c_double, dp]
+        L.ae_combine_runs.argtypes = [dp, dp, dp, dp, ctypes.c_int, dp, dp, dp, dp]
         L.ae_allocate.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
                                   ctypes.c_uint64, ctypes.c_int, P(ctypes.c_uint64), dp]
         L.ae_train_proposal.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
@@ -107,6 +114,33 @@ def _ptr(a, ct=ctypes.c_double):
     return None if a is None else a.ctypes.data_as(ctypes.POINTER(ct))
 
 
+def schedule_probabilities(sigma, N, t, p_floor=0.0):
+    """Host: the paper's optimal sampling probabilities (ae_schedule_probabilities)."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    N = np.ascontiguousarray(N, dtype=np.uint64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    p = np.empty(len(sigma))
+    rc = lib().ae_schedule_probabilities(_ptr(sigma), _ptr(N, ctypes.c_uint64), _ptr(t), len(sigma),
+                                         ctypes.c_double(p_floor), _ptr(p))
+    if rc != 0:
+        raise AeError("ae_schedule_probabilities: AE_ERR_ARG")
+    return p
+
+
+def combine_runs(v1, s1, v2, s2):
+    """Host: two calculations combined graph by graph, then summed
+    (ae_combine_runs).  Returns (v, s, total, total_sigma)."""
+    a = [np.ascontiguousarray(x, dtype=np.float64) for x in (v1, s1, v2, s2)]
+    n = len(a[0])
+    v = np.empty(n); s = np.empty(n)
+    tot = ctypes.c_double(); ts = ctypes.c_double()
+    rc = lib().ae_combine_runs(_ptr(a[0]), _ptr(a[1]), _ptr(a[2]), _ptr(a[3]), n, _ptr(v), _ptr(s),
+                               ctypes.byref(tot), ctypes.byref(ts))
+    if rc != 0:
+        raise AeError("ae_combine_runs: AE_ERR_ARG")
+    return v, s, tot.value, ts.value
+
+
 def seeded_subset(n_total, k, seed=0):
     """k of n_total indices chosen by the library's Philox-driven shuffle."""
     out = np.empty(k, dtype=np.int32)
@@ -118,6 +152,13 @@ def seeded_subset(n_total, k, seed=0):
 def default_opts():
     o = AeOpts()
     lib().ae_default_opts(ctypes.byref(o))
+    return o
+
+
+def calc1_opts():
+    """The paper's Calc 1 settings: MRG32k3a, C3 = C4 = 0.035."""
+    o = AeOpts()
+    lib().ae_calc1_opts(ctypes.byref(o))
     return o
 
 
@@ -190,6 +231,17 @@ class Context:
         self._check(lib().ae_integrate_batched(self._h, _ptr(ids, ctypes.c_int), len(ids),
                                                _ptr(ns, ctypes.c_uint64), int(seed),
                                                ctypes.byref(v), ctypes.byref(s), res))
+        return v.value, s.value, [r.as_dict() for r in res]
+
+    def integrate_adaptive(self, ids, block_size, n_rounds, blocks_per_round, p_floor=0.1, seed=0):
+        """The paper's controller: blocks drawn with the optimal probabilities."""
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        v = ctypes.c_double()
+        s = ctypes.c_double()
+        res = (AeGraphResult * len(ids))()
+        self._check(lib().ae_integrate_adaptive(self._h, _ptr(ids, ctypes.c_int), len(ids), int(block_size),
+                                                int(n_rounds), int(blocks_per_round), float(p_floor), int(seed),
+                                                ctypes.byref(v), ctypes.byref(s), res))
         return v.value, s.value, [r.as_dict() for r in res]
 
     def integrate_range(self, gid, first, count, seed=0):

@@ -85,6 +85,10 @@ double ae_exp2(double x);
 double ae_log2t(double x);
 double ae_exp2t(double x);
 const double *ae_exp2_table();   // 2^(j/32), j = 0..31
+// host Philox4x32-10 (same definition as the device generator)
+void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1);
+// MRG32k3a jump matrices A1^(2^k), A2^(2^k), k = 0..159 (18 words per k)
+const uint32_t *mrg_jump_table();
 const double *ae_log2_table();   // log2(j/32), j = 24..48
 
 // ------------------------------------------------------------- tapes -----

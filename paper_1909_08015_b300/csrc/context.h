@@ -48,6 +48,7 @@ struct ae_ctx {
   bool own_stream = true;
   // scratch
   Partial *d_part = nullptr; size_t part_cap = 0;
+  uint32_t *d_mrg = nullptr;    // MRG32k3a jump table on the device (opts.rng == 1)
   unsigned long long *d_queue = nullptr; size_t queue_cap = 0;
   unsigned long long *d_qcount = nullptr;
   double *d_yq = nullptr;

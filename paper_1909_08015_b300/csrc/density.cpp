@@ -197,6 +197,36 @@ void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1) {
   }
 }
 
+// MRG32k3a (L'Ecuyer 1999): jump matrices A1^(2^k) mod m1, A2^(2^k) mod m2,
+// k = 0..159, row-major, 18 words per k (A1 then A2).  Exact 128-bit products.
+static void mat3_mul(const uint64_t *A, const uint64_t *B, uint64_t *C, uint64_t m) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      unsigned __int128 acc = 0;
+      for (int k = 0; k < 3; ++k) acc += (unsigned __int128)A[3 * i + k] * B[3 * k + j];
+      C[3 * i + j] = (uint64_t)(acc % m);
+    }
+}
+
+const uint32_t *mrg_jump_table() {
+  static const std::vector<uint32_t> t = [] {
+    const uint64_t m1 = 4294967087ull, m2 = 4294944443ull;
+    uint64_t P1[9] = {0, 1, 0, 0, 0, 1, m1 - 810728, 1403580, 0};
+    uint64_t P2[9] = {0, 1, 0, 0, 0, 1, m2 - 1370589, 0, 527612};
+    std::vector<uint32_t> v(160 * 18);
+    for (int k = 0; k < 160; ++k) {
+      for (int e = 0; e < 9; ++e) { v[18 * k + e] = (uint32_t)P1[e]; v[18 * k + 9 + e] = (uint32_t)P2[e]; }
+      uint64_t Q1[9], Q2[9];
+      mat3_mul(P1, P1, Q1, m1);
+      mat3_mul(P2, P2, Q2, m2);
+      std::copy(Q1, Q1 + 9, P1);
+      std::copy(Q2, Q2 + 9, P2);
+    }
+    return v;
+  }();
+  return t.data();
+}
+
 }  // namespace ae
 
 // Seeded subset of k indices out of n_total: Fisher-Yates driven by Philox

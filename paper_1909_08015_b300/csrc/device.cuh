@@ -28,6 +28,71 @@ __device__ __forceinline__ double u01(uint32_t w0, uint32_t w1) {
   return __dmul_rn(__dadd_rn(__dadd_rn(__dmul_rn(a, 67108864.0), b), 0.5), 1.1102230246251565e-16);
 }
 
+// two words -> uniform double in (0, 1) from 52 of their bits, built as the
+// double 1.m in [1, 2) and shifted: (2k + 1) 2^-53, two exact additions
+// (used where the draw need not match the host operation by operation)
+__device__ __forceinline__ double u01_bits(uint32_t w0, uint32_t w1) {
+  const double d = __hiloint2double((int)(0x3FF00000u | (w0 >> 12)), (int)((w0 << 20) | (w1 >> 12)));
+  return __dadd_rn(__dadd_rn(d, -1.0), 1.1102230246251565e-16);
+}
+
+// ---------------------------------------------------------- MRG32k3a ----
+// L'Ecuyer's combined multiple recursive generator (the generator of the
+// paper's Calc 1): x1_n = (1403580 x1_{n-2} - 810728 x1_{n-3}) mod m1,
+// x2_n = (527612 x2_{n-1} - 1370589 x2_{n-3}) mod m2, output (x1 - x2) mod m1.
+// Counter-based use: sample i of graph g under seed s starts at output
+// position s 2^96 + g 2^80 + 64 i of the stream from the state (12345 x 6),
+// reached by the jump matrices A^(2^k) (a host table, k = 0..159).
+constexpr uint64_t kMrgM1 = 4294967087ull, kMrgM2 = 4294944443ull;
+
+// x mod m for m = 2^32 - c (c < 2^15): fold the high word twice
+__device__ __forceinline__ uint64_t mrg_mod(uint64_t x, uint64_t m, uint64_t c) {
+  x = (x >> 32) * c + (x & 0xffffffffull);
+  x = (x >> 32) * c + (x & 0xffffffffull);
+  return x >= m ? x - m : x;
+}
+
+struct MrgState { uint64_t a[3], b[3]; };   // (x_{n-3}, x_{n-2}, x_{n-1}) of both components
+
+__device__ __forceinline__ void mrg_apply(const uint32_t *J, MrgState &s) {
+  uint64_t r[3];
+  for (int i = 0; i < 3; ++i) {
+    uint64_t acc = 0;
+    for (int k = 0; k < 3; ++k) acc += mrg_mod((uint64_t)__ldg(J + 3 * i + k) * s.a[k], kMrgM1, 209);
+    r[i] = mrg_mod(acc, kMrgM1, 209);
+  }
+  for (int i = 0; i < 3; ++i) s.a[i] = r[i];
+  for (int i = 0; i < 3; ++i) {
+    uint64_t acc = 0;
+    for (int k = 0; k < 3; ++k) acc += mrg_mod((uint64_t)__ldg(J + 9 + 3 * i + k) * s.b[k], kMrgM2, 22853);
+    r[i] = mrg_mod(acc, kMrgM2, 22853);
+  }
+  for (int i = 0; i < 3; ++i) s.b[i] = r[i];
+}
+
+// state at the start of sample idx of graph g under seed (jump over the set
+// bits of s 2^96 + g 2^80 + 64 idx)
+__device__ __forceinline__ MrgState mrg_start(const uint32_t *jump, uint64_t seed, uint32_t g, uint64_t idx) {
+  MrgState s = {{12345, 12345, 12345}, {12345, 12345, 12345}};
+  for (int k = 0; k < 64; ++k)
+    if (idx >> k & 1) mrg_apply(jump + 18 * (k + 6), s);
+  for (int k = 0; k < 16; ++k)
+    if (g >> k & 1) mrg_apply(jump + 18 * (k + 80), s);
+  for (int k = 0; k < 64; ++k)
+    if (seed >> k & 1) mrg_apply(jump + 18 * (k + 96), s);
+  return s;
+}
+
+__device__ __forceinline__ uint32_t mrg_next(MrgState &s) {
+  const uint64_t x1 = mrg_mod(mrg_mod(1403580ull * s.a[1], kMrgM1, 209) +
+                              mrg_mod((kMrgM1 - 810728ull) * s.a[0], kMrgM1, 209), kMrgM1, 209);
+  const uint64_t x2 = mrg_mod(mrg_mod(527612ull * s.b[2], kMrgM2, 22853) +
+                              mrg_mod((kMrgM2 - 1370589ull) * s.b[0], kMrgM2, 22853), kMrgM2, 22853);
+  s.a[0] = s.a[1]; s.a[1] = s.a[2]; s.a[2] = x1;
+  s.b[0] = s.b[1]; s.b[1] = s.b[2]; s.b[2] = x2;
+  return (uint32_t)(x1 >= x2 ? x1 - x2 : x1 + kMrgM1 - x2);
+}
+
 // ------------------------------------------------- log2 / exp2 (series) ---
 // The same sequence of IEEE operations as the host's ae_log2/ae_exp2.  The
 // series coefficients 1/(2i+1) and 1/k! are the exact double quotients of

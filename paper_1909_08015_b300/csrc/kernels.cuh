@@ -16,6 +16,7 @@ struct GraphDev {
   const double *deg;      // 3 * 2^M
   const double *phi;      // 3 * 2^M
   const double *wt;       // 3 * 2^M: phi/deg (same IEEE quotient as the walk's definition)
+  const double *dinv;     // 3 * 2^M: 1/deg
   const Ins *code;       // tape (32-byte instructions)
   const double *khi, *klo;
   int M, ntape, nslots, outI, outK;
@@ -29,8 +30,10 @@ struct GraphDev {
   const double *lD = nullptr;    // Deg_theta(T)
   const double *lD2 = nullptr;   // log2 Deg_theta(T)
   const double *lDi = nullptr;   // 1 / Deg_theta(T)
+  const double *lPc = nullptr;   // 2^M x 16: sum of P(j' | T) over j' <= j in T
   double beta = 0.1;             // weight of the plain density in the mixture
   double l2beta = 0, l2nbeta = 0;   // log2 beta, log2 (1 - beta)
+  const uint32_t *mrg = nullptr;    // MRG32k3a jump table (null: Philox4x32-10)
 };
 
 struct Partial {
@@ -39,20 +42,37 @@ struct Partial {
 };
 
 
+// The 2M uniforms of sample idx: draw block b gives u[2b] and u[2b+1] from
+// four generator words (Philox4x32-10: counter (idx lo, idx hi, graph, b),
+// key = seed; MRG32k3a: outputs 4b..4b+3 after the sample's start position).
+// exact: the host's word-to-double mapping; else the two-addition form.
+__device__ __forceinline__ void draw_uniforms(const GraphDev &G, uint64_t idx, uint64_t seed, double *u, bool fast) {
+  const int M = G.M;
+  if (G.mrg) {
+    MrgState st = mrg_start(G.mrg, seed, (uint32_t)G.graph_id, idx);
+    for (int b = 0; b < M; ++b) {
+      const uint32_t w0 = mrg_next(st), w1 = mrg_next(st), w2 = mrg_next(st), w3 = mrg_next(st);
+      u[2 * b] = fast ? u01_bits(w0, w1) : u01(w0, w1);
+      u[2 * b + 1] = fast ? u01_bits(w2, w3) : u01(w2, w3);
+    }
+    return;
+  }
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int b = 0; b < M; ++b) {
+    uint32_t c[4] = {(uint32_t)idx, (uint32_t)(idx >> 32), (uint32_t)G.graph_id, (uint32_t)b};
+    philox4x32_10(c, k0, k1);
+    u[2 * b] = fast ? u01_bits(c[0], c[1]) : u01(c[0], c[1]);
+    u[2 * b + 1] = fast ? u01_bits(c[2], c[3]) : u01(c[2], c[3]);
+  }
+}
+
 // Draw one sample: z (M), log2 z (M) and log2 g.  Same steps, same order of
 // IEEE operations as the host-side definition of the sampler.
 static __device__ void draw_sample(const GraphDev &G, uint64_t idx, uint64_t seed, double *z, double *lz,
                             double &log2g) {
   const int M = G.M;
   double u[2 * 14 + 2];
-  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  int nb = M;
-  for (int b = 0; b < nb; ++b) {
-    uint32_t c[4] = {(uint32_t)idx, (uint32_t)(idx >> 32), (uint32_t)G.graph_id, (uint32_t)b};
-    philox4x32_10(c, k0, k1);
-    u[2 * b] = u01(c[0], c[1]);
-    u[2 * b + 1] = u01(c[2], c[3]);
-  }
+  draw_uniforms(G, idx, seed, u, false);
   double pick = u[0];
   int comp;
   if (pick < G.C1) comp = 0;
@@ -65,6 +85,7 @@ static __device__ void draw_sample(const GraphDev &G, uint64_t idx, uint64_t see
     const double *deg = G.deg + ((size_t)k << M);
     const double *phi = G.phi + ((size_t)k << M);
     const double *wt = G.wt + ((size_t)k << M);
+    const double *dinv = G.dinv + ((size_t)k << M);
     uint32_t T = full;
     double cur = 0.0;
     for (int l = 0; l < M - 1; ++l) {
@@ -82,21 +103,21 @@ static __device__ void draw_sample(const GraphDev &G, uint64_t idx, uint64_t see
       if (chosen < 0) chosen = last;
       lz[chosen] = cur;
       T ^= 1u << chosen;
-      cur = __dadd_rn(cur, __ddiv_rn(dlog2t(ut), __ldg(deg + T)));
+      cur = __dadd_rn(cur, __dmul_rn(dlog2t(ut), __ldg(dinv + T)));   // log2 t = log2(u) (1/Deg)
     }
     int lastj = __ffs(T) - 1;
     lz[lastj] = cur;
     double ssum = 0.0;
     for (int i = 0; i < M; ++i) { z[i] = dexp2t(lz[i]); ssum = __dadd_rn(ssum, z[i]); }
-    double ls = dlog2t(ssum);
-    for (int i = 0; i < M; ++i) { z[i] = __ddiv_rn(z[i], ssum); lz[i] = __dadd_rn(lz[i], -ls); }
+    double ls = dlog2t(ssum), rs = __ddiv_rn(1.0, ssum);
+    for (int i = 0; i < M; ++i) { z[i] = __dmul_rn(z[i], rs); lz[i] = __dadd_rn(lz[i], -ls); }
   } else {
     double ssum = 0.0;
     for (int i = 0; i < M; ++i) { z[i] = -dlog2t(u[1 + i]); ssum = __dadd_rn(ssum, z[i]); }
-    double ls = dlog2t(ssum);
+    double ls = dlog2t(ssum), rs = __ddiv_rn(1.0, ssum);
     for (int i = 0; i < M; ++i) {
       lz[i] = __dadd_rn(dlog2t(z[i]), -ls);
-      z[i] = __ddiv_rn(z[i], ssum);
+      z[i] = __dmul_rn(z[i], rs);
     }
   }
   // density: sector order = descending log2 z, ties by lower index
@@ -152,13 +173,7 @@ __device__ __forceinline__ double weight(double I, double lg) {
 static __device__ void draw_mix(const GraphDev &G, uint64_t idx, uint64_t seed, double *z, double *lz, double &log2q) {
   const int M = G.M;
   double u[2 * 14 + 2];
-  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  for (int b = 0; b < M; ++b) {
-    uint32_t c[4] = {(uint32_t)idx, (uint32_t)(idx >> 32), (uint32_t)G.graph_id, (uint32_t)b};
-    philox4x32_10(c, k0, k1);
-    u[2 * b] = u01(c[0], c[1]);
-    u[2 * b + 1] = u01(c[2], c[3]);
-  }
+  draw_uniforms(G, idx, seed, u, true);
   const uint32_t full = (1u << M) - 1;
   bool plain = u[0] < G.beta;
   if (plain) {
@@ -198,16 +213,14 @@ static __device__ void draw_mix(const GraphDev &G, uint64_t idx, uint64_t seed, 
     uint32_t T = full;
     double cur = 0.0;
     for (int l = 0; l < M - 1; ++l) {
+      // first j in T whose cumulative probability exceeds the uniform (the
+      // cumulative sums are tabulated in the order of j)
       double uc = u[1 + 2 * l];
-      double acc = 0.0;
-      int chosen = -1, last = 0;
+      int chosen = 31 - __clz(T);   // the last j in T, if rounding leaves uc above every sum
       for (int j = 0; j < M; ++j) {
         if (!(T >> j & 1)) continue;
-        acc += __ldg(G.lP + (size_t)T * 16 + j);
-        if (chosen < 0 && uc < acc) chosen = j;
-        last = j;
+        if (uc < __ldg(G.lPc + (size_t)T * 16 + j)) { chosen = j; break; }
       }
-      if (chosen < 0) chosen = last;
       lz[chosen] = cur;
       T ^= 1u << chosen;
       cur += log2(u[2 + 2 * l]) * __ldg(G.lDi + T);

@@ -166,10 +166,12 @@ __global__ void mlp_fwd_kernel(int M, const __nv_bfloat16 *Wbf, const float *P, 
 
 // Tables of the learned walk for every state T.
 //   lp[T*16+j]  = P(j | T) (0 for j not in T), lp2 = log2 of it;
+//   lpc[T*16+j] = sum of P(j' | T) over j' <= j (in the order of j: the
+//   sampler's cumulative comparison);
 //   ld[T] = Deg_theta(T), ld2 = log2 Deg_theta(T), ldi = 1 / Deg_theta(T)
 //   (proper nonempty T).
 __global__ void tables_kernel(int M, const float *O, const double *deg, const double *wplain, double *lp,
-                              double *lp2, double *ld, double *ld2, double *ldi) {
+                              double *lp2, double *lpc, double *ld, double *ld2, double *ldi) {
   uint32_t S = 1u << M, full = S - 1;
   for (uint32_t T = blockIdx.x * blockDim.x + threadIdx.x; T < S; T += gridDim.x * blockDim.x) {
     const float *o = O + (size_t)T * OUT;
@@ -188,10 +190,13 @@ __global__ void tables_kernel(int M, const float *O, const double *deg, const do
     for (int j = 0; j < 16; ++j)
       if (l[j] > -1e299) se += exp(l[j] - mx);
     double lse = mx + log(se);
+    double cum = 0.0;
     for (int j = 0; j < 16; ++j) {
       bool in = l[j] > -1e299;
       lp[(size_t)T * 16 + j] = in ? exp(l[j] - lse) : 0.0;
       lp2[(size_t)T * 16 + j] = in ? (l[j] - lse) * 1.4426950408889634 : 0.0;
+      if (in) cum += lp[(size_t)T * 16 + j];
+      lpc[(size_t)T * 16 + j] = cum;
     }
     if (T != 0 && T != full) {
       double dth = deg[T] * exp(KAP * tanh((double)o[15] / KAP));
@@ -447,7 +452,7 @@ __global__ void to_bf16_kernel(const float *src, __nv_bfloat16 *dst, int n) {
 struct Net {
   __nv_bfloat16 *Wbf, *H1, *H2, *H3;
   float *P, *master, *m, *v, *grad, *O, *dO, *part;
-  double *lp, *lp2, *ld, *ld2, *ldi, *deg, *wplain, *wsum_part, *loss_part;
+  double *lp, *lp2, *lpc, *ld, *ld2, *ldi, *deg, *wplain, *wsum_part, *loss_part;
   unsigned long long *acc;
   int M;
   int ntiles;
@@ -458,7 +463,7 @@ size_t net_bytes(int M) {
   size_t nt = (S + 63) / 64;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   return al(NPARAM * 2) + 3 * al(S * HID * 2) + al(NPARAM * 4) * 5 + al(S * OUT * 4) * 2 + al(nt * NPARAM * 4) +
-         al(S * 16 * 8) * 2 + al(S * 8) * 5 + al(1024 * 8) * 2 + al(S * 16 * 8);
+         al(S * 16 * 8) * 3 + al(S * 8) * 5 + al(1024 * 8) * 2 + al(S * 16 * 8);
 }
 
 void carve(Net &n, void *mem, int M) {
@@ -485,6 +490,7 @@ void carve(Net &n, void *mem, int M) {
   n.ld = (double *)take(S * 8);
   n.ld2 = (double *)take(S * 8);
   n.ldi = (double *)take(S * 8);
+  n.lpc = (double *)take(S * 16 * 8);
   n.deg = (double *)take(S * 8);
   n.wplain = (double *)take(S * 8);
   n.wsum_part = (double *)take(1024 * 8);
@@ -496,8 +502,8 @@ void carve(Net &n, void *mem, int M) {
 cudaError_t net_forward(Net &n, cudaStream_t st) {
   size_t S = (size_t)1 << n.M;
   mlp_fwd_kernel<<<n.ntiles, 128, 0, st>>>(n.M, n.Wbf, n.P, n.H1, n.H2, n.H3, n.O);
-  tables_kernel<<<(unsigned)((S + 127) / 128), 128, 0, st>>>(n.M, n.O, n.deg, n.wplain, n.lp, n.lp2, n.ld, n.ld2,
-                                                             n.ldi);
+  tables_kernel<<<(unsigned)((S + 127) / 128), 128, 0, st>>>(n.M, n.O, n.deg, n.wplain, n.lp, n.lp2, n.lpc, n.ld,
+                                                             n.ld2, n.ldi);
   return cudaGetLastError();
 }
 
@@ -554,6 +560,7 @@ static void attach_tables(LoadedGraph &lg, Net &n) {
   lg.dev.lD = n.ld;
   lg.dev.lD2 = n.ld2;
   lg.dev.lDi = n.ldi;
+  lg.dev.lPc = n.lpc;
 }
 
 extern "C" int ae_train_proposal(ae_ctx *c, int gid, uint64_t n_train, uint64_t seed, int steps, double lr,

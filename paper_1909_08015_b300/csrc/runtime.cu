@@ -372,6 +372,13 @@ extern "C" void ae_default_opts(ae_opts *o) {
   o->block_size = 0;
   o->ctas_per_sm = 0;
   o->stream = nullptr;
+  o->rng = 0;
+}
+
+extern "C" void ae_calc1_opts(ae_opts *o) {
+  ae_default_opts(o);
+  o->C3 = 0.035; o->C4 = 0.035;
+  o->rng = 1;
 }
 
 extern "C" int ae_create(ae_ctx **out, int dev, const ae_opts *opts) {
@@ -380,6 +387,7 @@ extern "C" int ae_create(ae_ctx **out, int dev, const ae_opts *opts) {
   ae_ctx *c = new (std::nothrow) ae_ctx();
   if (!c) return AE_ERR_OOM;
   if (opts) c->opts = *opts; else ae_default_opts(&c->opts);
+  if (c->opts.rng != 0 && c->opts.rng != 1) { delete c; return AE_ERR_ARG; }
   c->device = dev;
   if (dev >= 0) {
     cudaError_t e = cudaSetDevice(dev);
@@ -423,6 +431,7 @@ static void free_device(ae_ctx *c) {
 extern "C" void ae_destroy(ae_ctx *c) {
   if (!c) return;
   free_device(c);
+  if (c->d_mrg) cudaFree(c->d_mrg);
   if (c->stream && c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -498,24 +507,32 @@ static int load_impl(ae_ctx *c, int loops, const int *subset, int n_subset, int 
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     for (auto &lg : c->graphs) {
       size_t T = (size_t)1 << lg.g.M();
-      bytes += al(3 * T * 8) * 3 + al(lg.tape.khi.size() * 8) * 2 + al(lg.tape.code.size() * sizeof(Ins));
+      bytes += al(3 * T * 8) * 4 + al(lg.tape.khi.size() * 8) * 2 + al(lg.tape.code.size() * sizeof(Ins));
     }
     CUDA_TRY(c, cudaMalloc(&c->arena, bytes));
     c->arena_bytes = bytes;
+    if (c->opts.rng == 1 && !c->d_mrg) {
+      CUDA_TRY(c, cudaMalloc(&c->d_mrg, 160 * 18 * sizeof(uint32_t)));
+      CUDA_TRY(c, cudaMemcpy(c->d_mrg, mrg_jump_table(), 160 * 18 * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    }
     char *p = (char *)c->arena;
     for (size_t gi = 0; gi < c->graphs.size(); ++gi) {
       LoadedGraph &lg = c->graphs[gi];
       size_t T = (size_t)1 << lg.g.M();
-      std::vector<double> deg(3 * T), phi(3 * T), wt(3 * T, 0.0);
+      std::vector<double> deg(3 * T), phi(3 * T), wt(3 * T, 0.0), dinv(3 * T, 0.0);
       for (int k = 0; k < 3; ++k) {
         std::copy(lg.dens.deg[k].begin(), lg.dens.deg[k].end(), deg.begin() + k * T);
         std::copy(lg.dens.phi[k].begin(), lg.dens.phi[k].end(), phi.begin() + k * T);
-        for (size_t R = 1; R + 1 < T; ++R) wt[k * T + R] = lg.dens.phi[k][R] / lg.dens.deg[k][R];
+        for (size_t R = 1; R + 1 < T; ++R) {
+          wt[k * T + R] = lg.dens.phi[k][R] / lg.dens.deg[k][R];
+          dinv[k * T + R] = 1.0 / lg.dens.deg[k][R];
+        }
       }
       GraphDev &G = lg.dev;
       G.deg = (double *)p; CUDA_TRY(c, cudaMemcpy(p, deg.data(), 3 * T * 8, cudaMemcpyHostToDevice)); p += al(3 * T * 8);
       G.phi = (double *)p; CUDA_TRY(c, cudaMemcpy(p, phi.data(), 3 * T * 8, cudaMemcpyHostToDevice)); p += al(3 * T * 8);
       G.wt = (double *)p; CUDA_TRY(c, cudaMemcpy(p, wt.data(), 3 * T * 8, cudaMemcpyHostToDevice)); p += al(3 * T * 8);
+      G.dinv = (double *)p; CUDA_TRY(c, cudaMemcpy(p, dinv.data(), 3 * T * 8, cudaMemcpyHostToDevice)); p += al(3 * T * 8);
       size_t nk = lg.tape.khi.size();
       G.khi = (double *)p; if (nk) CUDA_TRY(c, cudaMemcpy(p, lg.tape.khi.data(), nk * 8, cudaMemcpyHostToDevice)); p += al(nk * 8);
       G.klo = (double *)p; if (nk) CUDA_TRY(c, cudaMemcpy(p, lg.tape.klo.data(), nk * 8, cudaMemcpyHostToDevice)); p += al(nk * 8);
@@ -523,7 +540,8 @@ static int load_impl(ae_ctx *c, int loops, const int *subset, int n_subset, int 
       CUDA_TRY(c, cudaMemcpy(p, lg.tape.code.data(), lg.tape.code.size() * sizeof(Ins), cudaMemcpyHostToDevice));
       p += al(lg.tape.code.size() * sizeof(Ins));
       G.M = lg.g.M(); G.ntape = (int)lg.tape.code.size(); G.nslots = lg.tape.nslots;
-      G.outI = lg.tape.out_I; G.outK = lg.tape.out_K; G.graph_id = canon[gi];   // Philox stream of the graph
+      G.outI = lg.tape.out_I; G.outK = lg.tape.out_K; G.graph_id = canon[gi];   // random stream of the graph
+      G.mrg = c->opts.rng == 1 ? c->d_mrg : nullptr;
       lg.canonical_id = canon[gi];
       G.C1 = lg.dens.C[0]; G.C2 = lg.dens.C[1]; G.C3 = lg.dens.C[2]; G.C4 = lg.dens.C[3];
       G.log2_fact = lg.dens.log2_fact;
@@ -1144,6 +1162,101 @@ extern "C" int ae_integrate_batched(ae_ctx *c, const int *ids, int n_ids, const 
 // C_j / sqrt(t_j) (the paper's optimum p_j), mode 1 proportional to the
 // variance estimate sigma_j^2.  Integer counts by largest remainder, at
 // least min(1024, n_total / n_ids) each.
+// The paper's integration controller (Sec. IV.C): blocks of samples whose
+// graphs are drawn with the optimal probabilities of the samples so far.
+extern "C" int ae_integrate_adaptive(ae_ctx *c, const int *ids, int n_ids, uint64_t block, int n_rounds,
+                                     int blocks_per_round, double p_floor, uint64_t seed, double *value,
+                                     double *sigma, ae_graph_result *per) {
+  if (!c) return AE_ERR_ARG;
+  if (c->device < 0) return fail(c, AE_ERR_NODEV, "integration needs a CUDA device");
+  if (c->graphs.empty()) return fail(c, AE_ERR_STATE, "no graphs loaded");
+  if (!ids || n_ids <= 0 || block == 0 || n_rounds < 1 || blocks_per_round < 1 || !(p_floor >= 0) || p_floor > 1)
+    return fail(c, AE_ERR_ARG, "need graphs, block_size > 0, n_rounds >= 1, blocks_per_round >= 1, 0 <= p_floor <= 1");
+  for (int i = 0; i < n_ids; ++i)
+    if (ids[i] < 0 || ids[i] >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  const size_t G = (size_t)n_ids;
+  std::vector<int> vid(ids, ids + n_ids);
+  std::vector<uint64_t> Nj(G, 0);
+  std::vector<double> sy(G, 0), syl(G, 0), sy2(G, 0), sy2l(G, 0), sa(G, 0), sal(G, 0), mx(G, 0), secs(G, 0),
+      ksecs(G, 0);
+  std::vector<uint64_t> ndd(G, 0), nbad(G, 0), launches(G, 0), d2h(G, 0), h2d(G, 0);
+  std::vector<double> tj(G), sig(G), p(G);
+  for (size_t i = 0; i < G; ++i) tj[i] = c->graphs[vid[i]].tape.flops + 150.0 * c->graphs[vid[i]].g.M();
+  BatchTune tune;
+  int rc = autotune_batched(c, vid, tune);
+  if (rc) return rc;
+  uint64_t draw = 0;   // counter of the block-draw stream
+  for (int r = 0; r < n_rounds; ++r) {
+    std::vector<uint64_t> nb(G, 0);
+    if (r == 0) {
+      for (size_t i = 0; i < G; ++i) nb[i] = 1;
+    } else {
+      for (size_t i = 0; i < G; ++i) {
+        double N = (double)Nj[i], var = (sy2[i] + sy2l[i]) / (N * N) - (sy[i] + syl[i]) * (sy[i] + syl[i]) / (N * N * N);
+        sig[i] = c->graphs[vid[i]].g.mult * std::sqrt(std::max(var, 0.0));
+      }
+      ae_schedule_probabilities(sig.data(), Nj.data(), tj.data(), n_ids, p_floor, p.data());
+      std::vector<double> cdf(G);
+      double acc = 0;
+      for (size_t i = 0; i < G; ++i) { acc += p[i]; cdf[i] = acc; }
+      for (int b = 0; b < blocks_per_round; ++b, ++draw) {
+        // one uniform per block: Philox of (draw index, 0, 0x5c4ed, 0) under seed
+        uint32_t w[4] = {(uint32_t)draw, (uint32_t)(draw >> 32), 0x5c4edu, 0u};
+        ae::philox_host(w, (uint32_t)seed, (uint32_t)(seed >> 32));
+        double u = (((double)(w[0] >> 5)) * 67108864.0 + (double)(w[1] >> 6) + 0.5) * 1.1102230246251565e-16;
+        size_t j = (size_t)(std::lower_bound(cdf.begin(), cdf.end(), u * acc) - cdf.begin());
+        if (j >= G) j = G - 1;
+        nb[j] += 1;
+      }
+    }
+    std::vector<int> rid;
+    std::vector<uint64_t> rn, rf;
+    std::vector<size_t> pos;
+    for (size_t i = 0; i < G; ++i)
+      if (nb[i]) { rid.push_back(vid[i]); rn.push_back(nb[i] * block); rf.push_back(Nj[i]); pos.push_back(i); }
+    std::vector<ae_graph_result> res;
+    double s_round = 0;
+    rc = run_batched(c, rid, rn, rf, seed, tune.block, tune.chunk, true, res, &s_round);
+    if (rc) return rc;
+    for (size_t k = 0; k < pos.size(); ++k) {
+      size_t i = pos[k];
+      const ae_graph_result &q = res[k];
+      host_dd_add(sy[i], syl[i], q.sum_y);
+      host_dd_add(sy2[i], sy2l[i], q.sum_y2);
+      host_dd_add(sa[i], sal[i], q.mean_abs * (double)q.n);
+      mx[i] = std::max(mx[i], q.max_y2);
+      Nj[i] += q.n; ndd[i] += q.n_dd; nbad[i] += q.n_nonfinite;
+      secs[i] += q.seconds; ksecs[i] += q.kernel_seconds;
+      launches[i] += q.launches; d2h[i] += q.d2h_bytes; h2d[i] += q.h2d_bytes;
+    }
+  }
+  double tot = 0, var = 0;
+  for (size_t i = 0; i < G; ++i) {
+    ae_graph_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.sum_y = sy[i] + syl[i]; r.sum_y2 = sy2[i] + sy2l[i];
+    r.n = Nj[i]; r.n_dd = ndd[i]; r.n_nonfinite = nbad[i];
+    double N = (double)r.n;
+    r.mean = r.sum_y / N;
+    double v1 = r.sum_y2 / (N * N) - r.sum_y * r.sum_y / (N * N * N);
+    r.sigma1 = v1 > 0 ? std::sqrt(v1) : 0.0;
+    r.mean_abs = (sa[i] + sal[i]) / N;
+    r.max_y2 = mx[i];
+    int mult = c->graphs[vid[i]].g.mult;
+    r.value = mult * r.mean;
+    r.sigma = mult * r.sigma1;
+    r.seconds = secs[i]; r.kernel_seconds = ksecs[i]; r.launches = launches[i];
+    r.d2h_bytes = d2h[i]; r.h2d_bytes = h2d[i];
+    tot += r.value;
+    var += r.sigma * r.sigma;
+    if (per) per[i] = r;
+  }
+  if (value) *value = tot;
+  if (sigma) *sigma = std::sqrt(var);
+  return AE_OK;
+}
+
 extern "C" int ae_allocate(ae_ctx *c, const int *ids, int n_ids, uint64_t n_pilot, uint64_t n_total, uint64_t seed,
                            int mode, uint64_t *n_out, double *sigma_out) {
   if (!c || !ids || !n_out || n_ids <= 0) return AE_ERR_ARG;

@@ -71,3 +71,24 @@ def test_resume_by_counter_range(ctx):
     assert abs(a["sum_y2"] + b["sum_y2"] - whole["sum_y2"]) <= 1e-12 * whole["sum_y2"]
     _, _, per = ctx.integrate([3], 400000, seed=4)
     assert abs(per[0]["sum_y"] - whole["sum_y"]) <= 1e-9 * abs(whole["sum_y"])
+
+
+def test_adaptive_controller(ctx):
+    """The paper's controller on the 2-loop set: closed form within 3 sigma,
+    deterministic, each graph's samples exactly those of integrate_range over
+    [0, N_j), and the graph with the largest C_j / sqrt(t_j) sampled most."""
+    import math
+    ctx.load_graphs(2)
+    A4 = -0.328478965579193 - (119.0 / 36.0 - math.pi ** 2 / 3.0)
+    v, s, per = ctx.integrate_adaptive([0, 1, 2, 3], 8192, 12, 96, p_floor=0.1, seed=21)
+    assert abs(v - A4) < 3 * s, (v, s)
+    total = sum(p["n"] for p in per)
+    assert total == 8192 * (4 + 11 * 96)
+    v2, s2, per2 = ctx.integrate_adaptive([0, 1, 2, 3], 8192, 12, 96, p_floor=0.1, seed=21)
+    assert v2 == v and s2 == s
+    for gi in (0, 3):
+        r = ctx.integrate_range(gi, 0, per[gi]["n"], seed=21)
+        assert abs(r["sum_y"] - per[gi]["sum_y"]) <= 1e-10 * abs(r["sum_y"])
+    info = [ctx.graph_info(i) for i in range(4)]
+    w = [per[i]["sigma"] * math.sqrt(per[i]["n"]) / math.sqrt(info[i]["flops"]) for i in range(4)]
+    assert int(np.argmax([p["n"] for p in per])) == int(np.argmax(w))

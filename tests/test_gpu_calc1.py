@@ -1,0 +1,52 @@
+"""The paper's second calculation (Sec. V, Calc 1): MRG32k3a and C3 = C4 =
+0.035.  Sample points and densities bit for bit against the oracle (which
+has its own MRG32k3a), the integrand within the parity tolerance, the 2-loop
+closed form within 3 sigma, and the two calculations combined graph by
+graph."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1909_08015_b300 as ae
+from oracle.estimate import GraphOracle
+from oracle.graphs import enumerate_graphs
+
+pytestmark = pytest.mark.gpu
+
+A4_NO_LEPTON_LOOPS = -0.328478965579193 - (119.0 / 36.0 - math.pi ** 2 / 3.0)
+
+
+@pytest.fixture(scope="module")
+def ctx1():
+    c = ae.Context(0, ae.calc1_opts())
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("n,ids,count", [(2, [0, 1, 2, 3], 128), (3, [5, 20], 32)])
+def test_calc1_samples_match_oracle(ctx1, n, ids, count):
+    ctx1.load_graphs(n)
+    gs = enumerate_graphs(n)
+    for gi in ids:
+        ref = GraphOracle(gs[gi], gi, calc=1).samples(0, count, seed=4)
+        d = ctx1.eval_samples(gi, 0, count, seed=4)
+        assert np.array_equal(d["z"], ref["z"])
+        assert np.array_equal(d["log2g"], ref["log2g"])
+        keep = ref["K"] <= 1e8 * np.abs(ref["I"])
+        err = np.abs(d["I"] - ref["I"])
+        assert np.all(err[keep] <= 1e-10 * np.abs(ref["I"][keep]) + 2.0 ** -40 * ref["K"][keep])
+
+
+def test_calc1_value_and_combination(ctx1):
+    ctx1.load_graphs(2)
+    v1, s1, p1 = ctx1.integrate([0, 1, 2, 3], 10 ** 7, seed=0)
+    assert abs(v1 - A4_NO_LEPTON_LOOPS) < 3 * s1, (v1, s1)
+    c2 = ae.Context(0)
+    c2.load_graphs(2)
+    v2, s2, p2 = c2.integrate([0, 1, 2, 3], 10 ** 7, seed=0)
+    c2.close()
+    _, _, tot, ts = ae.combine_runs([p["value"] for p in p1], [p["sigma"] for p in p1],
+                                    [p["value"] for p in p2], [p["sigma"] for p in p2])
+    assert ts < min(s1, s2)
+    assert abs(tot - A4_NO_LEPTON_LOOPS) < 3 * ts, (tot, ts)
