@@ -28,6 +28,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MC samples/s and 1/(σ²·s) per graph set, learned+batched vs plain pdf, 1 B300"
 
+# DRAM bytes (read + write) per batched_kernel launch in the default
+# workload's timed region: ncu dram__bytes_read.sum + dram__bytes_write.sum,
+# mean of the two launches of one step (profiles/batched_kernel_3loop_learned_set.md).
+# Applies to the default workload and the kernel revision it was taken on.
+TRAFFIC_DEFAULT_BYTES = 6.39e8
+
 
 # FP64 operations of the table-driven elementary functions (one division
 # counted as one operation): exp2 = range reduction (10) + degree-7 Horner
@@ -338,6 +344,9 @@ def main():
                          "after per-graph setup, %.1f s on %d processes)" % (cids, args.loops, args.oracle_samples,
                                                                              wall, cores)}
     isps = 1.0 / (sigma ** 2 * t_dev) if sigma > 0 else None
+    default_workload = (args.loops == 3 and args.graphs == 0 and args.samples == 1 << 24 and learned
+                        and not args.no_alloc)
+    traffic = TRAFFIC_DEFAULT_BYTES if default_workload else None
     line = {
         "metric": METRIC, "value": rate, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
@@ -358,7 +367,7 @@ def main():
         "allocation": {"min": min(alloc), "max": max(alloc), "mode": "pilot, n_j ~ sigma_j/sqrt(t_j)"}
         if learned and not args.no_alloc else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "frac": achieved / peak if peak else None, "traffic": traffic,
                      "kernel": ("batched_kernel" if learned else "integrate_kernel") + " (sampler + FP64 tape)",
                      "peak_source": "measured: own DFMA probe (ae_fp64_peak)"},
         "e2e": {"value": total / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
