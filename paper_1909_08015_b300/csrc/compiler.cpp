@@ -27,6 +27,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <set>
 #include <climits>
 #include <numeric>
 #include <stdexcept>
@@ -949,25 +950,13 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
       term_assigns[ti].push_back(as);
     }
   }
-  // ---- phase 2: per factor graph, graph functions then its numerators -----
+  // ---- phases 2 and 3: factor graphs, and each term as soon as its factors
+  // are there (so the numerator values of finished terms die early and the
+  // slot file stays small) ----------------------------------------------------
   std::map<std::string, std::vector<int>> numv;   // nkey -> j-vector values
   std::map<std::string, int> Vval;                // gkey -> V value
-  for (auto &kv : by_graph) {
-    const Need &n0 = needs[kv.second[0]];
-    Factor f = make_factor(g, subs, n0.S, n0.ch);
-    bool need_b = kv.first.back() == 'b';
-    FactorVals fv = emit_graph_functions(B, f, need_b);
-    Vval[kv.first] = fv.V;
-    for (const std::string &nk : kv.second) {
-      const Need &nd = needs[nk];
-      std::vector<Mono> ms = expand_factor(f, nd.chan, nd.child_chan, tm);
-      nmono += (int)ms.size();
-      numv[nk] = emit_numerator(B, fv, ms);
-    }
-  }
-  // ---- phase 3: terms ---------------------------------------------------------
   int Itot = B.zero(), Ktot = B.zero();
-  for (size_t ti = 0; ti < terms.size(); ++ti) {
+  auto emit_term = [&](size_t ti) {
     int termval = B.zero();
     const std::vector<Assign> &asg = term_assigns[ti];
     // W = sum of the factors' V (same factor graphs for every assignment)
@@ -1009,6 +998,53 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
     }
     B.fmac(Itot, termval, B.konst((double)terms[ti].sign));
     B.addabs(Ktot, termval);
+  };
+  std::vector<std::set<std::string>> term_g(terms.size());
+  for (size_t ti = 0; ti < terms.size(); ++ti)
+    for (const Assign &as : term_assigns[ti]) term_g[ti].insert(as.gkeys.begin(), as.gkeys.end());
+  std::set<std::string> done_g;
+  std::vector<char> term_done(terms.size(), 0);
+  std::vector<std::string> left;
+  for (auto &kv : by_graph) left.push_back(kv.first);
+  while (!left.empty()) {
+    // next factor graph: the one that completes most terms, then the one
+    // needed by most unfinished terms (first in key order on ties)
+    size_t pick = 0;
+    int best_c = -1, best_u = -1;
+    for (size_t q = 0; q < left.size(); ++q) {
+      int c = 0, u = 0;
+      for (size_t ti = 0; ti < terms.size(); ++ti) {
+        if (term_done[ti] || !term_g[ti].count(left[q])) continue;
+        ++u;
+        bool complete = true;
+        for (const std::string &gk : term_g[ti])
+          if (gk != left[q] && !done_g.count(gk)) { complete = false; break; }
+        if (complete) ++c;
+      }
+      if (c > best_c || (c == best_c && u > best_u)) { best_c = c; best_u = u; pick = q; }
+    }
+    const std::string gkey = left[pick];
+    left.erase(left.begin() + pick);
+    const std::vector<std::string> &nks = by_graph[gkey];
+    const Need &n0 = needs[nks[0]];
+    Factor f = make_factor(g, subs, n0.S, n0.ch);
+    bool need_b = gkey.back() == 'b';
+    FactorVals fv = emit_graph_functions(B, f, need_b);
+    Vval[gkey] = fv.V;
+    for (const std::string &nk : nks) {
+      const Need &nd = needs[nk];
+      std::vector<Mono> ms = expand_factor(f, nd.chan, nd.child_chan, tm);
+      nmono += (int)ms.size();
+      numv[nk] = emit_numerator(B, fv, ms);
+    }
+    done_g.insert(gkey);
+    for (size_t ti = 0; ti < terms.size(); ++ti) {
+      if (term_done[ti]) continue;
+      bool complete = true;
+      for (const std::string &gk : term_g[ti])
+        if (!done_g.count(gk)) { complete = false; break; }
+      if (complete) { emit_term(ti); term_done[ti] = 1; }
+    }
   }
   int nfac = (int)by_graph.size();
   // prefactor z_e 4^-n (-1)^n
