@@ -195,7 +195,9 @@ def main():
     ap.add_argument("--samples", type=int, default=1 << 24, help="samples per graph per step")
     ap.add_argument("--train", type=int, default=1 << 20, help="training samples per graph")
     ap.add_argument("--train-steps", type=int, default=150)
-    ap.add_argument("--plain", action="store_true", help="time the plain density only (no learned proposal)")
+    ap.add_argument("--plain", action="store_true", help="time the plain density only, one launch per graph")
+    ap.add_argument("--plain-batched", action="store_true",
+                    help="time the plain density in the batched persistent launch with pilot allocation")
     ap.add_argument("--no-alloc", action="store_true", help="equal samples per graph in the learned+batched form")
     ap.add_argument("--oracle-samples", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -234,7 +236,8 @@ def main():
     info = [ctx.graph_info(i) for i in ids]
     M = info[0]["M"]
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MB > L2
-    learned = not args.plain
+    learned = not args.plain and not args.plain_batched
+    batched = not args.plain
     train_s = 0.0
     if learned:
         t0 = time.perf_counter()
@@ -247,7 +250,7 @@ def main():
     # form: the same total budget per step, split n_j ~ sigma_j / sqrt(t_j)
     alloc = [args.samples] * ngr
     pilot_s = 0.0
-    if learned and not args.no_alloc:
+    if batched and not args.no_alloc:
         t0 = time.perf_counter()
         n_j, _ = ctx.allocate(ids, 1 << 18, args.samples * ngr, seed=99 + rank, mode=0)
         alloc = [int(x) for x in n_j]
@@ -255,7 +258,7 @@ def main():
         pilot_s = time.perf_counter() - t0
 
     def step(seed):
-        if learned:
+        if batched:
             return ctx.integrate_batched(ids, alloc, seed=seed + rank * 1000003)
         return ctx.integrate(ids, args.samples, seed=seed + rank * 1000003)
 
@@ -354,6 +357,7 @@ def main():
         "config": {"workload": "%s %d %d-loop vertex graphs without lepton loops, %s" % (
                        "all" if canon is None else "seeded subset of", len(ids), args.loops,
                        "learned mixture density, one batched persistent launch per step" if learned
+                       else "plain density, one batched persistent launch per step" if batched
                        else "plain density, one launch per graph"),
                    "samples_per_graph_per_step": args.samples, "seed": "step index (+ rank offset)",
                    "train_samples_per_graph": args.train if learned else 0,
@@ -365,14 +369,18 @@ def main():
         "plain_pdf": plain,
         "setup_seconds": {"compile": compile_s, "train": train_s, "pilot_allocation": pilot_s},
         "allocation": {"min": min(alloc), "max": max(alloc), "mode": "pilot, n_j ~ sigma_j/sqrt(t_j)"}
-        if learned and not args.no_alloc else None,
+        if batched and not args.no_alloc else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": traffic,
-                     "kernel": ("batched_kernel" if learned else "integrate_kernel") + " (sampler + FP64 tape)",
+                     "kernel": ("batched_kernel" if batched else "integrate_kernel") + " (sampler + FP64 tape)",
                      "peak_source": "measured: own DFMA probe (ae_fp64_peak)"},
         "e2e": {"value": total / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
+        "paper_v100": {"note": "context, not a target: the paper's own figures (five-loop set, Calc 2)",
+                       "hardware": "NVIDIA Tesla V100, supercomputer Govorun (JINR)",
+                       "integrand_gflops_eia": 2227.99, "samples_per_s_all_phases_derived": 2.32e6,
+                       "eia_fraction_of_v100_fp64_peak_derived": 0.297},
         "clocks": ck,
         "cpu_baseline": cpu,
     }

@@ -533,7 +533,7 @@ struct Builder {
   double flops = 0;
   bool horner = true;   // Horner trees for sums of monomials (else monomial chains)
   bool share = true;    // reuse identical Horner subtrees emitted recently
-  int share_window = 64;   // instructions
+  int share_window = 64;   // instructions (set per loop order in compile_integrand)
   std::map<std::vector<long long>, std::pair<int, size_t>> hcse;   // value id, program size after it
 
   int newval() { return nvals++; }
@@ -892,6 +892,11 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
   int n = g.n;
   Builder B;
   B.M = g.M();
+  // reuse window of Horner subtrees: a wider one saves more instructions but
+  // keeps more values live; at four and five loops the slot file limits
+  // occupancy, at three it does not (measured: 3 loops -2.8 % instructions
+  // at 1024 vs 64 with the same pitch; 5 loops +40 % pitch at 1024)
+  B.share_window = g.n <= 3 ? 1024 : g.n == 4 ? 256 : 64;
   B.nvals = B.M;    // z values are 0..M-1
   TraceMemo tm;
   int nmono = 0;
