@@ -40,6 +40,11 @@ TRAFFIC_DEFAULT_BYTES = 6.39e8
 # (14) + table product; log2 = reduction (9) + 3-step Horner (6) + 5.
 EXP2_OPS = 25
 LOG2_OPS = 20
+# the learned sampler's fused-multiply-add forms (FMA = 2): exp2 = reduction
+# (2 + 1 + 2) + degree-6 Horner (12) + table product and scaling (2);
+# log2 = reduction (5) + degree-7 Horner (14) + final FMA and sum (3)
+FEXP2_OPS = 19
+FLOG2_OPS = 22
 # per sample, both forms: the weight y = I/g = I 2^(kf - log2 g) 2^-kf
 # (floor, difference, exp2, product) and the double-double accumulation of
 # sum y, sum y^2, sum |y| (three two-sum updates of 10 operations, one square)
@@ -61,15 +66,15 @@ def sampler_flops(M, learned=False):
     log2, a product and a sum; normalisation (M exp2, M sums, one log2, one
     reciprocal, 2M products/differences); three sector densities; the
     learned density (5 ops per level); one five-term log-sum-exp (5 exp2, one
-    log2).  This path calls the device's exp2/log2; each call is counted at
-    the operation count of the table-driven form of the same function.
+    log2), with the fused-multiply-add exp2/log2; its uniforms cost two
+    additions each.
 
     Both forms add the estimator's own per-sample work (ESTIMATOR_OPS)."""
     if learned:
-        walk = sum((M - l) + 2 + LOG2_OPS for l in range(M - 1))
-        norm = M * EXP2_OPS + M + LOG2_OPS + 1 + 2 * M
-        pdf = 9 * (M - 1) + 14 + 5 * (M - 1) + 2 + 5 * (EXP2_OPS + 2) + LOG2_OPS + 1
-        return 8 * M + walk + norm + pdf + ESTIMATOR_OPS
+        walk = sum((M - l) + 2 + FLOG2_OPS for l in range(M - 1))
+        norm = M * FEXP2_OPS + M + FLOG2_OPS + 1 + 2 * M
+        pdf = 9 * (M - 1) + 14 + 5 * (M - 1) + 2 + 5 * (FEXP2_OPS + 2) + FLOG2_OPS + 1
+        return 4 * M + walk + norm + pdf + ESTIMATOR_OPS
     walk = sum(1 + (M - l) + LOG2_OPS + 2 for l in range(M - 1))
     norm = M * EXP2_OPS + M + LOG2_OPS + 1 + 2 * M
     pdf = M + 3 * (M - 1) * 3 + 9 + 4 * (2 + EXP2_OPS) + LOG2_OPS + 2

@@ -289,6 +289,11 @@ int ae_terms(ae_ctx *ctx, int graph_id, int *buf, int cap, int *len);
 int aetest_tape_replay(ae_ctx *ctx, int graph_id, const double *z, size_t count,
                        double *I, double *K);
 
+/* Test hook (device): the learned sampler's fused-multiply-add exp2 and log2
+ * next to the device library's exp2 and log2, on n arguments x (exp2) and y
+ * (log2, positive).  out: n*4 doubles (fexp2 x, exp2 x, flog2 y, log2 y). */
+int aetest_fast_elem(ae_ctx *ctx, const double *x, const double *y, size_t n, double *out);
+
 #ifdef __cplusplus
 }
 #endif

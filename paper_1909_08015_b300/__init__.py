@@ -106,6 +106,7 @@ def lib():
         L.ae_subgraphs.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)]
         L.ae_terms.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)]
         L.aetest_tape_replay.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t, dp, dp]
+        L.aetest_fast_elem.argtypes = [vp, dp, dp, ctypes.c_size_t, dp]
         _lib = L
     return _lib
 
@@ -342,6 +343,14 @@ class Context:
             els = [tuple(v[i + 2 + 3 * k:i + 5 + 3 * k]) for k in range(cnt)]
             out.append((sign, els))
             i += 2 + 3 * cnt
+        return out
+
+    def fast_elem(self, x, y):
+        """Test hook: (fexp2 x, exp2 x, flog2 y, log2 y) computed on the device."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        out = np.empty((len(x), 4))
+        self._check(lib().aetest_fast_elem(self._h, _ptr(x), _ptr(y), len(x), _ptr(out)))
         return out
 
     def tape_replay(self, gid, z):

@@ -89,6 +89,9 @@ const double *ae_exp2_table();   // 2^(j/32), j = 0..31
 void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1);
 // MRG32k3a jump matrices A1^(2^k), A2^(2^k), k = 0..159 (18 words per k)
 const uint32_t *mrg_jump_table();
+// tables and coefficients of the device's fused-multiply-add exp2/log2
+const double *ae_fast_tables();
+constexpr int kFastTabs = 177;
 const double *ae_log2_table();   // log2(j/32), j = 24..48
 
 // ------------------------------------------------------------- tapes -----

@@ -197,6 +197,28 @@ void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1) {
   }
 }
 
+// Tables and coefficients of the fused-multiply-add exp2/log2 of the learned
+// sampler (device): 2^(j/64), j = 0..63 and log2(j/64), 64/j, j = 48..96 from
+// the series definitions above; Taylor coefficients ln2^i / i! (i = 0..6) of
+// 2^r and (-1)^(k+1) / (k ln 2) (k = 1..8) of log2(1 + t), rounded from long
+// double.  Layout: 64 + 49 + 49 + 7 + 8 doubles.
+const double *ae_fast_tables() {
+  static const std::array<double, 177> t = [] {
+    std::array<double, 177> a{};
+    for (int j = 0; j < 64; ++j) a[j] = ae_exp2((double)j / 64.0);
+    for (int j = 48; j <= 96; ++j) {
+      a[64 + j - 48] = ae_log2((double)j / 64.0);
+      a[113 + j - 48] = 64.0 / (double)j;
+    }
+    const long double ln2 = 0.693147180559945309417232121458176568L;
+    long double c = 1.0L;
+    for (int i = 0; i <= 6; ++i) { a[162 + i] = (double)c; c = c * ln2 / (long double)(i + 1); }
+    for (int k = 1; k <= 8; ++k) a[169 + k - 1] = (double)(((k % 2) ? 1.0L : -1.0L) / ((long double)k * ln2));
+    return a;
+  }();
+  return t.data();
+}
+
 // MRG32k3a (L'Ecuyer 1999): jump matrices A1^(2^k) mod m1, A2^(2^k) mod m2,
 // k = 0..159, row-major, 18 words per k (A1 then A2).  Exact 128-bit products.
 static void mat3_mul(const uint64_t *A, const uint64_t *B, uint64_t *C, uint64_t m) {

@@ -146,12 +146,69 @@ __device__ __forceinline__ double dexp2(double x) {
 __device__ double kExp2Tab[32];
 __device__ double kLog2Tab[25];
 
+// Fused-multiply-add exp2/log2 for the learned sampler (not compared with the
+// host operation by operation; checked against the device library's exp2/log2):
+//   exp2: x = k/64 + r, |r| <= 1/128: 2^x = 2^(k div 64) 2^((k mod 64)/64) p(r),
+//         p the degree-6 Taylor polynomial of 2^r (remainder < 3e-20);
+//   log2: x = F 2^E, F in [3/4, 3/2), c = j/64 nearest to F, t = (F - c)(64/j)
+//         (F - c exact), log2 x = E + log2 c + t q(t), q of degree 7 from the
+//         series of log2(1 + t) (|t| <= 1/96, remainder < 2e-19 t).
+// Layout of kFast: 2^(j/64) (64), log2(j/64) (49, j = 48..96), 64/j (49),
+// ln2^i / i! (7), (-1)^(k+1)/(k ln 2) (8).
+__device__ double kFast[177];
+
 // Each translation unit that launches sampling kernels holds its own copy of
 // the tables and uploads it with this function.
-static inline cudaError_t upload_elem_tables(const double *exp2_tab, const double *log2_tab) {
+static inline cudaError_t upload_elem_tables(const double *exp2_tab, const double *log2_tab, const double *fast) {
   cudaError_t e = cudaMemcpyToSymbol(kExp2Tab, exp2_tab, 32 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(kLog2Tab, log2_tab, 25 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(kFast, fast, 177 * sizeof(double));
   return e;
+}
+
+// 2^x (0 below -1074, inf above 1023)
+__device__ __forceinline__ double fexp2(double x) {
+  if (!(x >= -1074.0 && x <= 1023.0)) return x != x ? x : (x > 0.0 ? CUDART_INF : 0.0);
+  const double magic = 6755399441055744.0;   // 1.5 * 2^52: rounds x*64 to an integer in the low word
+  const double kd = __fma_rn(x, 64.0, magic);
+  const int k = __double2loint(kd);
+  const double kr = kd - magic;
+  const double r = __fma_rn(kr, -0.015625, x);
+  const double *c = kFast + 162;
+  double p = __ldg(c + 6);
+  p = __fma_rn(p, r, __ldg(c + 5));
+  p = __fma_rn(p, r, __ldg(c + 4));
+  p = __fma_rn(p, r, __ldg(c + 3));
+  p = __fma_rn(p, r, __ldg(c + 2));
+  p = __fma_rn(p, r, __ldg(c + 1));
+  p = __fma_rn(p, r, __ldg(c + 0));
+  const int j = k & 63, m = k >> 6;
+  const double y = __ldg(kFast + j) * p;
+  if (m >= -1022) return y * __hiloint2double((m + 1023) << 20, 0);
+  return ldexp(y, m);
+}
+
+// log2 x for positive finite x (the sampler's arguments: uniforms, sums >= 1)
+__device__ __forceinline__ double flog2(double x) {
+  int hi = __double2hiint(x);
+  const int lo = __double2loint(x);
+  int e = ((hi >> 20) & 0x7ff) - 1023;
+  if (e == -1023) return log2(x);   // subnormal: not met by the sampler
+  double F = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);   // [1, 2)
+  if (F >= 1.5) { F = F * 0.5; e += 1; }
+  const int j = __double2int_rn(F * 64.0);   // 48..96
+  const double d = F - (double)j * 0.015625;
+  const double t = d * __ldg(kFast + 113 + j - 48);
+  const double *b = kFast + 169;
+  double q = __ldg(b + 7);
+  q = __fma_rn(q, t, __ldg(b + 6));
+  q = __fma_rn(q, t, __ldg(b + 5));
+  q = __fma_rn(q, t, __ldg(b + 4));
+  q = __fma_rn(q, t, __ldg(b + 3));
+  q = __fma_rn(q, t, __ldg(b + 2));
+  q = __fma_rn(q, t, __ldg(b + 1));
+  q = __fma_rn(q, t, __ldg(b + 0));
+  return __fma_rn(t, q, (double)e + __ldg(kFast + 64 + j - 48));
 }
 
 __device__ __forceinline__ double dexp2t(double x) {

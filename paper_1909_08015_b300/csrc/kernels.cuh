@@ -166,10 +166,10 @@ __device__ __forceinline__ double weight(double I, double lg) {
 //   log2 q = log2( (1-beta) 2^{log2 q_theta} + sum_k beta C_k 2^{log2 g_k} ),
 // one log-sum-exp over five terms.  This path is checked statistically
 // (normalisation, unbiasedness), not operation by operation against the
-// host, so it uses the device's own exp2/log2 (measured faster here than
-// the table-driven forms without fused multiply-adds that draw_sample
-// shares with the host) and a reciprocal table of the exponents (products
-// instead of quotients).
+// host, so it uses fused-multiply-add exp2/log2 (fexp2/flog2: faster than
+// the forms without fused multiply-adds that draw_sample shares with the
+// host) and a reciprocal table of the exponents (products instead of
+// quotients).
 static __device__ void draw_mix(const GraphDev &G, uint64_t idx, uint64_t seed, double *z, double *lz, double &log2q) {
   const int M = G.M;
   double u[2 * 14 + 2];
@@ -203,11 +203,11 @@ static __device__ void draw_mix(const GraphDev &G, uint64_t idx, uint64_t seed, 
         if (chosen < 0) chosen = last;
         lz[chosen] = cur;
         T ^= 1u << chosen;
-        cur += log2(u[2 + 2 * l]) / __ldg(deg + T);
+        cur += flog2(u[2 + 2 * l]) / __ldg(deg + T);
       }
       lz[__ffs(T) - 1] = cur;
     } else {
-      for (int i = 0; i < M; ++i) lz[i] = log2(-log2(u[1 + i]));
+      for (int i = 0; i < M; ++i) lz[i] = flog2(-flog2(u[1 + i]));
     }
   } else {
     uint32_t T = full;
@@ -223,14 +223,14 @@ static __device__ void draw_mix(const GraphDev &G, uint64_t idx, uint64_t seed, 
       }
       lz[chosen] = cur;
       T ^= 1u << chosen;
-      cur += log2(u[2 + 2 * l]) * __ldg(G.lDi + T);
+      cur += flog2(u[2 + 2 * l]) * __ldg(G.lDi + T);
     }
     lz[__ffs(T) - 1] = cur;
   }
   // normalise: z = 2^lz / sum, log2 z = lz - log2 sum
   double ssum = 0.0;
-  for (int i = 0; i < M; ++i) { z[i] = exp2(lz[i]); ssum += z[i]; }
-  const double ls = log2(ssum), rs = 1.0 / ssum;
+  for (int i = 0; i < M; ++i) { z[i] = fexp2(lz[i]); ssum += z[i]; }
+  const double ls = flog2(ssum), rs = 1.0 / ssum;
   for (int i = 0; i < M; ++i) { z[i] = z[i] * rs; lz[i] = lz[i] - ls; }
   // sector order at z (descending log2 z, ties by lower index)
   int ord[14];
@@ -274,8 +274,8 @@ static __device__ void draw_mix(const GraphDev &G, uint64_t idx, uint64_t seed, 
   }
   double m = fmax(fmax(fmax(t[0], t[1]), fmax(t[2], t[3])), t[4]);
   double rel = 0.0;
-  for (int k = 0; k < 5; ++k) rel += exp2(t[k] - m);
-  log2q = m + log2(rel);
+  for (int k = 0; k < 5; ++k) rel += fexp2(t[k] - m);
+  log2q = m + flog2(rel);
 }
 
 __device__ __forceinline__ void draw_any(const GraphDev &G, uint64_t idx, uint64_t seed, double *z, double *lz,

@@ -551,7 +551,9 @@ void init_params(std::vector<float> &p, uint64_t seed) {
 
 }  // namespace
 
-cudaError_t ae_learned_upload_tables() { return upload_elem_tables(ae_exp2_table(), ae_log2_table()); }
+cudaError_t ae_learned_upload_tables() {
+  return upload_elem_tables(ae_exp2_table(), ae_log2_table(), ae_fast_tables());
+}
 
 // Tables of the current proposal for the sampler (called after training).
 static void attach_tables(LoadedGraph &lg, Net &n) {

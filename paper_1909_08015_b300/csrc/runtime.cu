@@ -394,7 +394,7 @@ extern "C" int ae_create(ae_ctx **out, int dev, const ae_opts *opts) {
     if (e != cudaSuccess) { delete c; return AE_ERR_CUDA; }
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
     // tables of the sampler's log2/exp2, in both units that launch sampling kernels
-    e = upload_elem_tables(ae_exp2_table(), ae_log2_table());
+    e = upload_elem_tables(ae_exp2_table(), ae_log2_table(), ae_fast_tables());
     if (e == cudaSuccess) e = ae_learned_upload_tables();
     if (e != cudaSuccess) { delete c; return AE_ERR_CUDA; }
     if (c->opts.stream) {
@@ -1527,6 +1527,36 @@ extern "C" int ae_terms(ae_ctx *c, int gid, int *buf, int cap, int *len) {
   *len = (int)v.size();
   if (buf && cap >= (int)v.size()) std::copy(v.begin(), v.end(), buf);
   else if (buf) return fail(c, AE_ERR_ARG, "buffer too small");
+  return AE_OK;
+}
+
+// Test hook: the learned sampler's fused-multiply-add exp2/log2 next to the
+// device library's exp2/log2 on the same arguments (accuracy test).
+__global__ void fast_elem_kernel(const double *x, const double *y, size_t n, double *out) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[4 * i] = fexp2(x[i]);
+  out[4 * i + 1] = exp2(x[i]);
+  out[4 * i + 2] = flog2(y[i]);
+  out[4 * i + 3] = log2(y[i]);
+}
+
+extern "C" int aetest_fast_elem(ae_ctx *c, const double *x, const double *y, size_t n, double *out) {
+  if (!c || !x || !y || !out || n == 0) return AE_ERR_ARG;
+  if (c->device < 0) return fail(c, AE_ERR_NODEV, "needs a CUDA device");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  double *d = nullptr;
+  CUDA_TRY(c, cudaMalloc(&d, n * 6 * sizeof(double)));
+  cudaError_t e = cudaMemcpy(d, x, n * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d + n, y, n * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    fast_elem_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(d, d + n, n, d + 2 * n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d + 2 * n, n * 4 * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(c, AE_ERR_CUDA, std::string("fast_elem: ") + cudaGetErrorString(e));
   return AE_OK;
 }
 

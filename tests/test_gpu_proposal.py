@@ -61,3 +61,22 @@ def test_learned_mixture_normalised_and_unbiased(ctx):
     _, _, pp = ctx.integrate([gid], N, seed=4)
     a, b = pl[0], pp[0]
     assert abs(a["mean"] - b["mean"]) < 4 * math.hypot(a["sigma1"], b["sigma1"])
+
+
+def test_fast_exp2_log2_against_device_library(ctx):
+    """The learned sampler's fused-multiply-add exp2/log2 against the device
+    library's exp2/log2 (itself within a couple of ulp of the exact value):
+    within 4 ulp of it, exp2 on [-1020, 1] (0 below -1074), log2 on
+    (1e-300, 1e3); exact at powers of 2."""
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.uniform(-1070, 0, 100000), rng.uniform(-1, 1, 50000), [0.0, -1.0, -3.0, -2000.0]])
+    y = np.concatenate([np.exp(rng.uniform(-690, 6.9, 100000)), 1 + rng.uniform(-1e-6, 1e-6, 50000),
+                        [1.0, 2.0, 0.5, 0.25]])
+    out = ctx.fast_elem(x, y)
+    ok = x > -1020
+    e2 = np.abs(out[ok, 0] - out[ok, 1]) / np.spacing(np.abs(out[ok, 1]))
+    assert e2.max() <= 4, e2.max()
+    assert out[-1, 0] == 0.0 and list(out[-4:-1, 0]) == [1.0, 0.5, 0.125]
+    err = np.abs(out[:, 2] - out[:, 3]) / np.spacing(np.abs(out[:, 3]))
+    assert err.max() <= 4, err.max()
+    assert list(out[-4:, 2]) == [0.0, 1.0, -1.0, -2.0]
