@@ -30,9 +30,9 @@ METRIC = "MC samples/s and 1/(σ²·s) per graph set, learned+batched vs plain p
 
 # DRAM bytes (read + write) per batched_kernel launch in the default
 # workload's timed region: ncu dram__bytes_read.sum + dram__bytes_write.sum,
-# mean of the two launches of one step (profiles/batched_kernel_3loop_learned_set.md).
-# Applies to the default workload and the kernel revision it was taken on.
-TRAFFIC_DEFAULT_BYTES = 6.39e8
+# mean of the launches of one step (profiles/batched_kernel_3loop_learned_set.md).
+# None until taken on the current kernel revision.
+TRAFFIC_DEFAULT_BYTES = None
 
 
 # FP64 operations of the table-driven elementary functions (one division
