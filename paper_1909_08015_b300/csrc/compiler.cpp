@@ -822,8 +822,8 @@ static std::vector<int> emit_numerator(Builder &B, const FactorVals &fv, const s
     std::sort(vars.begin(), vars.end());
     order.push_back({vars, &m});
   }
-  // by Wick order j first (each j-accumulator's chain is contiguous and can
-  // live in the register accumulator), then lexicographically for prefix reuse
+  // by Wick order j first (one Horner tree, or one contiguous monomial chain,
+  // per j), then lexicographically for prefix reuse
   std::sort(order.begin(), order.end(), [](const std::pair<std::vector<int>, const Mono *> &x,
                                            const std::pair<std::vector<int>, const Mono *> &y) {
     if (x.second->j != y.second->j) return x.second->j < y.second->j;

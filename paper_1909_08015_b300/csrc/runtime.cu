@@ -2,11 +2,14 @@
 // graph set, and the integration kernels for sm_103a.
 //
 // Hot path (one launch per graph, or one persistent launch for a batch):
-//   Philox4x32-10 -> mixture pick -> Hepp-sector walk (Deg/Phi tables) ->
-//   log2 g -> tape interpreter (FP64, per-thread slot file in shared memory,
-//   instructions read warp-uniformly) -> y = I/g -> double-double
-//   accumulation of sum y, sum y^2, sum |y| -> warp-shuffle and CTA
-//   reduction -> one partial per CTA, summed on the host in fixed order.
+//   Philox4x32-10 (or MRG32k3a) -> mixture pick -> Hepp-sector walk
+//   (Deg/Phi tables, or the learned tables) -> log2 g -> tape interpreter
+//   (FP64 fused multiply-adds on a per-thread slot row in shared memory; the
+//   tape streamed into shared memory segment by segment by TMA bulk copies,
+//   all threads of a CTA stepping through it together) -> y = I/g ->
+//   double-double accumulation of sum y, sum y^2, sum |y| -> warp-shuffle
+//   and CTA reduction -> one partial per CTA (or chunk), summed on the host
+//   in fixed order.
 // Samples whose forest terms cancel badly (K > dd_ratio |I|) or whose value
 // is not finite are queued and re-evaluated by the double-double kernel.
 #include <cuda_runtime.h>
