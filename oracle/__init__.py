@@ -11,6 +11,7 @@ shares no code, tables or helpers with the CUDA path:
 * ``graphs``    -- graph set (Sec. I, footnote on arrow reversal; Table I).
 * ``forest``    -- UV-divergent subgraphs, forests and R^new terms (Sec. II).
 * ``philox``    -- Philox4x32-10 counter-based generator (Calc 2, Sec. V).
+* ``mrg32k3a``  -- MRG32k3a with jump-ahead (Calc 1, Sec. V).
 * ``sampler``   -- Deg(s), the Hepp-sector density g (Eqs. eq_pdf_final,
                    eq_pdf) and its exact sequential sampler (Sec. III.A).
 * ``dirac``     -- explicit 4x4 Dirac matrices and traces with contracted

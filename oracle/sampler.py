@@ -32,9 +32,13 @@ Readings of what the paper leaves to its missing references:
 The density is kept as log2 (the paper stores x*2^j, Sec. IV.A).
 
 Elementary functions: log2/exp2 are written here from their series
-(atanh series for log, Taylor series for exp) with plain IEEE multiply and
-add, so the sample point z is reproducible bit for bit by any other
-implementation of the same steps.
+(atanh series for log, Taylor series for exp); the sampler uses Tang's
+table-driven forms on tables of those series at the table points, with
+plain IEEE multiply, add and divide, so the sample point z is reproducible
+bit for bit by any other implementation of the same steps.  The walk
+multiplies by 1/Deg and the normalisation by 1/sum (products, not quotients).
+The density can be evaluated for the constants of either calculation
+(CALC1, CALC2).
 
 Pins: E_g[1/g] = 1/(M-1)! (simplex volume), E_g[z_i/g] = 1/M!, exact
 sector probabilities by enumeration for small M.
