@@ -39,8 +39,14 @@ typedef struct ae_opts {
   double C_bigZ, C_bigF, C_add;      /* Deg(s) constants kept, not used           */
   double deg_max;                    /* cap on Deg(s) (library reading, see the
                                         design notes); <= 0 means no cap          */
-  double dd_ratio;                   /* re-evaluate in double-double when
-                                        K > dd_ratio * |I| (default 1e8); <= 0 off */
+  double dd_tol;                     /* acceptance of an FP64 value: its certified
+                                        rounding-error bound, carried to y = I/g,
+                                        at most dd_tol * max(|y|, the graph's
+                                        floor, ae_set_accept_floor); others are
+                                        re-evaluated in double-double under the
+                                        same test, and count as zero if they fail
+                                        it again.  Default 1e-10; <= 0: accept
+                                        every finite value */
   int block_size;                    /* threads per CTA, 0 = automatic            */
   int ctas_per_sm;                   /* CTAs per SM for the grid, 0 = automatic   */
   void *stream;                      /* cudaStream_t to launch on; NULL = a stream
@@ -91,8 +97,12 @@ typedef struct ae_graph_meta {
   int klass[3];          /* (k, m, m') of Sec. V, Table I */
   int word[11];          /* path word, -1 = external vertex; 2n+1 entries */
   int n_subgraphs, n_terms, tape_len, nslots, n_monomials;
-  double flops;          /* FP64 flops of one tape evaluation (FMA = 2) */
+  double flops;          /* FP64 flops of one tape evaluation (FMA = 2), the
+                            error bound's magnitude twins included */
   int canonical_id;      /* index in the full canonical list */
+  int bound_depth;       /* D: roundings on the deepest chain into I; the
+                            bound is gamma_D M_I (Sec. III.A, library reading) */
+  double flops_bound;    /* of flops, those of the magnitude twins */
 } ae_graph_meta;
 int ae_graph_info(ae_ctx *ctx, int graph_id, ae_graph_meta *out);
 
@@ -137,7 +147,8 @@ int ae_integrate_range(ae_ctx *ctx, int graph_id, uint64_t first, uint64_t count
  * autotuner (timed trial runs on sample indices from 2^44 on, cached per
  * graph set) unless opts.block_size is set.  Per-graph `seconds` are the
  * launch time apportioned by sample count.  Same samples (indices 0..n-1) and
- * the same result as ae_integrate up to summation order. */
+ * the same result as ae_integrate up to summation order.  A graph given 0
+ * samples contributes value 0 and sigma 0. */
 int ae_integrate_batched(ae_ctx *ctx, const int *graph_ids, int n_ids,
                          const uint64_t *n_samples, uint64_t seed, double *value,
                          double *sigma, ae_graph_result *per_graph);
@@ -152,7 +163,8 @@ int ae_integrate_batched(ae_ctx *ctx, const int *graph_ids, int n_ids,
  * counterpart; this is a property of the library, not of the method.
  *
  * Same computation as ae_integrate for a single graph (FP64 integrand,
- * double-double re-evaluation of samples with K > dd_ratio |I|, fixed-order
+ * double-double re-evaluation of the samples that fail the acceptance test
+ * of ae_opts.dd_tol, fixed-order
  * reduction), but every intermediate lives in one fixed device array of
  * about 8.3 MB that the library declares statically; each GPU that loads the
  * library holds that array until the process exits.  The caller passes the
@@ -197,6 +209,16 @@ int ae_train_proposal(ae_ctx *ctx, int graph_id, uint64_t n_train, uint64_t seed
 /* Select a graph's density: mode 0 = plain g, 1 = learned mixture with weight
  * beta on g (needs a trained proposal). */
 int ae_set_proposal(ae_ctx *ctx, int graph_id, int mode, double beta);
+
+/* Absolute floor on |y| in the acceptance of a graph's values (see
+ * ae_opts.dd_tol): a value is kept when its bound is at most
+ * dd_tol * max(|y|, yfloor).  0 (the default) makes the test relative to
+ * each sample.  The paper fixes its tolerance from an initialisation pass
+ * (Sec. III.A, Eq. eq_interval_accept: a quarter of the graph's expected
+ * sigma); the library leaves the scale to the caller, e.g. the mean |y| of
+ * a pilot, which keeps the summed rounding error of N samples below
+ * 2 dd_tol N mean|y|.  yfloor finite and >= 0. */
+int ae_set_accept_floor(ae_ctx *ctx, int graph_id, double yfloor);
 
 /* Test entry: loss and gradient of the proposal for given parameters
  * (ae_proposal_nparams() floats: W1[64][32], b1, W2[64][64], b2, W3[64][64],
@@ -252,16 +274,19 @@ int ae_combine_runs(const double *v1, const double *s1, const double *v2, const 
                     double *v_out, double *s_out, double *total, double *total_sigma);
 
 /* Per-sample dump for parity tests: samples first .. first+count-1 of
- * graph_id under `seed`.  z: count*M, log2g, I, K, y: count each (any may be
- * NULL).  Host buffers. */
+ * graph_id under `seed`, evaluated in FP64.  z: count*M, log2g, I, K, y, E:
+ * count each (any may be NULL); E is the certified bound on |I - exact I|
+ * (rounding only: gamma_D times the magnitude evaluation of I).  Host
+ * buffers. */
 int ae_eval_samples(ae_ctx *ctx, int graph_id, uint64_t first, uint64_t count,
                     uint64_t seed, double *z, double *log2g, double *I, double *K,
-                    double *y);
+                    double *y, double *E);
 
 /* Same samples, every one evaluated by the double-double (about 106-bit)
- * twin of the integrand tape.  I, K, y: count each (any may be NULL). */
+ * twin of the integrand tape.  I, K, y, E: count each (any may be NULL); E
+ * is the bound at the double-double unit. */
 int ae_eval_samples_dd(ae_ctx *ctx, int graph_id, uint64_t first, uint64_t count,
-                       uint64_t seed, double *I, double *K, double *y);
+                       uint64_t seed, double *I, double *K, double *y, double *E);
 
 /* Philox4x32-10 on the device: count (counter[4], key[2]) -> word[4]. */
 int ae_philox(ae_ctx *ctx, const uint32_t *ctr, const uint32_t *key, uint32_t *out,
@@ -284,10 +309,11 @@ int ae_subgraphs(ae_ctx *ctx, int graph_id, int *buf, int cap, int *len);
 int ae_terms(ae_ctx *ctx, int graph_id, int *buf, int cap, int *len);
 
 /* Test hook (host, no device): replay a graph's tape at count points z
- * (count*M doubles).  Used only by the test suite to check the compiler
- * against the oracle on machines without a GPU; no integration call uses it. */
+ * (count*M doubles): I, K and (E non-NULL) the rounding-error bound of I.
+ * Used only by the test suite to check the compiler against the oracle on
+ * machines without a GPU; no integration call uses it. */
 int aetest_tape_replay(ae_ctx *ctx, int graph_id, const double *z, size_t count,
-                       double *I, double *K);
+                       double *I, double *K, double *E);
 
 /* Test hook (device): the learned sampler's fused-multiply-add exp2 and log2
  * next to the device library's exp2 and log2, on n arguments x (exp2) and y

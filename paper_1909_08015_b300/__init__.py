@@ -23,7 +23,7 @@ class AeOpts(ctypes.Structure):
     _fields_ = [("C2", ctypes.c_double), ("C3", ctypes.c_double), ("C4", ctypes.c_double),
                 ("D", ctypes.c_double), ("C_subI", ctypes.c_double), ("C_subSE", ctypes.c_double),
                 ("C_subO", ctypes.c_double), ("C_bigZ", ctypes.c_double), ("C_bigF", ctypes.c_double),
-                ("C_add", ctypes.c_double), ("deg_max", ctypes.c_double), ("dd_ratio", ctypes.c_double),
+                ("C_add", ctypes.c_double), ("deg_max", ctypes.c_double), ("dd_tol", ctypes.c_double),
                 ("block_size", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("rng", ctypes.c_int)]
 
@@ -33,7 +33,8 @@ class AeGraphMeta(ctypes.Structure):
                 ("klass", ctypes.c_int * 3), ("word", ctypes.c_int * 11),
                 ("n_subgraphs", ctypes.c_int), ("n_terms", ctypes.c_int),
                 ("tape_len", ctypes.c_int), ("nslots", ctypes.c_int),
-                ("n_monomials", ctypes.c_int), ("flops", ctypes.c_double), ("canonical_id", ctypes.c_int)]
+                ("n_monomials", ctypes.c_int), ("flops", ctypes.c_double), ("canonical_id", ctypes.c_int),
+                ("bound_depth", ctypes.c_int), ("flops_bound", ctypes.c_double)]
 
 
 class AeTrainReport(ctypes.Structure):
@@ -92,20 +93,21 @@ def lib():
         L.ae_train_proposal.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_double, P(AeTrainReport)]
         L.ae_set_proposal.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        L.ae_set_accept_floor.argtypes = [vp, ctypes.c_int, ctypes.c_double]
         L.ae_proposal_eval.argtypes = [vp, ctypes.c_int, P(ctypes.c_float), dp, dp, P(ctypes.c_uint8),
                                        P(ctypes.c_float), dp, ctypes.c_uint64, dp, P(ctypes.c_float), dp, dp]
         L.ae_proposal_nparams.restype = ctypes.c_int
         L.ae_integrate_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, P(AeGraphResult)]
         L.ae_eval_samples.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
-                                      dp, dp, dp, dp, dp]
+                                      dp, dp, dp, dp, dp, dp]
         L.ae_eval_samples_dd.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
-                                         dp, dp, dp]
+                                         dp, dp, dp, dp]
         L.ae_philox.argtypes = [vp, P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32), ctypes.c_size_t]
         L.ae_density_tables.argtypes = [vp, ctypes.c_int, dp, dp]
         L.ae_fp64_peak.argtypes = [vp, dp]
         L.ae_subgraphs.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)]
         L.ae_terms.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)]
-        L.aetest_tape_replay.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t, dp, dp]
+        L.aetest_tape_replay.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t, dp, dp, dp]
         L.aetest_fast_elem.argtypes = [vp, dp, dp, ctypes.c_size_t, dp]
         _lib = L
     return _lib
@@ -267,6 +269,11 @@ class Context:
     def set_proposal(self, gid, mode, beta=0.1):
         self._check(lib().ae_set_proposal(self._h, gid, int(mode), float(beta)))
 
+    def set_accept_floor(self, gid, yfloor):
+        """Absolute floor on |y| in the acceptance test of the graph's FP64
+        values (kept when bound <= dd_tol * max(|y|, yfloor))."""
+        self._check(lib().ae_set_accept_floor(self._h, gid, float(yfloor)))
+
     def proposal_eval(self, M, params, deg, wplain, order, lt, w):
         params = np.ascontiguousarray(params, dtype=np.float32)
         deg = np.ascontiguousarray(deg, dtype=np.float64)
@@ -295,14 +302,16 @@ class Context:
         M = self.graph_info(gid)["M"]
         z = np.empty((count, M))
         lg = np.empty(count); I = np.empty(count); K = np.empty(count); y = np.empty(count)
+        E = np.empty(count)
         self._check(lib().ae_eval_samples(self._h, gid, first, count, seed, _ptr(z), _ptr(lg),
-                                          _ptr(I), _ptr(K), _ptr(y)))
-        return dict(z=z, log2g=lg, I=I, K=K, y=y)
+                                          _ptr(I), _ptr(K), _ptr(y), _ptr(E)))
+        return dict(z=z, log2g=lg, I=I, K=K, y=y, E=E)
 
     def eval_samples_dd(self, gid, first, count, seed=0):
-        I = np.empty(count); K = np.empty(count); y = np.empty(count)
-        self._check(lib().ae_eval_samples_dd(self._h, gid, first, count, seed, _ptr(I), _ptr(K), _ptr(y)))
-        return dict(I=I, K=K, y=y)
+        I = np.empty(count); K = np.empty(count); y = np.empty(count); E = np.empty(count)
+        self._check(lib().ae_eval_samples_dd(self._h, gid, first, count, seed, _ptr(I), _ptr(K), _ptr(y),
+                                             _ptr(E)))
+        return dict(I=I, K=K, y=y, E=E)
 
     def philox(self, ctr, key):
         ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
@@ -353,9 +362,10 @@ class Context:
         self._check(lib().aetest_fast_elem(self._h, _ptr(x), _ptr(y), len(x), _ptr(out)))
         return out
 
-    def tape_replay(self, gid, z):
-        """Test hook: host replay of the compiled tape at points z."""
+    def tape_replay(self, gid, z, bound=False):
+        """Test hook: host replay of the compiled tape at points z: (I, K),
+        and the rounding-error bound E of I with bound=True."""
         z = np.ascontiguousarray(z, dtype=np.float64)
-        I = np.empty(z.shape[0]); K = np.empty(z.shape[0])
-        self._check(lib().aetest_tape_replay(self._h, gid, _ptr(z), z.shape[0], _ptr(I), _ptr(K)))
-        return I, K
+        I = np.empty(z.shape[0]); K = np.empty(z.shape[0]); E = np.empty(z.shape[0])
+        self._check(lib().aetest_tape_replay(self._h, gid, _ptr(z), z.shape[0], _ptr(I), _ptr(K), _ptr(E)))
+        return (I, K, E) if bound else (I, K)

@@ -112,6 +112,8 @@ enum TapeOp : uint8_t {
   T_ZERO = 11, // d = 0
   T_ADDABS = 12, // d = d + |a|
   T_G = 13,    // d = a * (b or K[b]) + (c or K[c]); flags G_BK, G_CK
+  T_GA = 14,   // d = |a| * |b or K[b]| + |c or K[c]|   (magnitude twin)
+  T_GAC = 15,  // d = |d| + |a| * |b or K[b]|           (accumulating twin)
 };
 enum : uint8_t { G_BK = 1, G_CK = 2 };
 
@@ -119,7 +121,9 @@ enum : uint8_t { G_BK = 1, G_CK = 2 };
 // fused multiply-add
 //     S[d] = S[a] * (I_BK ? kb : S[b]) + (I_CK ? kc : S[c]),
 // so the interpreter needs no dispatch beyond one test of the special code
-// (division, absolute value, accumulated absolute value).  Slot fields are
+// (division, absolute value, accumulated absolute value).  With I_AB the
+// three operands enter the fused multiply-add as absolute values; those
+// instructions carry the magnitudes of the running error bound.  Slot fields are
 // byte offsets (slot * 8) into the thread's row of the slot file; a field
 // that names an immediate holds 0 (a valid slot).  kbi/kci index the
 // constant pool (hi, lo) so that the double-double evaluation can use the
@@ -134,6 +138,7 @@ struct Ins {
 static_assert(sizeof(Ins) == 32, "Ins must be 32 bytes");
 enum : uint16_t {
   I_BK = 1, I_CK = 2,
+  I_AB = 4,           // S[d] = |S[a]| * |kb or S[b]| + |kc or S[c]|
   I_DIV = 1 << 8,     // S[d] = S[a] / S[b]
   I_ABS = 2 << 8,     // S[d] = |S[a]|
   I_ADDABS = 3 << 8,  // S[d] = S[c] + |S[a]|
@@ -144,7 +149,10 @@ struct Tape {
   std::vector<double> khi, klo;  // constant pool
   int nslots = 0;                 // row pitch of the slot file (odd: conflict-free rows)
   int out_I = -1, out_K = -1;     // output slots
+  int out_E = -1;                 // slot of the rounding-error bound of I
+  int depth = 0;                  // roundings along the deepest chain into I
   double flops = 0;               // FP64 flops per evaluation (FMA = 2)
+  double flops_bound = 0;         // of which the error bound's magnitude twins
   int M = 0;
   int n_terms = 0;
 };
@@ -156,6 +164,6 @@ Tape compile_integrand(const Graph &g, CompileStats *st);
 
 // Host replay of a tape (test harness only; not an evaluation path of the
 // library's integration calls).
-void tape_replay(const Tape &t, const double *z, double *I, double *K);
+void tape_replay(const Tape &t, const double *z, double *I, double *K, double *E = nullptr);
 
 }  // namespace ae

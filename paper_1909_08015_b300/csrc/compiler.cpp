@@ -530,7 +530,7 @@ struct Builder {
   int nvals = 0;
   int M = 0;
   std::map<std::tuple<int, int, int>, int> cse;
-  double flops = 0;
+  double flops = 0, flops_bound = 0;
   bool horner = true;   // Horner trees for sums of monomials (else monomial chains)
   bool share = true;    // reuse identical Horner subtrees emitted recently
   int share_window = 64;   // instructions (set per loop order in compile_integrand)
@@ -1062,14 +1062,15 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
   // value operands of an intermediate instruction
   auto b_is_val = [](const Builder::SIns &in) {
     return in.op == T_ADD || in.op == T_SUB || in.op == T_MUL || in.op == T_DIV || in.op == T_FMA ||
-           (in.op == T_G && !(in.fl & G_BK));
+           ((in.op == T_G || in.op == T_GA || in.op == T_GAC) && !(in.fl & G_BK));
   };
-  auto c_is_val = [](const Builder::SIns &in) { return in.op == T_G && !(in.fl & G_CK); };
-  auto accum = [](uint8_t op) { return op == T_FMA || op == T_FMAC || op == T_ADDABS; };
+  auto c_is_val = [](const Builder::SIns &in) { return (in.op == T_G || in.op == T_GA) && !(in.fl & G_CK); };
+  auto accum = [](uint8_t op) { return op == T_FMA || op == T_FMAC || op == T_ADDABS || op == T_GAC; };
   const int zk = B.konst(0.0);
-  {
+  const int k_one = B.konst(1.0), k_mone = B.konst(-1.0);
+  auto dce = [&](std::vector<int> roots) {
     std::vector<char> live(B.nvals, 0);
-    live[outI] = live[outK] = 1;
+    for (int r : roots) live[r] = 1;
     std::vector<char> keep(B.prog.size(), 0);
     for (int i = (int)B.prog.size() - 1; i >= 0; --i) {
       auto &in = B.prog[i];
@@ -1081,16 +1082,179 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
       if (accum(in.op)) live[in.d] = 1;
     }
     std::vector<Builder::SIns> np;
-    double fl = 0;
     for (size_t i = 0; i < B.prog.size(); ++i)
-      if (keep[i]) {
-        const auto &in = B.prog[i];
-        np.push_back(in);
-        if (in.op == T_G) fl += ((in.fl & G_CK) && in.c == zk) ? 1 : 2;
-        else fl += (in.op == T_FMA || in.op == T_FMAC) ? 2 : (in.op == T_CONST || in.op == T_ZERO) ? 0 : 1;
-      }
+      if (keep[i]) np.push_back(B.prog[i]);
     B.prog.swap(np);
+  };
+  dce({outI, outK});
+  // ------------------------------------------------ running error bound --
+  // The paper certifies every FP64 value with an interval whose radius is
+  // estimated next to the centres (Sec. III.A, Eq. eq_interval_accept).  The
+  // library's form of that estimate is the classical running bound for
+  // straight-line code: a value reached through k roundings on its deepest
+  // chain lies within gamma_k * M of the exact one, M being the same
+  // computation done on absolute values (products add depths, sums take the
+  // larger; a quotient a/b has M = (M_a + |a/b| M_b) / |b| to first order).
+  // A value whose operands never meet with opposite signs has M = |value|
+  // and costs nothing; only the others get a magnitude twin (T_GA, T_GAC).
+  int outE = -1, depth = 0;
+  {
+    const size_t n0 = B.prog.size();
+    const size_t cap = (size_t)B.nvals + 3 * n0 + 8;
+    std::vector<uint8_t> sg(cap, 1);   // bit 0: may be > 0, bit 1: may be < 0
+    std::vector<int> mv(cap, -1);      // magnitude twin, -1: |value| itself
+    std::vector<int> kd(cap, 0);       // roundings on the deepest chain
+    auto ksg = [&](int k) -> uint8_t { double v = B.khi[k]; return v > 0 ? 1 : v < 0 ? 2 : 0; };
+    auto kdep = [&](int k) { return B.klo[k] != 0.0 ? 1 : 0; };
+    auto mulsg = [](uint8_t x, uint8_t y) -> uint8_t {
+      uint8_t r = 0;
+      if (((x & 1) && (y & 1)) || ((x & 2) && (y & 2))) r |= 1;
+      if (((x & 1) && (y & 2)) || ((x & 2) && (y & 1))) r |= 2;
+      return r;
+    };
+    auto mag = [&](int v) { return mv[v] >= 0 ? mv[v] : v; };
+    auto tracked = [&](int v) { return mv[v] >= 0; };
+    std::vector<Builder::SIns> np;
+    np.reserve(2 * n0 + 4);
+    auto twin = [&](uint8_t op, int d, int a, int b, int c, uint8_t fl) {
+      Builder::SIns t;
+      t.op = op; t.d = d; t.a = a; t.b = b; t.c = c; t.fl = fl;
+      np.push_back(t);
+    };
+    // d = A * Bv + Cv, operands given as (is constant, id); C absent: c < 0
+    struct Opd { bool k; int id; };
+    auto opsg = [&](Opd o) -> uint8_t { return o.id < 0 ? 0 : o.k ? ksg(o.id) : sg[o.id]; };
+    auto opdep = [&](Opd o) { return o.id < 0 ? 0 : o.k ? kdep(o.id) : kd[o.id]; };
+    auto optr = [&](Opd o) { return o.id >= 0 && !o.k && tracked(o.id); };
+    for (size_t i = 0; i < n0; ++i) {
+      const Builder::SIns in = B.prog[i];
+      Opd A{false, in.a}, Bo{false, -1}, Co{false, -1};
+      bool acc = false, special = false;
+      switch (in.op) {
+        case T_ADD: Bo = {true, k_one}; Co = {false, in.b}; break;
+        case T_SUB: A = {false, in.b}; Bo = {true, k_mone}; Co = {false, in.a}; break;
+        case T_MUL: Bo = {false, in.b}; break;
+        case T_FMA: Bo = {false, in.b}; Co = {false, in.d}; acc = true; break;
+        case T_FMAC: Bo = {true, in.b}; Co = {false, in.d}; acc = true; break;
+        case T_MULC: Bo = {true, in.b}; break;
+        case T_G:
+          Bo = (in.fl & G_BK) ? Opd{true, in.b} : Opd{false, in.b};
+          Co = (in.fl & G_CK) ? Opd{true, in.c} : Opd{false, in.c};
+          break;
+        default: special = true; break;
+      }
+      if (!special) {
+        const uint8_t sP = mulsg(opsg(A), opsg(Bo)), sC = opsg(Co);
+        const bool cancel = ((sP & 1) && (sC & 2)) || ((sP & 2) && (sC & 1));
+        const int kP = opdep(A) + opdep(Bo);
+        // magnitude operands
+        const int ma = mag(A.id);
+        const int mb = Bo.k ? Bo.id : mag(Bo.id);
+        const uint8_t fb = Bo.k ? G_BK : 0;
+        if (acc) {
+          const int d = in.d;
+          if (tracked(d)) {
+            twin(T_GAC, mv[d], ma, mb, -1, fb);
+          } else if (cancel || optr(A) || optr(Bo)) {
+            const int md = B.newval();
+            twin(T_GA, md, ma, mb, d, fb);   // reads d before the update below
+            mv[d] = md;
+          }
+          np.push_back(in);
+          sg[d] = (uint8_t)(sP | sC);
+          kd[d] = std::max(kP, kd[d]) + 1;
+        } else {
+          np.push_back(in);
+          const int d = in.d;
+          sg[d] = (uint8_t)(sP | sC);
+          kd[d] = std::max(kP, opdep(Co)) + 1;
+          int ex;
+          if (in.op == T_MULC && std::fabs(std::frexp(B.khi[in.b], &ex)) == 0.5) kd[d] = kP;   // exact scaling
+          if (cancel || optr(A) || optr(Bo) || optr(Co)) {
+            const int md = B.newval();
+            int mc; uint8_t fc;
+            if (Co.id < 0) { mc = zk; fc = G_CK; }
+            else if (Co.k) { mc = Co.id; fc = G_CK; }
+            else { mc = mag(Co.id); fc = 0; }
+            twin(T_GA, md, ma, mb, mc, (uint8_t)(fb | fc));
+            mv[d] = md;
+          }
+        }
+        continue;
+      }
+      const int d = in.d;
+      switch (in.op) {
+        case T_DIV: {
+          np.push_back(in);
+          sg[d] = mulsg(sg[in.a], sg[in.b]);
+          kd[d] = kd[in.a] + kd[in.b] + 1;
+          if (tracked(in.a) || tracked(in.b)) {
+            const int t = B.newval(), md = B.newval();
+            twin(T_GA, t, d, mag(in.b), mag(in.a), 0);   // |a/b| M_b + M_a
+            twin(T_DIV, md, t, in.b, -1, 0);             // over b (sign dropped by the readers)
+            mv[d] = md;
+          }
+          break;
+        }
+        case T_CONST:
+          np.push_back(in);
+          sg[d] = ksg(in.b); kd[d] = kdep(in.b);
+          break;
+        case T_ZERO:
+          np.push_back(in);
+          sg[d] = 0; kd[d] = 0;
+          break;
+        case T_ABS: case T_NEG: {
+          np.push_back(in);
+          const uint8_t s = sg[in.a];
+          sg[d] = in.op == T_ABS ? (uint8_t)(s ? 1 : 0) : (uint8_t)(((s & 1) << 1) | ((s & 2) >> 1));
+          kd[d] = kd[in.a];
+          if (tracked(in.a)) {   // own copy: the operand may be an accumulator that changes later
+            const int md = B.newval();
+            twin(T_GA, md, mv[in.a], k_one, zk, G_BK | G_CK);
+            mv[d] = md;
+          }
+          break;
+        }
+        case T_ADDABS: {   // d = d + |a|
+          const uint8_t sP = sg[in.a] ? 1 : 0, sC = sg[d];
+          const bool cancel = (sP & 1) && (sC & 2);
+          if (tracked(d)) twin(T_GAC, mv[d], mag(in.a), k_one, -1, G_BK);
+          else if (cancel || tracked(in.a)) {
+            const int md = B.newval();
+            twin(T_GA, md, mag(in.a), k_one, d, G_BK);
+            mv[d] = md;
+          }
+          np.push_back(in);
+          sg[d] = (uint8_t)(sP | sC);
+          kd[d] = std::max(kd[in.a], kd[d]) + 1;
+          break;
+        }
+        default: throw std::runtime_error("error bound: unknown intermediate operation");
+      }
+    }
+    // E = gamma_D * M_I,  gamma_D = D u / (1 - D u),  u = 2^-53, with a 2 %
+    // allowance for the rounding of M itself and first-order terms
+    depth = kd[outI];
+    const double u = std::ldexp(1.0, -53);
+    const double gam = 1.02 * depth * u / (1.0 - depth * u);
+    outE = B.newval();
+    twin(T_GA, outE, mag(outI), B.konst(gam), zk, G_BK | G_CK);
+    B.prog.swap(np);
+  }
+  dce({outI, outK, outE});
+  {
+    double fl = 0, flb = 0;
+    for (const auto &in : B.prog) {
+      double f;
+      if (in.op == T_G || in.op == T_GA) f = ((in.fl & G_CK) && in.c == zk) ? 1 : 2;
+      else f = (in.op == T_FMA || in.op == T_FMAC || in.op == T_GAC) ? 2
+             : (in.op == T_CONST || in.op == T_ZERO) ? 0 : 1;
+      fl += f;
+      if (in.op == T_GA || in.op == T_GAC) flb += f;
+    }
     B.flops = fl;
+    B.flops_bound = flb;
   }
   // ---------------------------------------------------- slot allocation --
   std::vector<int> last(B.nvals, -1);
@@ -1101,7 +1265,7 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
     if (c_is_val(in) && in.c >= 0) last[in.c] = (int)i;
     if (accum(in.op)) last[in.d] = (int)i;
   }
-  last[outI] = last[outK] = (int)B.prog.size();
+  last[outI] = last[outK] = last[outE] = (int)B.prog.size();
   std::vector<int> slot(B.nvals, -1);
   std::vector<int> freelist;
   int nslots = B.M;
@@ -1136,13 +1300,12 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
       if (last[in.d] <= (int)i) freelist.push_back(sd);   // never read
     }
     for (int v : rel) freelist.push_back(slot[v]);
-    if (acc && last[in.d] == (int)i && in.d != outI && in.d != outK) freelist.push_back(sd);
+    if (acc && last[in.d] == (int)i && in.d != outI && in.d != outK && in.d != outE) freelist.push_back(sd);
     low.push_back({&in, sd, sa, sb, sc});
   }
   if (nslots > 8191) throw std::runtime_error("tape needs more than 8191 slots");
   // ------------------------------------------- lowering to instructions --
   // every arithmetic operation becomes  d = a * (b | kb) + (c | kc)
-  const int k_one = B.konst(1.0), k_mone = B.konst(-1.0);
   if (B.khi.size() > 65535) throw std::runtime_error("constant pool exceeds 16-bit indices");
   Tape tp;
   tp.M = B.M;
@@ -1169,6 +1332,16 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
         if (in.fl & G_BK) setb(in.b); else bb = l.sb;
         if (in.fl & G_CK) setc(in.c); else cc = l.sc;
         break;
+      case T_GA:
+        o.op = I_AB;
+        if (in.fl & G_BK) setb(in.b); else bb = l.sb;
+        if (in.fl & G_CK) setc(in.c); else cc = l.sc;
+        break;
+      case T_GAC:
+        o.op = I_AB;
+        if (in.fl & G_BK) setb(in.b); else bb = l.sb;
+        cc = l.sd;
+        break;
       default: throw std::runtime_error("unknown intermediate operation");
     }
     o.d = (uint16_t)(l.sd * 8);
@@ -1179,8 +1352,10 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
   }
   tp.khi = B.khi; tp.klo = B.klo;
   tp.nslots = nslots | 1;   // odd row pitch: the rows of a warp fall in distinct banks
-  tp.out_I = slot[outI]; tp.out_K = slot[outK];
+  tp.out_I = slot[outI]; tp.out_K = slot[outK]; tp.out_E = slot[outE];
+  tp.depth = depth;
   tp.flops = B.flops;
+  tp.flops_bound = B.flops_bound;
   tp.n_terms = (int)terms.size();
   if (st) { st->n_terms = (int)terms.size(); st->n_factors = nfac; st->n_monomials = nmono; }
   return tp;
@@ -1189,7 +1364,7 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
 // Host replay of a tape: used only by the test suite to check the compiler
 // against the oracle without a GPU.  Same operations as the device
 // interpreter.
-void tape_replay(const Tape &t, const double *z, double *I, double *K) {
+void tape_replay(const Tape &t, const double *z, double *I, double *K, double *E) {
   std::vector<double> s(t.nslots, 0.0);
   for (int i = 0; i < t.M; ++i) s[i] = z[i];
   for (const Ins &in : t.code) {
@@ -1198,7 +1373,7 @@ void tape_replay(const Tape &t, const double *z, double *I, double *K) {
     const double c = (in.op & I_CK) ? in.kc : s[in.c / 8];
     double r;
     switch (in.op >> 8) {   // special code
-      case 0: r = std::fma(a, b, c); break;
+      case 0: r = (in.op & I_AB) ? std::fma(std::fabs(a), std::fabs(b), std::fabs(c)) : std::fma(a, b, c); break;
       case I_DIV >> 8: r = a / b; break;
       case I_ABS >> 8: r = std::fabs(a); break;
       case I_ADDABS >> 8: r = c + std::fabs(a); break;
@@ -1208,6 +1383,7 @@ void tape_replay(const Tape &t, const double *z, double *I, double *K) {
   }
   *I = s[t.out_I];
   *K = s[t.out_K];
+  if (E) *E = s[t.out_E];
 }
 
 }  // namespace ae

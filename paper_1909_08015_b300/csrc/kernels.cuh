@@ -19,8 +19,9 @@ struct GraphDev {
   const double *dinv;     // 3 * 2^M: 1/deg
   const Ins *code;       // tape (32-byte instructions)
   const double *khi, *klo;
-  int M, ntape, nslots, outI, outK;
+  int M, ntape, nslots, outI, outK, outE;
   int graph_id;
+  double yfloor = 0;      // absolute floor on |y| in the acceptance of a value
   double C1, C2, C3, C4, log2_fact;
   double log2C[4];        // log2 of C1..C4 (g1, g2, g3, g4 order)
   double log2phi_full[3];
@@ -82,7 +83,6 @@ static __device__ void draw_sample(const GraphDev &G, uint64_t idx, uint64_t see
   const uint32_t full = (1u << M) - 1;
   if (comp != 1) {
     int k = comp == 0 ? 0 : comp - 1;
-    const double *deg = G.deg + ((size_t)k << M);
     const double *phi = G.phi + ((size_t)k << M);
     const double *wt = G.wt + ((size_t)k << M);
     const double *dinv = G.dinv + ((size_t)k << M);
@@ -158,6 +158,30 @@ __device__ __forceinline__ double weight(double I, double lg) {
   double s = dexp2t(__dadd_rn(kf, -lg));
   double kc = fmin(fmax(kf, -100000.0), 100000.0);
   return ldexp(__dmul_rn(I, s), -(int)kc);
+}
+
+// weight() of I and of its error bound E with one exponential
+__device__ __forceinline__ void weight2(double I, double E, double lg, double &y, double &Ey) {
+  double kf = floor(lg);
+  double s = dexp2t(__dadd_rn(kf, -lg));
+  int kc = (int)fmin(fmax(kf, -100000.0), 100000.0);
+  y = ldexp(__dmul_rn(I, s), -kc);
+  Ey = ldexp(__dmul_rn(E, s), -kc);
+}
+
+// Acceptance of a value (Sec. III.A, Eq. eq_interval_accept, library
+// reading): the certified rounding-error bound of I, carried to y = I/g like
+// I, must not exceed tol * max(|y|, yfloor).  tol <= 0 accepts every finite
+// value.  For the double-double twin the bound is scaled from the FP64 unit
+// 2^-53 to 2^-100 (the double-double operations' unit with a margin for the
+// non-normalising additions).
+__device__ __forceinline__ bool fp64_rejected(const GraphDev &G, double y, double Ey, double tol) {
+  if (!isfinite(y) || !isfinite(Ey)) return true;
+  return tol > 0 && Ey > tol * fmax(fabs(y), G.yfloor);
+}
+__device__ __forceinline__ bool dd_rejected(const GraphDev &G, double y, double Ey, double tol) {
+  if (!isfinite(y) || !isfinite(Ey)) return true;
+  return tol > 0 && Ey * 0x1p-47 > tol * fmax(fabs(y), G.yfloor);
 }
 
 // Defensive mixture q = (1-beta) q_theta + beta g.  u[0] < beta selects the
@@ -299,13 +323,21 @@ static __device__ __noinline__ double special_op(uint32_t sp, double va, double 
   return __dadd_rn(vc, fabs(va));   // I_ADDABS
 }
 
+// Clears the sign bit of x when m = 0x7fffffff (m = 0xffffffff: x unchanged).
+__device__ __forceinline__ double absmask(double x, uint32_t m) {
+  return __hiloint2double(__double2hiint(x) & (int)m, __double2loint(x));
+}
+
 // One tape instruction on this thread's slot row Sb:
-//   S[d] = S[a] * (kb | S[b]) + (kc | S[c])   or a special operation.
+//   S[d] = S[a] * (kb | S[b]) + (kc | S[c])   or a special operation;
+// with I_AB the operands enter as absolute values (magnitude twins of the
+// error bound), by a sign mask rather than a branch.
 __device__ __forceinline__ void tape_step(const uint4 &w0, const uint4 &w1, char *Sb) {
   const uint32_t op = w0.x & 0xffffu, d = w0.x >> 16, a = w0.y & 0xffffu, b = w0.y >> 16, c = w0.z & 0xffffu;
-  const double va = *reinterpret_cast<const double *>(Sb + a);
-  const double vb = sel64(op & I_BK, __hiloint2double((int)w1.y, (int)w1.x), *reinterpret_cast<const double *>(Sb + b));
-  const double vc = sel64(op & I_CK, __hiloint2double((int)w1.w, (int)w1.z), *reinterpret_cast<const double *>(Sb + c));
+  const uint32_t m = ~((op & I_AB) << 29);   // I_AB = 4: bit 31
+  const double va = absmask(*reinterpret_cast<const double *>(Sb + a), m);
+  const double vb = absmask(sel64(op & I_BK, __hiloint2double((int)w1.y, (int)w1.x), *reinterpret_cast<const double *>(Sb + b)), m);
+  const double vc = absmask(sel64(op & I_CK, __hiloint2double((int)w1.w, (int)w1.z), *reinterpret_cast<const double *>(Sb + c)), m);
   const uint32_t sp = op & 0xff00u;
   *reinterpret_cast<double *>(Sb + d) = sp == 0 ? __fma_rn(va, vb, vc) : special_op(sp, va, vb, vc);
 }
@@ -437,7 +469,8 @@ static __device__ void run_tape_dd(const GraphDev &G, dd *S) {
     const dd vc = (op & I_CK) ? dd{__ldg(G.khi + kci), __ldg(G.klo + kci)} : *reinterpret_cast<const dd *>(Sb + c);
     dd r;
     const uint32_t sp = op & 0xff00u;
-    if (sp == 0) r = dd_fma_fast(vc, vb, va);
+    if (op & I_AB) r = dd{__fma_rn(fabs(va.hi), fabs(vb.hi), fabs(vc.hi)), 0.0};   // magnitudes: FP64 is enough
+    else if (sp == 0) r = dd_fma_fast(vc, vb, va);
     else if (sp == I_DIV) r = dd_div(va, vb);
     else if (sp == I_ABS) r = dd_abs(va);
     else r = dd_add_fast(vc, dd_abs(va));   // I_ADDABS

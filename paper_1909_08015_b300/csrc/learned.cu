@@ -675,6 +675,14 @@ extern "C" int ae_set_proposal(ae_ctx *c, int gid, int mode, double beta) {
   return AE_OK;
 }
 
+extern "C" int ae_set_accept_floor(ae_ctx *c, int gid, double yfloor) {
+  if (!c) return AE_ERR_ARG;
+  if (gid < 0 || gid >= (int)c->graphs.size()) return ae_fail(c, AE_ERR_ARG, "graph id out of range");
+  if (!(yfloor >= 0) || !std::isfinite(yfloor)) return ae_fail(c, AE_ERR_ARG, "floor must be finite and >= 0");
+  c->graphs[gid].dev.yfloor = yfloor;
+  return AE_OK;
+}
+
 // Test entry: loss, gradient and tables for given parameters and samples
 // (host buffers), on the device, without sampling or training.
 extern "C" int ae_proposal_eval(ae_ctx *c, int M, const float *params, const double *deg, const double *wplain,

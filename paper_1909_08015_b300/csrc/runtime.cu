@@ -10,8 +10,11 @@
 //   double-double accumulation of sum y, sum y^2, sum |y| -> warp-shuffle
 //   and CTA reduction -> one partial per CTA (or chunk), summed on the host
 //   in fixed order.
-// Samples whose forest terms cancel badly (K > dd_ratio |I|) or whose value
-// is not finite are queued and re-evaluated by the double-double kernel.
+// Every FP64 evaluation carries a certified rounding-error bound E of I (the
+// tape's magnitude twins).  Samples whose bound, carried to y, exceeds
+// dd_tol * max(|y|, the graph's floor on |y|), or whose value is not finite,
+// are queued and re-evaluated by the double-double kernel, which applies the
+// same test at its own unit; samples that fail it too count as zero.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,10 +53,11 @@ static int fail(ae_ctx *c, int code, const std::string &msg) { return ae_fail(c,
 // contiguous chunk in rounds of blockDim.x samples (one per thread), each
 // round's tapes run together, staged through shared memory.
 __global__ void integrate_kernel(GraphDev Gp, uint64_t first, uint64_t count, uint64_t seed,
-                                 double dd_ratio, Partial *part, unsigned long long *queue,
+                                 double dd_tol, Partial *part, unsigned long long *queue,
                                  unsigned long long qcap, unsigned long long *qcount, int *err) {
   extern __shared__ __align__(128) unsigned char dsm[];
-  __shared__ GraphDev G;
+  __shared__ __align__(16) unsigned char Gmem[sizeof(GraphDev)];   // raw: no dynamic initialisation
+  GraphDev &G = *reinterpret_cast<GraphDev *>(Gmem);
   __shared__ uint64_t bars[2];
   Stage st{reinterpret_cast<Ins *>(dsm), bars, 0, 0};
   if (threadIdx.x == 0) { G = Gp; stage_init(st); }
@@ -76,10 +80,9 @@ __global__ void integrate_kernel(GraphDev Gp, uint64_t first, uint64_t count, ui
     }
     if (!run_tape_staged(st, G, S, active, base + blockDim.x < hi, err)) return;
     if (!active) continue;
-    double I = S[G.outI], Kv = S[G.outK];
-    double y = weight(I, lg);
-    bool bad = !isfinite(I) || !isfinite(Kv) || !isfinite(y) ||
-               (dd_ratio > 0 && Kv > dd_ratio * fabs(I));
+    double y, Ey;
+    weight2(S[G.outI], S[G.outE], lg, y, Ey);
+    const bool bad = fp64_rejected(G, y, Ey, dd_tol);
     p.n += 1;
     if (bad) {
       p.n_flag += 1;
@@ -99,7 +102,7 @@ __global__ void integrate_kernel(GraphDev Gp, uint64_t first, uint64_t count, ui
 // Double-double re-evaluation of queued samples: y_out[i] and status
 // (0 ok, 1 still failing -> the sample counts as zero).
 __global__ void dd_kernel(GraphDev G, uint64_t seed, const unsigned long long *queue, uint64_t nq,
-                          double dd_ratio, double *y_out, int *status) {
+                          double dd_tol, double *y_out, int *status) {
   extern __shared__ dd dslots[];
   dd *S = dslots + threadIdx.x * G.nslots;   // this thread's row of the slot file
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
@@ -108,12 +111,9 @@ __global__ void dd_kernel(GraphDev G, uint64_t seed, const unsigned long long *q
     draw_any(G, queue[i], seed, z, lz, lg);
     for (int k = 0; k < G.M; ++k) S[k] = {z[k], 0.0};
     run_tape_dd(G, S);
-    dd I = S[G.outI], K = S[G.outK];
-    double y = weight(I.hi + I.lo, lg);
-    // accepted when the double-double result keeps ~8 significant digits
-    // (2^-104 K / |I| below 1e-8)
-    bool bad = !isfinite(I.hi) || !isfinite(K.hi) || !isfinite(y) ||
-               K.hi > 2.0e23 * fabs(I.hi);
+    double y, Ey;
+    weight2(S[G.outI].hi + S[G.outI].lo, S[G.outE].hi, lg, y, Ey);
+    const bool bad = dd_rejected(G, y, Ey, dd_tol);
     y_out[i] = bad ? 0.0 : y;
     status[i] = bad ? 1 : 0;
   }
@@ -121,7 +121,7 @@ __global__ void dd_kernel(GraphDev G, uint64_t seed, const unsigned long long *q
 
 // Per-sample dump for parity tests.
 __global__ void eval_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t seed, double *z_out,
-                            double *lg_out, double *I_out, double *K_out, double *y_out) {
+                            double *lg_out, double *I_out, double *K_out, double *y_out, double *E_out) {
   extern __shared__ double slots[];
   double *S = slots + threadIdx.x * G.nslots;   // this thread's row of the slot file
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < count;
@@ -133,13 +133,13 @@ __global__ void eval_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t
     for (int k = 0; k < G.M; ++k) { S[k] = z[k]; z_out[i * G.M + k] = z[k]; }
     run_tape(G, S);
     double I = S[G.outI], Kv = S[G.outK];
-    lg_out[i] = lg; I_out[i] = I; K_out[i] = Kv; y_out[i] = weight(I, lg);
+    lg_out[i] = lg; I_out[i] = I; K_out[i] = Kv; y_out[i] = weight(I, lg); E_out[i] = S[G.outE];
   }
 }
 
 // Per-sample dump with every sample evaluated in double-double.
 __global__ void eval_dd_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t seed,
-                               double *I_out, double *K_out, double *y_out) {
+                               double *I_out, double *K_out, double *y_out, double *E_out) {
   extern __shared__ dd dslots2[];
   dd *S = dslots2 + threadIdx.x * G.nslots;   // this thread's row of the slot file
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < count;
@@ -153,6 +153,7 @@ __global__ void eval_dd_kernel(GraphDev G, uint64_t first, uint64_t count, uint6
     dd I = S[G.outI], K = S[G.outK];
     double Iv = I.hi + I.lo;
     I_out[i] = Iv; K_out[i] = K.hi + K.lo; y_out[i] = weight(Iv, lg);
+    E_out[i] = S[G.outE].hi * 0x1p-47;   // bound at the double-double unit
   }
 }
 
@@ -193,12 +194,13 @@ struct Chunk {
 // not depend on which CTA ran it.  Flagged samples go to the queue as
 // (graph, sample index).
 __global__ void batched_kernel(const GraphDev *graphs, const Chunk *chunks, int nchunks, uint64_t seed,
-                               double dd_ratio, Partial *part, unsigned long long *queue_idx, int *queue_gi,
+                               double dd_tol, Partial *part, unsigned long long *queue_idx, int *queue_gi,
                                unsigned long long qcap, unsigned long long *qcount, int *next, int *err) {
   // chunks/part point at this launch's slice of the chunk list
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ int cur, curg;
-  __shared__ GraphDev G;     // descriptor of the current chunk's graph
+  __shared__ __align__(16) unsigned char Gmem[sizeof(GraphDev)];   // raw: no dynamic initialisation
+  GraphDev &G = *reinterpret_cast<GraphDev *>(Gmem);               // descriptor of the current chunk's graph
   __shared__ uint64_t bars[2];
   Stage st{reinterpret_cast<Ins *>(dsm), bars, 0, 0};
   double z[14], lz[14];
@@ -228,9 +230,9 @@ __global__ void batched_kernel(const GraphDev *graphs, const Chunk *chunks, int 
       }
       if (!run_tape_staged(st, G, S, active, base + blockDim.x < ch.count, err)) return;
       if (!active) continue;
-      double I = S[G.outI], Kv = S[G.outK];
-      double y = weight(I, lg);
-      bool bad = !isfinite(I) || !isfinite(Kv) || !isfinite(y) || (dd_ratio > 0 && Kv > dd_ratio * fabs(I));
+      double y, Ey;
+      weight2(S[G.outI], S[G.outE], lg, y, Ey);
+      const bool bad = fp64_rejected(G, y, Ey, dd_tol);
       p.n += 1;
       if (bad) {
         p.n_flag += 1;
@@ -280,7 +282,7 @@ __global__ void queue_scatter_kernel(const unsigned long long *qi, const int *qg
 // of the launch (the largest of its bucket), not that of the thread's graph.
 __global__ void batched_dd_kernel(const GraphDev *graphs, uint64_t seed, const unsigned long long *queue_idx,
                                   const int *queue_gi, const unsigned int *beg, const unsigned int *end,
-                                  double *y_out, int *status, int pitch) {
+                                  double *y_out, int *status, int pitch, double dd_tol) {
   extern __shared__ dd bdsl[];
   dd *S = bdsl + threadIdx.x * pitch;   // this thread's row of the slot file
   uint64_t i0 = beg ? *beg : 0, i1 = *end;
@@ -290,9 +292,9 @@ __global__ void batched_dd_kernel(const GraphDev *graphs, uint64_t seed, const u
     draw_any(G, queue_idx[i], seed, z, lz, lg);
     for (int k = 0; k < G.M; ++k) S[k] = {z[k], 0.0};
     run_tape_dd(G, S);
-    dd I = S[G.outI], K = S[G.outK];
-    double y = weight(I.hi + I.lo, lg);
-    bool bad = !isfinite(I.hi) || !isfinite(K.hi) || !isfinite(y) || K.hi > 2.0e23 * fabs(I.hi);
+    double y, Ey;
+    weight2(S[G.outI].hi + S[G.outI].lo, S[G.outE].hi, lg, y, Ey);
+    const bool bad = dd_rejected(G, y, Ey, dd_tol);
     y_out[i] = bad ? 0.0 : y;
     status[i] = bad ? 1 : 0;
   }
@@ -318,7 +320,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes
 
 // Double-double pass writing by sample offset (deterministic order later).
 __global__ void dd_dense_kernel(GraphDev G, uint64_t first, uint64_t seed, const unsigned long long *queue,
-                                const unsigned long long *qcount, double *y_off, unsigned char *flag) {
+                                const unsigned long long *qcount, double *y_off, unsigned char *flag,
+                                double dd_tol) {
   extern __shared__ dd dsl3[];
   dd *S = dsl3 + threadIdx.x * G.nslots;   // this thread's row of the slot file
   uint64_t nq = *qcount;
@@ -329,9 +332,9 @@ __global__ void dd_dense_kernel(GraphDev G, uint64_t first, uint64_t seed, const
     draw_any(G, idx, seed, z, lz, lg);
     for (int k = 0; k < G.M; ++k) S[k] = {z[k], 0.0};
     run_tape_dd(G, S);
-    dd I = S[G.outI], K = S[G.outK];
-    double y = weight(I.hi + I.lo, lg);
-    bool bad = !isfinite(I.hi) || !isfinite(K.hi) || !isfinite(y) || K.hi > 2.0e23 * fabs(I.hi);
+    double y, Ey;
+    weight2(S[G.outI].hi + S[G.outI].lo, S[G.outE].hi, lg, y, Ey);
+    const bool bad = dd_rejected(G, y, Ey, dd_tol);
     y_off[idx - first] = bad ? 0.0 : y;
     flag[idx - first] = bad ? 2 : 1;
   }
@@ -371,7 +374,7 @@ extern "C" void ae_default_opts(ae_opts *o) {
   o->C_subI = 0.2; o->C_subSE = 0.0; o->C_subO = 0.2;
   o->C_bigZ = 0.256; o->C_bigF = 0.839; o->C_add = 0.786;
   o->deg_max = 1.0;
-  o->dd_ratio = 1e8;
+  o->dd_tol = 1e-10;
   o->block_size = 0;
   o->ctas_per_sm = 0;
   o->stream = nullptr;
@@ -543,7 +546,7 @@ static int load_impl(ae_ctx *c, int loops, const int *subset, int n_subset, int 
       CUDA_TRY(c, cudaMemcpy(p, lg.tape.code.data(), lg.tape.code.size() * sizeof(Ins), cudaMemcpyHostToDevice));
       p += al(lg.tape.code.size() * sizeof(Ins));
       G.M = lg.g.M(); G.ntape = (int)lg.tape.code.size(); G.nslots = lg.tape.nslots;
-      G.outI = lg.tape.out_I; G.outK = lg.tape.out_K; G.graph_id = canon[gi];   // random stream of the graph
+      G.outI = lg.tape.out_I; G.outK = lg.tape.out_K; G.outE = lg.tape.out_E; G.graph_id = canon[gi];   // random stream of the graph
       G.mrg = c->opts.rng == 1 ? c->d_mrg : nullptr;
       lg.canonical_id = canon[gi];
       G.C1 = lg.dens.C[0]; G.C2 = lg.dens.C[1]; G.C3 = lg.dens.C[2]; G.C4 = lg.dens.C[3];
@@ -568,6 +571,7 @@ extern "C" int ae_graph_info(ae_ctx *c, int id, ae_graph_meta *o) {
   o->tape_len = (int)lg.tape.code.size(); o->nslots = lg.tape.nslots;
   o->n_monomials = lg.st.n_monomials; o->flops = lg.tape.flops;
   o->canonical_id = lg.canonical_id;
+  o->bound_depth = lg.tape.depth; o->flops_bound = lg.tape.flops_bound;
   return AE_OK;
 }
 
@@ -575,10 +579,18 @@ extern "C" int ae_graph_info(ae_ctx *c, int id, ae_graph_meta *o) {
 // the candidate with the most resident warps per SM (the slot file, not the
 // register file, is what limits residency for long tapes), ties to the
 // larger block.
+// Largest block the kernel can launch with (its registers per thread).
+static int max_threads(const void *kernel) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, kernel) != cudaSuccess) return 0;
+  return a.maxThreadsPerBlock;
+}
+
 static int pick_block_for(const ae_ctx *c, const void *kernel, int nslots, size_t elem, size_t extra = 0) {
   const size_t smem_cap = 224 * 1024;
   if (c->opts.block_size > 0) {
     int bs = c->opts.block_size;
+    if (kernel && bs > max_threads(kernel)) return -1;
     return extra + (size_t)bs * nslots * elem > smem_cap ? -1 : bs;
   }
   int best = -1, best_warps = 0;
@@ -598,9 +610,6 @@ static int pick_block_for(const ae_ctx *c, const void *kernel, int nslots, size_
   return best;
 }
 
-static int pick_block(const ae_ctx *c, int nslots, size_t elem) {
-  return pick_block_for(c, nullptr, nslots, elem);
-}
 
 static int ensure_scratch(ae_ctx *c, size_t nparts, size_t qcap) {
   if (nparts > c->part_cap) {
@@ -662,7 +671,7 @@ static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_g
     cudaEvent_t e0, e1, ek;
     cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&ek);
     cudaEventRecord(e0, c->stream);
-    integrate_kernel<<<(unsigned)grid, bs, smem, c->stream>>>(G, start, len, seed, c->opts.dd_ratio, c->d_part,
+    integrate_kernel<<<(unsigned)grid, bs, smem, c->stream>>>(G, start, len, seed, c->opts.dd_tol, c->d_part,
                                                               c->d_queue, c->queue_cap, c->d_qcount,
                                                               (int *)(c->d_qcount + 1));
     CUDA_TRY(c, cudaGetLastError());
@@ -686,7 +695,7 @@ static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_g
       size_t sm2 = (size_t)bsd * G.nslots * 16;
       CUDA_TRY(c, cudaFuncSetAttribute(dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
       unsigned g2 = (unsigned)std::min<uint64_t>((nq + bsd - 1) / bsd, (uint64_t)c->sm_count * 8);
-      dd_kernel<<<g2, bsd, sm2, c->stream>>>(G, seed, c->d_queue, nq, c->opts.dd_ratio, c->d_yq, c->d_qstat);
+      dd_kernel<<<g2, bsd, sm2, c->stream>>>(G, seed, c->d_queue, nq, c->opts.dd_tol, c->d_yq, c->d_qstat);
       CUDA_TRY(c, cudaGetLastError());
       ++launches;
     }
@@ -762,7 +771,7 @@ extern "C" int ae_integrate_range(ae_ctx *c, int gid, uint64_t first, uint64_t c
   std::vector<uint64_t> ns = {count}, fs = {first};
   std::vector<ae_graph_result> res;
   double secs = 0;
-  int bs = pick_block(c, c->graphs[gid].dev.nslots, 8);
+  int bs = pick_block_for(c, (const void *)batched_kernel, c->graphs[gid].dev.nslots, 8, kStageBytes);
   if (bs < 0) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
   int rc = run_batched(c, ids, ns, fs, seed, bs, 16384, false, res, &secs);
   if (rc) return rc;
@@ -820,7 +829,6 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
                          bool use_graph, std::vector<ae_graph_result> &res, double *secs_out, bool full_queue) {
   int maxslots = 0;
   for (int g : ids) maxslots = std::max(maxslots, c->graphs[g].dev.nslots);
-  int per_sm = 1;
   // Buckets of similar slot-file size, one persistent launch each (a launch
   // sized for the largest tape would cut the occupancy of all the others);
   // inside a bucket, graphs by decreasing tape length (balances the tail).
@@ -840,7 +848,6 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   // Chunks graph by graph.  A graph gets at least ~2 chunks per resident CTA
   // when its budget allows, so the CTAs work on one or two tapes at a time and
   // the tape stays in L2 (many different tapes in flight thrash it).
-  uint64_t resident = (uint64_t)c->sm_count * per_sm;
   std::vector<Chunk> chunks;
   struct Launch { size_t c0, c1; int bs; size_t smem; unsigned grid; };
   std::vector<Launch> launches;
@@ -852,7 +859,7 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     Launch L;
     L.c0 = chunks.size();
     // block size: the tuned one if it fits, else the occupancy choice for this bucket
-    L.bs = (kStageBytes + (size_t)bs * bslots * 8 <= 224 * 1024)
+    L.bs = (kStageBytes + (size_t)bs * bslots * 8 <= 224 * 1024 && bs <= max_threads((const void *)batched_kernel))
                ? bs : pick_block_for(c, (const void *)batched_kernel, bslots, 8, kStageBytes);
     if (L.bs < 0) return fail(c, AE_ERR_STATE, "batched slot file does not fit in shared memory");
     L.smem = kStageBytes + (size_t)L.bs * bslots * 8;
@@ -872,7 +879,6 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     launches.push_back(L);
     k = k1;
   }
-  (void)resident;
   size_t smax = 0;
   for (const Launch &L : launches) smax = std::max(smax, L.smem);
   CUDA_TRY(c, cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
@@ -945,7 +951,6 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     }
   }
   if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ddmax);
-  unsigned grid = (unsigned)(c->sm_count * per_sm);
   unsigned grid2 = (unsigned)(c->sm_count * 4);
   cudaEvent_t e0 = nullptr, e1 = nullptr, ek = nullptr;
   // events recorded with cudaEventRecordExternal so that, inside a captured
@@ -960,7 +965,7 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     cudaMemsetAsync(hist, 0, ids.size() * 4, c->stream);
     for (size_t l = 0; l < launches.size(); ++l) {
       const Launch &L = launches[l];
-      batched_kernel<<<L.grid, L.bs, L.smem, c->stream>>>(dG, dC + L.c0, (int)(L.c1 - L.c0), seed, c->opts.dd_ratio,
+      batched_kernel<<<L.grid, L.bs, L.smem, c->stream>>>(dG, dC + L.c0, (int)(L.c1 - L.c0), seed, c->opts.dd_tol,
                                                           dP + L.c0, qi, qg, qcap, qcount, next + l, derr);
     }
     rec(ek);
@@ -972,7 +977,7 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     for (size_t l = 0; l < launches.size(); ++l) {
       const unsigned int *bg = l == 0 ? nullptr : hist + bucket_last[l - 1];
       batched_dd_kernel<<<grid2, dd_bs[l], dd_sm[l], c->stream>>>(dG, seed, qi2, qg2, bg, hist + bucket_last[l], qy, qs,
-                                                                  dd_pitch[l]);
+                                                                  dd_pitch[l], c->opts.dd_tol);
     }
     rec(e1);
   };
@@ -1060,10 +1065,11 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     r.sum_y = sy[gi] + syl[gi]; r.sum_y2 = sy2[gi] + sy2l[gi];
     r.n = n[gi]; r.n_dd = ndd[gi]; r.n_nonfinite = nbad[gi];
     double N = (double)r.n;
-    r.mean = r.sum_y / N;
-    double var = r.sum_y2 / (N * N) - r.sum_y * r.sum_y / (N * N * N);
+    // a graph given no samples contributes value 0 and sigma 0
+    r.mean = r.n ? r.sum_y / N : 0.0;
+    double var = r.n ? r.sum_y2 / (N * N) - r.sum_y * r.sum_y / (N * N * N) : 0.0;
     r.sigma1 = var > 0 ? std::sqrt(var) : 0.0;
-    r.mean_abs = (sa[gi] + sal[gi]) / N;
+    r.mean_abs = r.n ? (sa[gi] + sal[gi]) / N : 0.0;
     r.max_y2 = mx[gi];
     int mult = c->graphs[ids[gi]].g.mult;
     r.value = mult * r.mean;
@@ -1130,10 +1136,12 @@ extern "C" int ae_integrate_batched(ae_ctx *c, const int *ids, int n_ids, const 
   if (!ids || !ns || n_ids <= 0) return fail(c, AE_ERR_ARG, "empty graph list");
   std::vector<int> vid(ids, ids + n_ids);
   std::vector<uint64_t> vn(ns, ns + n_ids), vf(n_ids, 0);
+  uint64_t total = 0;
   for (int i = 0; i < n_ids; ++i) {
     if (ids[i] < 0 || ids[i] >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
-    if (ns[i] == 0) return fail(c, AE_ERR_ARG, "zero samples for a graph");
+    total += ns[i];
   }
+  if (total == 0) return fail(c, AE_ERR_ARG, "no samples requested");
   CUDA_TRY(c, cudaSetDevice(c->device));
   BatchTune t;
   if (c->opts.block_size > 0) { t.block = c->opts.block_size; t.chunk = 16384; }
@@ -1190,7 +1198,18 @@ extern "C" int ae_integrate_adaptive(ae_ctx *c, const int *ids, int n_ids, uint6
   int rc = autotune_batched(c, vid, tune);
   if (rc) return rc;
   uint64_t draw = 0;   // counter of the block-draw stream
+  // The first round is the initialisation pass: graphs without a floor of
+  // their own take its mean |y| as the floor of the acceptance test for the
+  // later rounds (restored on return).
+  struct FloorGuard {
+    ae_ctx *c; std::vector<int> ids; std::vector<double> old;
+    ~FloorGuard() { for (size_t i = 0; i < ids.size(); ++i) c->graphs[ids[i]].dev.yfloor = old[i]; }
+  } guard{c, vid, {}};
+  for (int id : vid) guard.old.push_back(c->graphs[id].dev.yfloor);
   for (int r = 0; r < n_rounds; ++r) {
+    if (r == 1)
+      for (size_t i = 0; i < G; ++i)
+        if (guard.old[i] == 0 && Nj[i] > 0) c->graphs[vid[i]].dev.yfloor = (sa[i] + sal[i]) / (double)Nj[i];
     std::vector<uint64_t> nb(G, 0);
     if (r == 0) {
       for (size_t i = 0; i < G; ++i) nb[i] = 1;
@@ -1300,23 +1319,23 @@ extern "C" int ae_allocate(ae_ctx *c, const int *ids, int n_ids, uint64_t n_pilo
 }
 
 extern "C" int ae_eval_samples(ae_ctx *c, int gid, uint64_t first, uint64_t count, uint64_t seed,
-                               double *z, double *log2g, double *I, double *K, double *y) {
+                               double *z, double *log2g, double *I, double *K, double *y, double *E) {
   if (!c) return AE_ERR_ARG;
   if (c->device < 0) return fail(c, AE_ERR_NODEV, "eval_samples needs a CUDA device");
   if (gid < 0 || gid >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
   if (count == 0) return AE_OK;
   CUDA_TRY(c, cudaSetDevice(c->device));
   GraphDev &G = c->graphs[gid].dev;
-  int bs = pick_block(c, G.nslots, 8);
+  int bs = pick_block_for(c, (const void *)eval_kernel, G.nslots, 8);
   if (bs < 0) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
   size_t smem = (size_t)bs * G.nslots * 8;
   CUDA_TRY(c, cudaFuncSetAttribute(eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   double *d = nullptr;
-  size_t per = (size_t)G.M + 4;
+  size_t per = (size_t)G.M + 5;
   CUDA_TRY(c, cudaMalloc(&d, count * per * 8));
-  double *dz = d, *dl = d + count * G.M, *dI = dl + count, *dK = dI + count, *dy = dK + count;
+  double *dz = d, *dl = d + count * G.M, *dI = dl + count, *dK = dI + count, *dy = dK + count, *dE = dy + count;
   unsigned grid = (unsigned)std::min<uint64_t>((count + bs - 1) / bs, (uint64_t)c->sm_count * 8);
-  eval_kernel<<<grid, bs, smem, c->stream>>>(G, first, count, seed, dz, dl, dI, dK, dy);
+  eval_kernel<<<grid, bs, smem, c->stream>>>(G, first, count, seed, dz, dl, dI, dK, dy, dE);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess && z) e = cudaMemcpy(z, dz, count * G.M * 8, cudaMemcpyDeviceToHost);
@@ -1324,6 +1343,7 @@ extern "C" int ae_eval_samples(ae_ctx *c, int gid, uint64_t first, uint64_t coun
   if (e == cudaSuccess && I) e = cudaMemcpy(I, dI, count * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && K) e = cudaMemcpy(K, dK, count * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && y) e = cudaMemcpy(y, dy, count * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && E) e = cudaMemcpy(E, dE, count * 8, cudaMemcpyDeviceToHost);
   cudaFree(d);
   if (e != cudaSuccess) return fail(c, AE_ERR_CUDA, std::string("eval_samples: ") + cudaGetErrorString(e));
   return AE_OK;
@@ -1380,14 +1400,15 @@ extern "C" int ae_integrate_noalloc(ae_ctx *c, int gid, uint64_t nsamp, uint64_t
   // per-sample flags
   CUDA_TRY(c, cudaMemsetAsync(qcount, 0, 2 * sizeof(unsigned long long), c->stream));
   CUDA_TRY(c, cudaMemsetAsync(flag, 0, nsamp, c->stream));
-  integrate_kernel<<<(unsigned)grid, bs, smem, c->stream>>>(G, 0, nsamp, seed, c->opts.dd_ratio, part, queue,
+  integrate_kernel<<<(unsigned)grid, bs, smem, c->stream>>>(G, 0, nsamp, seed, c->opts.dd_tol, part, queue,
                                                             kNaMaxSamples, qcount, werr);
   CUDA_TRY(c, cudaGetLastError());
-  int bsd = pick_block(c, G.nslots, 16);
+  int bsd = pick_block_for(c, (const void *)dd_dense_kernel, G.nslots, 16);
   if (bsd < 0) return fail(c, AE_ERR_STATE, "double-double slot file does not fit in shared memory");
   size_t sm2 = (size_t)bsd * G.nslots * 16;
   CUDA_TRY(c, cudaFuncSetAttribute(dd_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-  dd_dense_kernel<<<(unsigned)(c->sm_count * 2), bsd, sm2, c->stream>>>(G, 0, seed, queue, qcount, y_off, flag);
+  dd_dense_kernel<<<(unsigned)(c->sm_count * 2), bsd, sm2, c->stream>>>(G, 0, seed, queue, qcount, y_off, flag,
+                                                                        c->opts.dd_tol);
   CUDA_TRY(c, cudaGetLastError());
   noalloc_reduce_kernel<<<1, 256, 0, c->stream>>>(part, (int)grid, y_off, flag, nsamp, result);
   CUDA_TRY(c, cudaGetLastError());
@@ -1417,26 +1438,27 @@ extern "C" int ae_integrate_noalloc(ae_ctx *c, int gid, uint64_t nsamp, uint64_t
 }
 
 extern "C" int ae_eval_samples_dd(ae_ctx *c, int gid, uint64_t first, uint64_t count, uint64_t seed,
-                                  double *I, double *K, double *y) {
+                                  double *I, double *K, double *y, double *E) {
   if (!c) return AE_ERR_ARG;
   if (c->device < 0) return fail(c, AE_ERR_NODEV, "eval_samples_dd needs a CUDA device");
   if (gid < 0 || gid >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
   if (count == 0) return AE_OK;
   CUDA_TRY(c, cudaSetDevice(c->device));
   GraphDev &G = c->graphs[gid].dev;
-  int bs = pick_block(c, G.nslots, 16);
+  int bs = pick_block_for(c, (const void *)eval_dd_kernel, G.nslots, 16);
   if (bs < 0) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
   size_t smem = (size_t)bs * G.nslots * 16;
   CUDA_TRY(c, cudaFuncSetAttribute(eval_dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   double *d = nullptr;
-  CUDA_TRY(c, cudaMalloc(&d, count * 3 * 8));
+  CUDA_TRY(c, cudaMalloc(&d, count * 4 * 8));
   unsigned grid = (unsigned)std::min<uint64_t>((count + bs - 1) / bs, (uint64_t)c->sm_count * 8);
-  eval_dd_kernel<<<grid, bs, smem, c->stream>>>(G, first, count, seed, d, d + count, d + 2 * count);
+  eval_dd_kernel<<<grid, bs, smem, c->stream>>>(G, first, count, seed, d, d + count, d + 2 * count, d + 3 * count);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess && I) e = cudaMemcpy(I, d, count * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && K) e = cudaMemcpy(K, d + count, count * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && y) e = cudaMemcpy(y, d + 2 * count, count * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && E) e = cudaMemcpy(E, d + 3 * count, count * 8, cudaMemcpyDeviceToHost);
   cudaFree(d);
   if (e != cudaSuccess) return fail(c, AE_ERR_CUDA, std::string("eval_samples_dd: ") + cudaGetErrorString(e));
   return AE_OK;
@@ -1563,10 +1585,11 @@ extern "C" int aetest_fast_elem(ae_ctx *c, const double *x, const double *y, siz
   return AE_OK;
 }
 
-extern "C" int aetest_tape_replay(ae_ctx *c, int gid, const double *z, size_t count, double *I, double *K) {
+extern "C" int aetest_tape_replay(ae_ctx *c, int gid, const double *z, size_t count, double *I, double *K,
+                                  double *E) {
   if (!c || !z || !I || !K) return AE_ERR_ARG;
   if (gid < 0 || gid >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
   const Tape &t = c->graphs[gid].tape;
-  for (size_t i = 0; i < count; ++i) tape_replay(t, z + i * t.M, I + i, K + i);
+  for (size_t i = 0; i < count; ++i) tape_replay(t, z + i * t.M, I + i, K + i, E ? E + i : nullptr);
   return AE_OK;
 }

@@ -24,7 +24,7 @@ def main():
     a = ap.parse_args()
     o = default_opts()
     if a.no_dd:
-        o.dd_ratio = 0.0
+        o.dd_tol = 0.0
     c = Context(0, o)
     total = {1: 1, 2: 4, 3: 28, 4: 269, 5: 3213}[a.loops]
     ids = seeded_subset(total, min(a.graphs, total), 0)

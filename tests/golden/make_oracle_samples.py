@@ -3,7 +3,8 @@ CPU oracle (and nothing else) for a few graphs whose oracle set-up takes
 minutes, so that the GPU parity tests can compare against them without
 rebuilding the oracle's coefficient tables on every run.
 
-    python tests/golden/make_oracle_samples.py 4 0 5 134 --count 12
+    python tests/golden/make_oracle_samples.py 3 0 1 2 ... 27 --count 24
+    python tests/golden/make_oracle_samples.py 4 0 5 30 60 100 134 200 268 --count 12
 
 Each line: graph id, sample index, then z (M values), log2 g, I, K, all as
 hexadecimal floating-point literals (exact round trip).  Seed 0.

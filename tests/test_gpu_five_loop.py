@@ -15,6 +15,7 @@ from oracle.estimate import weight
 from oracle.graphs import enumerate_graphs
 from oracle.philox import uniforms
 from oracle.sampler import Density, sample
+from tests.acceptance import rejected
 
 pytestmark = pytest.mark.gpu
 
@@ -54,13 +55,12 @@ def test_five_loop_integration_sums(ctx5):
     for gi in range(len(CANON)):
         d = ctx5.eval_samples(gi, 0, N, seed=3)
         dd = ctx5.eval_samples_dd(gi, 0, N, seed=3)
-        flagged = ~np.isfinite(d["I"]) | ~np.isfinite(d["K"]) | ~np.isfinite(d["y"]) | \
-            (d["K"] > 1e8 * np.abs(d["I"]))
-        bad_dd = ~np.isfinite(dd["I"]) | ~np.isfinite(dd["K"]) | ~np.isfinite(dd["y"]) | \
-            (dd["K"] > 2.0e23 * np.abs(dd["I"]))
+        flagged = rejected(d["y"], d["E"], d["log2g"])
+        bad_dd = rejected(dd["y"], dd["E"], d["log2g"])
         y = np.where(flagged, np.where(bad_dd, 0.0, dd["y"]), d["y"])
         assert per[gi]["n"] == N
         assert per[gi]["n_dd"] == int(flagged.sum())
+        assert per[gi]["n_nonfinite"] == int((flagged & bad_dd).sum())
         sy = math.fsum(y)
         sy2 = math.fsum(y * y)
         assert abs(per[gi]["sum_y"] - sy) <= 1e-9 * abs(sy)

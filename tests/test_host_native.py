@@ -104,3 +104,25 @@ def test_host_context_refuses_device_calls(host):
         host.graph_info(5)
     with pytest.raises(ae.AeError, match="AE_ERR_ARG"):
         host.load_graphs(7)
+
+
+@pytest.mark.parametrize("n,ids,worst", [(2, [0, 1, 2, 3], 40), (3, [12], 30)])
+def test_error_bound_holds_at_worst_points(host, n, ids, worst):
+    """The tape's certified rounding-error bound E (magnitude twins, gamma_D
+    times the absolute-value evaluation) against the oracle's exact rational
+    integrand, at the sampler's most ill-conditioned points (largest E/|I|
+    out of 2048, which reach the sector corners where the forest terms
+    cancel): |I_fp64 - I_exact| <= E everywhere.  And E is informative:
+    at most 1e-10 |I| on the median point."""
+    from oracle.estimate import GraphOracle
+    host.load_graphs(n)
+    gs = enumerate_graphs(n)
+    for gi in ids:
+        pts = GraphOracle(gs[gi], gi).points(0, 2048, seed=11)
+        I, K, E = host.tape_replay(gi, pts["z"], bound=True)
+        r = E / np.abs(I)
+        assert np.median(r) < 1e-10
+        It = Integrand(gs[gi])
+        for k in np.argsort(-r)[:worst]:
+            ex = It.evaluate(pts["z"][k])[0]
+            assert abs(I[k] - ex) <= E[k] + 2.0 ** -52 * abs(ex), (gi, k, I[k], ex, E[k])
