@@ -490,9 +490,9 @@ __device__ __forceinline__ void dd_merge(double &hi, double &lo, double h2, doub
   hi = r.hi; lo = r.lo;
 }
 
-// Block reduction of the per-thread accumulators into one Partial.
-static __device__ void block_reduce(Partial p, Partial *out) {
-  __shared__ Partial red[32];
+// Warp reduction of the per-lane accumulators (fixed tree: lane 0 holds the
+// result, the same for any schedule).
+__device__ __forceinline__ void warp_reduce(Partial &p) {
   const unsigned full = 0xffffffffu;
   for (int off = 16; off > 0; off >>= 1) {
     Partial q;
@@ -508,6 +508,12 @@ static __device__ void block_reduce(Partial p, Partial *out) {
     p.max_y2 = fmax(p.max_y2, q.max_y2);
     p.n += q.n; p.n_flag += q.n_flag; p.n_overflow += q.n_overflow;
   }
+}
+
+// Block reduction of the per-thread accumulators into one Partial.
+static __device__ void block_reduce(Partial p, Partial *out) {
+  __shared__ Partial red[32];
+  warp_reduce(p);
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) red[wid] = p;
   __syncthreads();

@@ -99,10 +99,11 @@ __global__ void integrate_kernel(GraphDev Gp, uint64_t first, uint64_t count, ui
   block_reduce(p, part + blockIdx.x);
 }
 
-// Double-double re-evaluation of queued samples: y_out[i] and status
-// (0 ok, 1 still failing -> the sample counts as zero).
+// Double-double re-evaluation of queued samples, written to the sample's
+// dense slot (offset from `first`): y and a flag (1 re-evaluated, 2 still
+// failing -> the sample counts as zero).
 __global__ void dd_kernel(GraphDev G, uint64_t seed, const unsigned long long *queue, uint64_t nq,
-                          double dd_tol, double *y_out, int *status) {
+                          double dd_tol, uint64_t first, double *ydense, unsigned char *fdense) {
   extern __shared__ dd dslots[];
   dd *S = dslots + threadIdx.x * G.nslots;   // this thread's row of the slot file
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
@@ -114,8 +115,8 @@ __global__ void dd_kernel(GraphDev G, uint64_t seed, const unsigned long long *q
     double y, Ey;
     weight2(S[G.outI].hi + S[G.outI].lo, S[G.outE].hi, lg, y, Ey);
     const bool bad = dd_rejected(G, y, Ey, dd_tol);
-    y_out[i] = bad ? 0.0 : y;
-    status[i] = bad ? 1 : 0;
+    ydense[queue[i] - first] = bad ? 0.0 : y;
+    fdense[queue[i] - first] = bad ? 2 : 1;
   }
 }
 
@@ -282,7 +283,8 @@ __global__ void queue_scatter_kernel(const unsigned long long *qi, const int *qg
 // of the launch (the largest of its bucket), not that of the thread's graph.
 __global__ void batched_dd_kernel(const GraphDev *graphs, uint64_t seed, const unsigned long long *queue_idx,
                                   const int *queue_gi, const unsigned int *beg, const unsigned int *end,
-                                  double *y_out, int *status, int pitch, double dd_tol) {
+                                  const unsigned long long *gpos, double *ydense, unsigned char *fdense,
+                                  int pitch, double dd_tol) {
   extern __shared__ dd bdsl[];
   dd *S = bdsl + threadIdx.x * pitch;   // this thread's row of the slot file
   uint64_t i0 = beg ? *beg : 0, i1 = *end;
@@ -295,8 +297,66 @@ __global__ void batched_dd_kernel(const GraphDev *graphs, uint64_t seed, const u
     double y, Ey;
     weight2(S[G.outI].hi + S[G.outI].lo, S[G.outE].hi, lg, y, Ey);
     const bool bad = dd_rejected(G, y, Ey, dd_tol);
-    y_out[i] = bad ? 0.0 : y;
-    status[i] = bad ? 1 : 0;
+    // dense slot of the sample: the graph's base in this launch + offset
+    const int gq = queue_gi[i];
+    const unsigned long long pos = gpos[2 * gq] + (queue_idx[i] - gpos[2 * gq + 1]);
+    ydense[pos] = bad ? 0.0 : y;
+    fdense[pos] = bad ? 2 : 1;
+  }
+}
+
+// Re-evaluated samples of each chunk, summed in sample order: one warp per
+// chunk, lane l taking offsets l, l+32, ... (flags 1 = re-evaluated, 2 =
+// zeroed), then the fixed warp tree.  n_flag counts re-evaluated samples,
+// n_overflow the zeroed ones.  The result does not depend on the order in
+// which the double-double pass ran.
+__global__ void chunk_dd_reduce_kernel(const Chunk *chunks, int nchunks, const unsigned long long *gpos,
+                                       const double *ydense, const unsigned char *fdense, Partial *out) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); c < nchunks; c += warps) {
+    const Chunk ch = chunks[c];
+    const unsigned long long pos0 = gpos[2 * ch.gi] + (ch.first - gpos[2 * ch.gi + 1]);
+    Partial p = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (unsigned long long o = lane; o < ch.count; o += 32) {
+      const unsigned char f = fdense[pos0 + o];
+      if (!f) continue;
+      const double y = ydense[pos0 + o];
+      p.n_flag += 1;
+      if (f == 2) p.n_overflow += 1;
+      dd_acc(p.sy_hi, p.sy_lo, y);
+      dd_acc(p.sy2_hi, p.sy2_lo, y * y);
+      dd_acc(p.sa_hi, p.sa_lo, fabs(y));
+      p.max_y2 = fmax(p.max_y2, y * y);
+    }
+    warp_reduce(p);
+    if (lane == 0) out[c] = p;
+  }
+}
+
+// Same sums over a dense range of len samples cut into segments of seg:
+// one warp per segment, segment s to out[s].
+__global__ void dense_dd_reduce_kernel(uint64_t len, uint64_t seg, const double *ydense,
+                                       const unsigned char *fdense, Partial *out) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t nseg = (len + seg - 1) / seg;
+  const uint64_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint64_t sg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sg < nseg; sg += warps) {
+    const uint64_t pos0 = sg * seg, cnt = min(seg, len - pos0);
+    Partial p = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint64_t o = lane; o < cnt; o += 32) {
+      const unsigned char f = fdense[pos0 + o];
+      if (!f) continue;
+      const double y = ydense[pos0 + o];
+      p.n_flag += 1;
+      if (f == 2) p.n_overflow += 1;
+      dd_acc(p.sy_hi, p.sy_lo, y);
+      dd_acc(p.sy2_hi, p.sy2_lo, y * y);
+      dd_acc(p.sa_hi, p.sa_lo, fabs(y));
+      p.max_y2 = fmax(p.max_y2, y * y);
+    }
+    warp_reduce(p);
+    if (lane == 0) out[sg] = p;
   }
 }
 
@@ -664,10 +724,16 @@ static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_g
     uint64_t grid = (uint64_t)c->sm_count * per_sm;
     if (grid * bs > len) grid = std::max<uint64_t>(1, (len + bs - 1) / bs);
     size_t qcap = (size_t)std::max<uint64_t>(len, 65536);   // every sample may need re-evaluation
-    int rc = ensure_scratch(c, grid, qcap);
+    const uint64_t SEG = 1ull << 14;
+    const uint64_t nseg = (len + SEG - 1) / SEG;
+    int rc = ensure_scratch(c, grid + nseg, qcap);
     if (rc) return rc;
+    // dense double-double results of the slice: y in d_yq, flags in d_qstat
+    double *ydense = c->d_yq;
+    unsigned char *fdense = reinterpret_cast<unsigned char *>(c->d_qstat);
     // d_qcount[0]: queue length, d_qcount[1]: wait-timeout flag
     CUDA_TRY(c, cudaMemsetAsync(c->d_qcount, 0, 2 * sizeof(unsigned long long), c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(fdense, 0, len, c->stream));
     cudaEvent_t e0, e1, ek;
     cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&ek);
     cudaEventRecord(e0, c->stream);
@@ -695,21 +761,17 @@ static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_g
       size_t sm2 = (size_t)bsd * G.nslots * 16;
       CUDA_TRY(c, cudaFuncSetAttribute(dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
       unsigned g2 = (unsigned)std::min<uint64_t>((nq + bsd - 1) / bsd, (uint64_t)c->sm_count * 8);
-      dd_kernel<<<g2, bsd, sm2, c->stream>>>(G, seed, c->d_queue, nq, c->opts.dd_tol, c->d_yq, c->d_qstat);
+      dd_kernel<<<g2, bsd, sm2, c->stream>>>(G, seed, c->d_queue, nq, c->opts.dd_tol, start, ydense, fdense);
       CUDA_TRY(c, cudaGetLastError());
-      ++launches;
+      dense_dd_reduce_kernel<<<(unsigned)std::min<uint64_t>((nseg + 7) / 8, (uint64_t)c->sm_count * 16), 256, 0,
+                               c->stream>>>(len, SEG, ydense, fdense, c->d_part + grid);
+      CUDA_TRY(c, cudaGetLastError());
+      launches += 2;
     }
     cudaEventRecord(e1, c->stream);
-    std::vector<Partial> parts(grid);
-    CUDA_TRY(c, cudaMemcpyAsync(parts.data(), c->d_part, grid * sizeof(Partial), cudaMemcpyDeviceToHost, c->stream));
-    std::vector<unsigned long long> q(nq);
-    std::vector<double> yq(nq);
-    std::vector<int> qs(nq);
-    if (nq) {
-      CUDA_TRY(c, cudaMemcpyAsync(q.data(), c->d_queue, nq * 8, cudaMemcpyDeviceToHost, c->stream));
-      CUDA_TRY(c, cudaMemcpyAsync(yq.data(), c->d_yq, nq * 8, cudaMemcpyDeviceToHost, c->stream));
-      CUDA_TRY(c, cudaMemcpyAsync(qs.data(), c->d_qstat, nq * 4, cudaMemcpyDeviceToHost, c->stream));
-    }
+    const size_t np = nq ? grid + nseg : grid;
+    std::vector<Partial> parts(np);
+    CUDA_TRY(c, cudaMemcpyAsync(parts.data(), c->d_part, np * sizeof(Partial), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     float ms = 0, mk = 0;
     cudaEventElapsedTime(&ms, e0, e1);
@@ -717,25 +779,18 @@ static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_g
     cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(ek);
     secs += ms * 1e-3;
     ksecs += mk * 1e-3;
-    d2h += sizeof(unsigned long long) + grid * sizeof(Partial) + nq * (8 + 8 + 4);
-    for (auto &p : parts) {
+    d2h += 2 * sizeof(unsigned long long) + np * sizeof(Partial);
+    // CTA partials in CTA order, then the re-evaluated samples' segment sums
+    // in segment order (deterministic)
+    for (size_t k = 0; k < np; ++k) {
+      const Partial &p = parts[k];
       host_dd_add(sy, syl, p.sy_hi); host_dd_add(sy, syl, p.sy_lo);
       host_dd_add(sy2, sy2l, p.sy2_hi); host_dd_add(sy2, sy2l, p.sy2_lo);
       host_dd_add(sa, sal, p.sa_hi); host_dd_add(sa, sal, p.sa_lo);
       mx = std::max(mx, p.max_y2);
-      n += p.n;
+      if (k < grid) n += p.n;
+      else { ndd += p.n_flag; nbad += p.n_overflow; }
     }
-    // queued samples in sample order (deterministic)
-    std::vector<size_t> ord(nq);
-    for (size_t i = 0; i < nq; ++i) ord[i] = i;
-    std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return q[a] < q[b]; });
-    for (size_t t : ord) {
-      double y = yq[t];
-      if (qs[t]) ++nbad;
-      host_dd_add(sy, syl, y); host_dd_add(sy2, sy2l, y * y); host_dd_add(sa, sal, std::fabs(y));
-      mx = std::max(mx, y * y);
-    }
-    ndd += nq;
   }
   res->sum_y = sy + syl; res->sum_y2 = sy2 + sy2l;
   res->n = n; res->n_dd = ndd; res->n_nonfinite = nbad;
@@ -888,8 +943,9 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   size_t qcap = (size_t)std::max<uint64_t>(full_queue ? total : total / 4, 65536);
   // device buffers (graph descriptors, chunks, partials, queue), kept in the
   // context and grown when a larger batch arrives
-  size_t need = ids.size() * sizeof(GraphDev) + nch * sizeof(Chunk) + nch * sizeof(Partial) +
-                qcap * (8 + 4 + 8 + 4 + 8 + 4) + ids.size() * 8 + 64 * 4 + 8 * 768;
+  // dense double-double results: one y and one flag byte per sample of the batch
+  size_t need = ids.size() * sizeof(GraphDev) + nch * sizeof(Chunk) + 2 * nch * sizeof(Partial) +
+                qcap * (8 + 4 + 8 + 4) + ids.size() * (8 + 16) + total * 9 + 64 * 4 + 8 * 1024;
   if (need > c->bbuf_bytes) {
     if (c->bbuf) cudaFree(c->bbuf);
     c->bbuf = nullptr;
@@ -903,10 +959,12 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   GraphDev *dG = (GraphDev *)p; p += al(ids.size() * sizeof(GraphDev));
   Chunk *dC = (Chunk *)p; p += al(nch * sizeof(Chunk));
   Partial *dP = (Partial *)p; p += al(nch * sizeof(Partial));
+  Partial *dP2 = (Partial *)p; p += al(nch * sizeof(Partial));
   unsigned long long *qi = (unsigned long long *)p; p += al(qcap * 8);
   int *qg = (int *)p; p += al(qcap * 4);
-  double *qy = (double *)p; p += al(qcap * 8);
-  int *qs = (int *)p; p += al(qcap * 4);
+  unsigned long long *gpos = (unsigned long long *)p; p += al(ids.size() * 16);
+  double *ydense = (double *)p; p += al(total * 8);
+  unsigned char *fdense = (unsigned char *)p; p += al(total);
   unsigned long long *qi2 = (unsigned long long *)p; p += al(qcap * 8);
   int *qg2 = (int *)p; p += al(qcap * 4);
   unsigned int *hist = (unsigned int *)p; p += al(ids.size() * 4);
@@ -932,6 +990,14 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   cudaError_t e = cudaMemcpyAsync(dG, hg.data(), hg.size() * sizeof(GraphDev), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(drank, hrank.data(), hrank.size() * 4, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dC, chunks.data(), nch * sizeof(Chunk), cudaMemcpyHostToDevice, c->stream);
+  // dense layout of the batch: graph i's samples firsts[i] .. firsts[i]+ns[i]-1
+  // at base_i .. base_i+ns[i]-1, bases in id order
+  std::vector<unsigned long long> hgpos(2 * ids.size());
+  {
+    unsigned long long base = 0;
+    for (size_t i = 0; i < ids.size(); ++i) { hgpos[2 * i] = base; hgpos[2 * i + 1] = firsts[i]; base += ns[i]; }
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(gpos, hgpos.data(), hgpos.size() * 8, cudaMemcpyHostToDevice, c->stream);
   // one double-double launch per bucket, shaped for that bucket's slots
   std::vector<int> dd_bs(launches.size()), dd_pitch(launches.size());
   std::vector<size_t> dd_sm(launches.size());
@@ -963,6 +1029,7 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     rec(e0);
     cudaMemsetAsync(qcount, 0, 256, c->stream);
     cudaMemsetAsync(hist, 0, ids.size() * 4, c->stream);
+    cudaMemsetAsync(fdense, 0, total, c->stream);
     for (size_t l = 0; l < launches.size(); ++l) {
       const Launch &L = launches[l];
       batched_kernel<<<L.grid, L.bs, L.smem, c->stream>>>(dG, dC + L.c0, (int)(L.c1 - L.c0), seed, c->opts.dd_tol,
@@ -976,9 +1043,11 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     // [hist[last of l-1], hist[last of l])
     for (size_t l = 0; l < launches.size(); ++l) {
       const unsigned int *bg = l == 0 ? nullptr : hist + bucket_last[l - 1];
-      batched_dd_kernel<<<grid2, dd_bs[l], dd_sm[l], c->stream>>>(dG, seed, qi2, qg2, bg, hist + bucket_last[l], qy, qs,
-                                                                  dd_pitch[l], c->opts.dd_tol);
+      batched_dd_kernel<<<grid2, dd_bs[l], dd_sm[l], c->stream>>>(dG, seed, qi2, qg2, bg, hist + bucket_last[l], gpos,
+                                                                  ydense, fdense, dd_pitch[l], c->opts.dd_tol);
     }
+    chunk_dd_reduce_kernel<<<(unsigned)std::min<size_t>((nch + 7) / 8, (size_t)c->sm_count * 16), 256, 0,
+                             c->stream>>>(dC, (int)nch, gpos, ydense, fdense, dP2);
     rec(e1);
   };
   cudaGraph_t graph = nullptr;
@@ -1001,10 +1070,11 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   }
   unsigned long long nq = 0;
   int herr = 0;
-  std::vector<Partial> parts(nch);
+  std::vector<Partial> parts(nch), parts2(nch);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nq, qcount, 8, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(parts.data(), dP, nch * sizeof(Partial), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(parts2.data(), dP2, nch * sizeof(Partial), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   float ms = 0, mk = 0;
   if (e == cudaSuccess) {
@@ -1012,15 +1082,6 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     if (t1 != cudaSuccess || t2 != cudaSuccess) e = t1 != cudaSuccess ? t1 : t2;
   }
   nq = std::min<unsigned long long>(nq, qcap);
-  std::vector<unsigned long long> hq(nq);
-  std::vector<int> hgq(nq), hs(nq);
-  std::vector<double> hy(nq);
-  if (e == cudaSuccess && nq) {
-    e = cudaMemcpy(hq.data(), qi2, nq * 8, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(hgq.data(), qg2, nq * 4, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(hy.data(), qy, nq * 8, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(hs.data(), qs, nq * 4, cudaMemcpyDeviceToHost);
-  }
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
   if (e0) cudaEventDestroy(e0);
@@ -1031,8 +1092,8 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   for (auto &pp : parts)
     if (pp.n_overflow) return fail(c, AE_ERR_STATE, "double-double queue overflow");
   (void)buf;
-  // per graph: chunk partials in chunk order, then re-evaluated samples in
-  // sample order
+  // per graph, in chunk order: each chunk's FP64 partial, then the sums of
+  // its re-evaluated samples (in sample order, reduced on the device)
   size_t G = ids.size();
   std::vector<double> sy(G, 0), syl(G, 0), sy2(G, 0), sy2l(G, 0), sa(G, 0), sal(G, 0), mx(G, 0);
   std::vector<uint64_t> n(G, 0), ndd(G, 0), nbad(G, 0);
@@ -1044,19 +1105,12 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     host_dd_add(sa[gi], sal[gi], q.sa_hi); host_dd_add(sa[gi], sal[gi], q.sa_lo);
     mx[gi] = std::max(mx[gi], q.max_y2);
     n[gi] += q.n;
-  }
-  std::vector<size_t> ord(nq);
-  for (size_t i = 0; i < nq; ++i) ord[i] = i;
-  std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) {
-    return hgq[a] != hgq[b] ? hgq[a] < hgq[b] : hq[a] < hq[b];
-  });
-  for (size_t t : ord) {
-    int gi = hgq[t];
-    double y = hy[t];
-    if (hs[t]) ++nbad[gi];
-    ++ndd[gi];
-    host_dd_add(sy[gi], syl[gi], y); host_dd_add(sy2[gi], sy2l[gi], y * y); host_dd_add(sa[gi], sal[gi], std::fabs(y));
-    mx[gi] = std::max(mx[gi], y * y);
+    const Partial &r = parts2[k];
+    host_dd_add(sy[gi], syl[gi], r.sy_hi); host_dd_add(sy[gi], syl[gi], r.sy_lo);
+    host_dd_add(sy2[gi], sy2l[gi], r.sy2_hi); host_dd_add(sy2[gi], sy2l[gi], r.sy2_lo);
+    host_dd_add(sa[gi], sal[gi], r.sa_hi); host_dd_add(sa[gi], sal[gi], r.sa_lo);
+    mx[gi] = std::max(mx[gi], r.max_y2);
+    ndd[gi] += r.n_flag; nbad[gi] += r.n_overflow;
   }
   res.assign(G, ae_graph_result{});
   for (size_t gi = 0; gi < G; ++gi) {
@@ -1076,9 +1130,9 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     r.sigma = mult * r.sigma1;
     r.seconds = ms * 1e-3 * (double)ns[gi] / (double)total;   // share of the launch by samples
     r.kernel_seconds = mk * 1e-3 * (double)ns[gi] / (double)total;
-    r.launches = gi == 0 ? (uint64_t)(2 * launches.size() + 3) : 0;
-    r.d2h_bytes = gi == 0 ? (8 + nch * sizeof(Partial) + nq * 24) : 0;
-    r.h2d_bytes = gi == 0 ? (ids.size() * sizeof(GraphDev) + nch * sizeof(Chunk)) : 0;
+    r.launches = gi == 0 ? (uint64_t)(2 * launches.size() + 4) : 0;
+    r.d2h_bytes = gi == 0 ? (8 + 4 + 2 * nch * sizeof(Partial)) : 0;
+    r.h2d_bytes = gi == 0 ? (ids.size() * (sizeof(GraphDev) + 4 + 16) + nch * sizeof(Chunk)) : 0;
   }
   if (secs_out) *secs_out = ms * 1e-3;
   return AE_OK;
