@@ -139,6 +139,10 @@ static_assert(sizeof(Ins) == 32, "Ins must be 32 bytes");
 enum : uint16_t {
   I_BK = 1, I_CK = 2,
   I_AB = 4,           // S[d] = |S[a]| * |kb or S[b]| + |kc or S[c]|
+  // hints for the double-double evaluation (the FP64 interpreter ignores them)
+  I_KX = 8,           // every constant operand is an exact double (no low part)
+  I_C0 = 16,          // c is the constant 0: a product
+  I_B1 = 32,          // b is the constant +1 or -1: a sum
   I_DIV = 1 << 8,     // S[d] = S[a] / S[b]
   I_ABS = 2 << 8,     // S[d] = |S[a]|
   I_ADDABS = 3 << 8,  // S[d] = S[c] + |S[a]|

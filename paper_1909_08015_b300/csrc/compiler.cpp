@@ -1344,6 +1344,12 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
         break;
       default: throw std::runtime_error("unknown intermediate operation");
     }
+    if (!(o.op & 0xff00) && !(o.op & I_AB)) {
+      const bool bx = !(o.op & I_BK) || B.klo[o.kbi] == 0.0, cx = !(o.op & I_CK) || B.klo[o.kci] == 0.0;
+      if (bx && cx) o.op |= I_KX;
+      if ((o.op & I_CK) && o.kc == 0.0 && cx) o.op |= I_C0;
+      if ((o.op & I_BK) && (o.kb == 1.0 || o.kb == -1.0) && bx) o.op |= I_B1;
+    }
     o.d = (uint16_t)(l.sd * 8);
     o.a = (uint16_t)(a * 8);
     o.b = (uint16_t)(bb * 8);

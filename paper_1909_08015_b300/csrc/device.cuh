@@ -299,6 +299,19 @@ __device__ __forceinline__ dd dd_mul_fast(dd a, dd b) {
   e = __fma_rn(a.hi, b.lo, __fma_rn(a.lo, b.hi, e));
   return quick_two_sum(p, e);
 }
+// k an exact double: k*a (no addend) and d + k*a
+__device__ __forceinline__ dd dd_scale_x(double k, dd a) {
+  double p = __dmul_rn(k, a.hi);
+  double e = __fma_rn(k, a.lo, __fma_rn(k, a.hi, -p));
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ dd dd_fma_x(dd d, double k, dd a) {
+  double p = __dmul_rn(k, a.hi);
+  double e = __fma_rn(k, a.lo, __fma_rn(k, a.hi, -p));
+  dd s = two_sum(d.hi, p);
+  s.lo = __dadd_rn(s.lo, __dadd_rn(d.lo, e));
+  return quick_two_sum(s.hi, s.lo);
+}
 __device__ __forceinline__ dd dd_fma_fast(dd d, dd k, dd a) {
   double p = __dmul_rn(k.hi, a.hi);
   double e = __fma_rn(k.hi, a.hi, -p);

@@ -454,9 +454,9 @@ static __device__ bool run_tape_staged(Stage &st, const GraphDev &G, double *S, 
 }
 
 // Double-double twin of run_tape (rows of hi/lo pairs; offsets scaled by 2;
-// constants with their low parts from the pool).  Every result is stored at
-// once, so forwarded operands are read from their slots and I_NOST is
-// ignored.
+// constants with their low parts from the pool).  Magnitude twins stay in
+// FP64 (their low parts are zero); the compiler's hints I_KX, I_C0, I_B1
+// select the shorter exact forms of a product, a scaling and a sum.
 static __device__ void run_tape_dd(const GraphDev &G, dd *S) {
   char *Sb = reinterpret_cast<char *>(S);
   const uint4 *code = reinterpret_cast<const uint4 *>(G.code);
@@ -470,7 +470,14 @@ static __device__ void run_tape_dd(const GraphDev &G, dd *S) {
     dd r;
     const uint32_t sp = op & 0xff00u;
     if (op & I_AB) r = dd{__fma_rn(fabs(va.hi), fabs(vb.hi), fabs(vc.hi)), 0.0};   // magnitudes: FP64 is enough
-    else if (sp == 0) r = dd_fma_fast(vc, vb, va);
+    else if (sp == 0) {
+      // the compiler's hints pick the shortest exact form of c + a*b
+      const bool bx = (op & (I_BK | I_KX)) == (I_BK | I_KX);   // b an exact constant
+      if (op & I_C0) r = bx ? dd_scale_x(vb.hi, va) : dd_mul_fast(va, vb);
+      else if (op & I_B1) r = dd_add_fast(vc, vb.hi > 0 ? va : dd{-va.hi, -va.lo});
+      else if (bx) r = dd_fma_x(vc, vb.hi, va);
+      else r = dd_fma_fast(vc, vb, va);
+    }
     else if (sp == I_DIV) r = dd_div(va, vb);
     else if (sp == I_ABS) r = dd_abs(va);
     else r = dd_add_fast(vc, dd_abs(va));   // I_ADDABS
