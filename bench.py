@@ -257,7 +257,7 @@ def main():
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
 
-    # initialisation pass (Sec. III.A): 2^16 samples per graph; their mean |y|
+    # initialisation pass (Sec. IV.A): 2^16 samples per graph; their mean |y|
     # becomes the graph's floor in the acceptance test of FP64 values (a
     # value is kept when its certified rounding bound, carried to y, is at
     # most 1e-10 max(|y|, floor); the rest are re-evaluated in double-double)

@@ -101,7 +101,7 @@ typedef struct ae_graph_meta {
                             error bound's magnitude twins included */
   int canonical_id;      /* index in the full canonical list */
   int bound_depth;       /* D: roundings on the deepest chain into I; the
-                            bound is gamma_D M_I (Sec. III.A, library reading) */
+                            bound is gamma_D M_I (Sec. IV.A, library reading) */
   double flops_bound;    /* of flops, those of the magnitude twins */
 } ae_graph_meta;
 int ae_graph_info(ae_ctx *ctx, int graph_id, ae_graph_meta *out);
@@ -214,7 +214,7 @@ int ae_set_proposal(ae_ctx *ctx, int graph_id, int mode, double beta);
  * ae_opts.dd_tol): a value is kept when its bound is at most
  * dd_tol * max(|y|, yfloor).  0 (the default) makes the test relative to
  * each sample.  The paper fixes its tolerance from an initialisation pass
- * (Sec. III.A, Eq. eq_interval_accept: a quarter of the graph's expected
+ * (Sec. IV.A, Eq. eq_interval_accept: a quarter of the graph's expected
  * sigma); the library leaves the scale to the caller, e.g. the mean |y| of
  * a pilot, which keeps the summed rounding error of N samples below
  * 2 dd_tol N mean|y|.  yfloor finite and >= 0. */

@@ -1,7 +1,8 @@
 // Integrand compiler: from a graph to a straight-line FP64 tape that
-// evaluates the subtracted Feynman-parametric integrand I(z) and the sum of
-// the absolute values of its forest terms K(z) (Sec. II, Sec. III.A,
-// Eq. eq_feyn_integral; Sec. IV.A on splitting integrand code).
+// evaluates the subtracted Feynman-parametric integrand I(z), the sum of
+// the absolute values of its forest terms K(z) and a certified bound E(z)
+// of the rounding error of I (Sec. II, Eq. eq_feyn_integral; Sec. IV.A on
+// round-off control and on splitting integrand code).
 //
 // Construction (the paper defers the formulas to earlier work; this is the
 // library's reading, stated once here):
@@ -1089,7 +1090,7 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
   dce({outI, outK});
   // ------------------------------------------------ running error bound --
   // The paper certifies every FP64 value with an interval whose radius is
-  // estimated next to the centres (Sec. III.A, Eq. eq_interval_accept).  The
+  // estimated next to the centres (Sec. IV.A, Eq. eq_interval_accept).  The
   // library's form of that estimate is the classical running bound for
   // straight-line code: a value reached through k roundings on its deepest
   // chain lies within gamma_k * M of the exact one, M being the same

@@ -169,7 +169,7 @@ __device__ __forceinline__ void weight2(double I, double E, double lg, double &y
   Ey = ldexp(__dmul_rn(E, s), -kc);
 }
 
-// Acceptance of a value (Sec. III.A, Eq. eq_interval_accept, library
+// Acceptance of a value (Sec. IV.A, Eq. eq_interval_accept, library
 // reading): the certified rounding-error bound of I, carried to y = I/g like
 // I, must not exceed tol * max(|y|, yfloor).  tol <= 0 accepts every finite
 // value.  For the double-double twin the bound is scaled from the FP64 unit

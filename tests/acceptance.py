@@ -1,5 +1,5 @@
 """The library's acceptance test of an integrand value, restated for the tests
-(Sec. III.A, Eq. eq_interval_accept, library reading): a sample's value is
+(Sec. IV.A, Eq. eq_interval_accept, library reading): a sample's value is
 kept when its certified rounding-error bound E, carried to y = I/g like I,
 is at most tol * max(|y|, floor).  The FP64 dump returns E at the FP64 unit,
 the double-double dump at its own unit, so one function serves both."""
