@@ -206,6 +206,8 @@ def main():
     ap.add_argument("--samples", type=int, default=1 << 24, help="samples per graph per step")
     ap.add_argument("--train", type=int, default=1 << 20, help="training samples per graph")
     ap.add_argument("--train-steps", type=int, default=150)
+    ap.add_argument("--cost-ratio", type=float, default=0.0,
+                    help="cost-aware proposal training: weight |y|/sqrt(1+R) for samples that need double-double")
     ap.add_argument("--plain", action="store_true", help="time the plain density only, one launch per graph")
     ap.add_argument("--plain-batched", action="store_true",
                     help="time the plain density in the batched persistent launch with pilot allocation")
@@ -249,15 +251,7 @@ def main():
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MB > L2
     learned = not args.plain and not args.plain_batched
     batched = not args.plain
-    train_s = 0.0
-    if learned:
-        t0 = time.perf_counter()
-        for i in ids:
-            ctx.train_proposal(i, args.train, seed=7 + rank, steps=args.train_steps, lr=3e-3, beta=0.1)
-        torch.cuda.synchronize()
-        train_s = time.perf_counter() - t0
-
-    # initialisation pass (Sec. IV.A): 2^16 samples per graph; their mean |y|
+    # initialisation pass (Sec. IV.A), plain density: 2^16 samples per graph; their mean |y|
     # becomes the graph's floor in the acceptance test of FP64 values (a
     # value is kept when its certified rounding bound, carried to y, is at
     # most 1e-10 max(|y|, floor); the rest are re-evaluated in double-double)
@@ -267,6 +261,15 @@ def main():
         ctx.set_accept_floor(i, per0[i]["mean_abs"])
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t0
+
+    train_s = 0.0
+    if learned:
+        ctx.set_train_cost_ratio(args.cost_ratio)
+        t0 = time.perf_counter()
+        for i in ids:
+            ctx.train_proposal(i, args.train, seed=7 + rank, steps=args.train_steps, lr=3e-3, beta=0.1)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
 
     # inter-graph allocation (Sec. IV.C) from a pilot, for the learned+batched
     # form: the same total budget per step, split n_j ~ sigma_j / sqrt(t_j)
@@ -383,6 +386,7 @@ def main():
                        else "plain density, one launch per graph"),
                    "samples_per_graph_per_step": args.samples, "seed": "step index (+ rank offset)",
                    "train_samples_per_graph": args.train if learned else 0,
+                   "train_cost_ratio": args.cost_ratio if learned else None,
                    "l2": "256 MB buffer written between timed steps", "parallelism": "dp%d" % world},
         "inv_sigma2_per_s": isps,
         "inv_sigma2_per_s_incl_training": (1.0 / (sigma ** 2 * (t_dev + train_s + pilot_s + init_s)) if sigma > 0 else None),

@@ -220,6 +220,16 @@ int ae_set_proposal(ae_ctx *ctx, int graph_id, int mode, double beta);
  * 2 dd_tol N mean|y|.  yfloor finite and >= 0. */
 int ae_set_accept_floor(ae_ctx *ctx, int graph_id, double yfloor);
 
+/* Cost-aware training weights of the learned proposal (library design; the
+ * paper has no learned part): with ratio R > 0, a training sample that the
+ * acceptance test would send to double-double has its weight |y| divided by
+ * sqrt(1 + R), R being the cost of a re-evaluation in units of an FP64
+ * evaluation.  The proposal then approaches |f| / sqrt(cost), the density
+ * that minimises variance x expected cost, instead of |f|.  0 (default): the
+ * plain weights |y|.  Applies to later ae_train_proposal calls; uses each
+ * graph's acceptance floor as set at that time. */
+int ae_set_train_cost_ratio(ae_ctx *ctx, double ratio);
+
 /* Test entry: loss and gradient of the proposal for given parameters
  * (ae_proposal_nparams() floats: W1[64][32], b1, W2[64][64], b2, W3[64][64],
  * b3, W4[16][64], b4) and given samples (order: n*16 bytes, descending lines;

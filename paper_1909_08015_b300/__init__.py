@@ -94,6 +94,7 @@ def lib():
                                         ctypes.c_double, ctypes.c_double, P(AeTrainReport)]
         L.ae_set_proposal.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
         L.ae_set_accept_floor.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+        L.ae_set_train_cost_ratio.argtypes = [vp, ctypes.c_double]
         L.ae_proposal_eval.argtypes = [vp, ctypes.c_int, P(ctypes.c_float), dp, dp, P(ctypes.c_uint8),
                                        P(ctypes.c_float), dp, ctypes.c_uint64, dp, P(ctypes.c_float), dp, dp]
         L.ae_proposal_nparams.restype = ctypes.c_int
@@ -268,6 +269,11 @@ class Context:
 
     def set_proposal(self, gid, mode, beta=0.1):
         self._check(lib().ae_set_proposal(self._h, gid, int(mode), float(beta)))
+
+    def set_train_cost_ratio(self, ratio):
+        """Cost-aware training weights: |y| / sqrt(1 + ratio) for samples that
+        need double-double (0: plain |y|)."""
+        self._check(lib().ae_set_train_cost_ratio(self._h, float(ratio)))
 
     def set_accept_floor(self, gid, yfloor):
         """Absolute floor on |y| in the acceptance test of the graph's FP64

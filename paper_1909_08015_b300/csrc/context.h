@@ -49,6 +49,7 @@ struct ae_ctx {
   // scratch
   Partial *d_part = nullptr; size_t part_cap = 0;
   uint32_t *d_mrg = nullptr;    // MRG32k3a jump table on the device (opts.rng == 1)
+  double train_cost_ratio = 0;  // R of the proposal's training weights |y| / sqrt(1 + R [re-evaluated])
   unsigned long long *d_queue = nullptr; size_t queue_cap = 0;
   unsigned long long *d_qcount = nullptr;
   double *d_yq = nullptr;

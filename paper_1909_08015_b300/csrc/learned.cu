@@ -212,9 +212,12 @@ __global__ void tables_kernel(int M, const float *O, const double *deg, const do
 }
 
 // Training samples from the plain density: order[16] (descending z),
-// ln t at levels 1..M-1, and w = |I|/g.
+// ln t at levels 1..M-1, and w = |I|/g, divided by sqrt(1 + R) for samples
+// the acceptance test sends to double-double (R = 0: the plain weights).
+// With per-sample cost c, the density minimising variance x expected cost
+// is proportional to |f| / sqrt(c) rather than to |f|.
 __global__ void train_gen_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t seed, uint8_t *order,
-                                 float *lt, double *w) {
+                                 float *lt, double *w, double dd_tol, double cost_ratio) {
   extern __shared__ double slots[];
   double *Sl = slots + threadIdx.x * G.nslots;   // this thread's row of the slot file
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < count; base += (uint64_t)gridDim.x * blockDim.x) {
@@ -224,8 +227,11 @@ __global__ void train_gen_kernel(GraphDev G, uint64_t first, uint64_t count, uin
     draw_sample(G, first + i, seed, z, lz, lg);
     for (int k = 0; k < G.M; ++k) Sl[k] = z[k];
     run_tape(G, Sl);
-    double y = weight(Sl[G.outI], lg);
-    w[i] = isfinite(y) ? fabs(y) : 0.0;
+    double y, Ey;
+    weight2(Sl[G.outI], Sl[G.outE], lg, y, Ey);
+    double wi = isfinite(y) ? fabs(y) : 0.0;
+    if (cost_ratio > 0 && fp64_rejected(G, y, Ey, dd_tol)) wi /= sqrt(1.0 + cost_ratio);
+    w[i] = wi;
     int ord[14];
     for (int a = 0; a < G.M; ++a) {
       int p = a;
@@ -613,7 +619,7 @@ extern "C" int ae_train_proposal(ae_ctx *c, int gid, uint64_t n_train, uint64_t 
   size_t smem = (size_t)bs * G.nslots * 8;
   cudaFuncSetAttribute(train_gen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   train_gen_kernel<<<(unsigned)std::min<uint64_t>((n_train + bs - 1) / bs, (uint64_t)c->sm_count * 8), bs, smem, st>>>(
-      G, 1ull << 40, n_train, seed, d_order, d_lt, d_w);
+      G, 1ull << 40, n_train, seed, d_order, d_lt, d_w, c->opts.dd_tol, c->train_cost_ratio);
   wsum_kernel<<<1024, 256, 0, st>>>(d_w, n_train, n.wsum_part);
   std::vector<double> wp(1024);
   cudaMemcpyAsync(wp.data(), n.wsum_part, 1024 * 8, cudaMemcpyDeviceToHost, st);
@@ -672,6 +678,13 @@ extern "C" int ae_set_proposal(ae_ctx *c, int gid, int mode, double beta) {
   lg.dev.l2nbeta = beta < 1 ? std::log2(1.0 - beta) : -1e300;
   lg.learned.beta = beta;
   lg.learned.active = true;
+  return AE_OK;
+}
+
+extern "C" int ae_set_train_cost_ratio(ae_ctx *c, double ratio) {
+  if (!c) return AE_ERR_ARG;
+  if (!(ratio >= 0) || !std::isfinite(ratio)) return ae_fail(c, AE_ERR_ARG, "ratio must be finite and >= 0");
+  c->train_cost_ratio = ratio;
   return AE_OK;
 }
 

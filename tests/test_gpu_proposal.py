@@ -63,6 +63,28 @@ def test_learned_mixture_normalised_and_unbiased(ctx):
     assert abs(a["mean"] - b["mean"]) < 4 * math.hypot(a["sigma1"], b["sigma1"])
 
 
+def test_cost_aware_training_normalised_and_unbiased(ctx):
+    """Cost-aware weights (|y| / sqrt(1 + R) where double-double is needed):
+    the trained mixture is still normalised and its estimate agrees with the
+    plain density's; the ratio returns to 0 afterwards."""
+    ctx.load_graphs(3)
+    gid = 12
+    ctx.set_train_cost_ratio(8.0)
+    try:
+        ctx.train_proposal(gid, 1 << 18, seed=1, steps=80, lr=3e-3, beta=0.1)
+    finally:
+        ctx.set_train_cost_ratio(0.0)
+    d = ctx.eval_samples(gid, 0, 1 << 20, seed=2)
+    wq = np.exp2(-d["log2g"]) * math.factorial(7)
+    assert abs(wq.mean() - 1) < 4 * wq.std() / math.sqrt(len(wq))
+    N = 1 << 22
+    _, _, pl = ctx.integrate([gid], N, seed=3)
+    ctx.set_proposal(gid, 0)
+    _, _, pp = ctx.integrate([gid], N, seed=4)
+    a, b = pl[0], pp[0]
+    assert abs(a["mean"] - b["mean"]) < 4 * math.hypot(a["sigma1"], b["sigma1"])
+
+
 def test_fast_exp2_log2_against_device_library(ctx):
     """The learned sampler's fused-multiply-add exp2/log2 against the device
     library's exp2/log2 (itself within a couple of ulp of the exact value):

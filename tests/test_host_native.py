@@ -96,6 +96,21 @@ def test_tape_matches_oracle_integrand(host, n, ids):
         assert np.all(np.abs(Kc - ref[:, 1]) <= 1e-10 * ref[:, 1])
 
 
+def test_settings_validate_arguments(host):
+    host.load_graphs(1)
+    host.set_train_cost_ratio(8.0)
+    host.set_train_cost_ratio(0.0)
+    host.set_accept_floor(0, 0.5)
+    host.set_accept_floor(0, 0.0)
+    for bad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(ae.AeError, match="AE_ERR_ARG"):
+            host.set_train_cost_ratio(bad)
+        with pytest.raises(ae.AeError, match="AE_ERR_ARG"):
+            host.set_accept_floor(0, bad)
+    with pytest.raises(ae.AeError, match="AE_ERR_ARG"):
+        host.set_accept_floor(3, 1.0)
+
+
 def test_host_context_refuses_device_calls(host):
     host.load_graphs(1)
     with pytest.raises(ae.AeError, match="AE_ERR_NODEV"):
