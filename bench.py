@@ -30,9 +30,10 @@ METRIC = "MC samples/s and 1/(σ²·s) per graph set, learned+batched vs plain p
 
 # DRAM bytes (read + write) per batched_kernel launch in the default
 # workload's timed region: ncu dram__bytes_read.sum + dram__bytes_write.sum,
-# mean of the launches of one step (profiles/batched_kernel_3loop_learned_set.md).
-# None until taken on the current kernel revision.
-TRAFFIC_DEFAULT_BYTES = None
+# mean of the three launches of one step (53.4 MB read + 1206.8 MB write in
+# all; profiles/batched_kernel_3loop_learned_set.md).  Set to None whenever
+# the kernel changes until it is captured again.
+TRAFFIC_DEFAULT_BYTES = 420.09e6
 
 
 # FP64 operations of the table-driven elementary functions (one division

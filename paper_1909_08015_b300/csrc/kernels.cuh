@@ -460,13 +460,24 @@ static __device__ bool run_tape_staged(Stage &st, const GraphDev &G, double *S, 
 static __device__ void run_tape_dd(const GraphDev &G, dd *S) {
   char *Sb = reinterpret_cast<char *>(S);
   const uint4 *code = reinterpret_cast<const uint4 *>(G.code);
-  for (int pc = 0; pc < G.ntape; ++pc) {
-    const uint4 w0 = __ldg(code + 2 * pc);
+  const double *khi = G.khi, *klo = G.klo;
+  const int n = G.ntape;
+  if (n <= 0) return;
+  uint4 w0 = __ldg(code), w1 = __ldg(code + 1);   // next instruction prefetched in the loop
+  for (int pc = 0; pc < n; ++pc) {
+    const int nx = 2 * min(pc + 1, n - 1);
+    const uint4 n0 = __ldg(code + nx), n1 = __ldg(code + nx + 1);
     const uint32_t op = w0.x & 0xffffu, d = (w0.x >> 16) * 2, a = (w0.y & 0xffffu) * 2, b = (w0.y >> 16) * 2,
                    c = (w0.z & 0xffffu) * 2, kbi = w0.z >> 16, kci = w0.w & 0xffffu;
     const dd va = *reinterpret_cast<const dd *>(Sb + a);
-    const dd vb = (op & I_BK) ? dd{__ldg(G.khi + kbi), __ldg(G.klo + kbi)} : *reinterpret_cast<const dd *>(Sb + b);
-    const dd vc = (op & I_CK) ? dd{__ldg(G.khi + kci), __ldg(G.klo + kci)} : *reinterpret_cast<const dd *>(Sb + c);
+    // exact constants (I_KX) come from the instruction's immediates, others
+    // with their low parts from the pool
+    const dd vb = !(op & I_BK) ? *reinterpret_cast<const dd *>(Sb + b)
+                  : (op & I_KX) ? dd{__hiloint2double((int)w1.y, (int)w1.x), 0.0}
+                                : dd{__ldg(khi + kbi), __ldg(klo + kbi)};
+    const dd vc = !(op & I_CK) ? *reinterpret_cast<const dd *>(Sb + c)
+                  : (op & I_KX) ? dd{__hiloint2double((int)w1.w, (int)w1.z), 0.0}
+                                : dd{__ldg(khi + kci), __ldg(klo + kci)};
     dd r;
     const uint32_t sp = op & 0xff00u;
     if (op & I_AB) r = dd{__fma_rn(fabs(va.hi), fabs(vb.hi), fabs(vc.hi)), 0.0};   // magnitudes: FP64 is enough
@@ -482,6 +493,7 @@ static __device__ void run_tape_dd(const GraphDev &G, dd *S) {
     else if (sp == I_ABS) r = dd_abs(va);
     else r = dd_add_fast(vc, dd_abs(va));   // I_ADDABS
     *reinterpret_cast<dd *>(Sb + d) = r;
+    w0 = n0; w1 = n1;
   }
 }
 
