@@ -116,7 +116,8 @@ typedef struct ae_graph_result {
   double max_y2;         /* largest single y^2                                     */
   uint64_t n;            /* samples                                               */
   uint64_t n_dd;         /* samples re-evaluated in double-double                 */
-  uint64_t n_nonfinite;  /* samples whose value stayed non-finite: set to zero    */
+  uint64_t n_nonfinite;  /* samples that failed the acceptance test in double-double
+                            too (or stayed non-finite): counted as zero          */
   double seconds;        /* device time of the graph's launches                    */
   uint64_t launches;     /* kernels launched for this graph                        */
   double kernel_seconds; /* device time of the FP64 integrand kernel alone         */
