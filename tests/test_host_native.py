@@ -121,7 +121,7 @@ def test_host_context_refuses_device_calls(host):
         host.load_graphs(7)
 
 
-@pytest.mark.parametrize("n,ids,worst", [(2, [0, 1, 2, 3], 40), (3, [12], 30)])
+@pytest.mark.parametrize("n,ids,worst", [(2, [0, 1, 2, 3], 40), (3, [0, 12], 20)])
 def test_error_bound_holds_at_worst_points(host, n, ids, worst):
     """The tape's certified rounding-error bound E (magnitude twins, gamma_D
     times the absolute-value evaluation) against the oracle's exact rational
