@@ -330,6 +330,9 @@ def main():
     rate = total / t_dev
     # roofline of the dominant kernel: FP64 integrand kernel (sampler + tape)
     kern_s = sum(p["kernel_seconds"] for per in per_all for p in per)
+    # device time of the whole step (FP64 kernels, queue sort, double-double
+    # pass, reduction): the part after the FP64 kernels is reported apart
+    step_s = sum(p["seconds"] for per in per_all for p in per)
     flops_per = [info[i]["flops"] + sampler_flops(M, learned) for i in ids]
     fl_total = sum(flops_per[i] * alloc[i] for i in ids) * args.steps
     achieved = fl_total / kern_s / 1e12
@@ -393,6 +396,10 @@ def main():
         "inv_sigma2_per_s_incl_training": (1.0 / (sigma ** 2 * (t_dev + train_s + pilot_s + init_s)) if sigma > 0 else None),
         "estimate": {"value": val, "sigma_down": sigma, "samples": total, "dd_reevaluated": int(n_dd),
                      "zeroed": int(zeroed)},
+        "dd_pass": {"reevaluated": int(n_dd), "zeroed": int(zeroed),
+                    "seconds": max(step_s - kern_s, 0.0),
+                    "share_of_step": (max(step_s - kern_s, 0.0) / step_s) if step_s > 0 else None,
+                    "note": "double-double re-evaluation, queue sort and reduction; not credited to the FP64 fraction"},
         "plain_pdf": plain,
         "setup_seconds": {"compile": compile_s, "train": train_s, "pilot_allocation": pilot_s,
                           "initialisation": init_s},
