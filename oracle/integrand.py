@@ -48,9 +48,10 @@ part is expanded into monomials whose coefficients come from explicit
 numeric traces (``dirac.trace``), computed once per graph.
 
 Pinned by A_1^(2) = 1/2 (1-loop, deterministic quadrature), by the 2-loop
-no-lepton-loop sum -0.344166387438296 within 3 sigma, and by finiteness of the
-subtracted integrands (scaling tests).  3-, 4-, 5-loop graphs: parity
-unpinned beyond these properties.
+no-lepton-loop sum -0.344166387438296 within 3 sigma, and by UV/IR finiteness
+of the subtracted integrands (scaling of every line subset: all 2-loop graphs
+and three-loop graphs 0, 12, 27).  3-, 4-, 5-loop values: parity unpinned
+beyond these properties.
 """
 from fractions import Fraction
 from itertools import product
