@@ -10,6 +10,9 @@ For sample index i of graph j under seed s:
 value = (1/N) sum y, sigma_down^2 = sum y^2/N^2 - (sum y)^2/N^3
 (Eq. eq_sigma_down); set sums add mult_j value_j with sigma^2 = sum
 (mult_j sigma_j)^2 (Eq. eq_sigma_sum).  Sums are compensated (math.fsum).
+
+Pins: summarize() on hand-computed sigma_down; the 2-loop set sum against
+the closed form (samples_batched, a statistical pin).
 """
 import math
 import numpy as np
@@ -26,6 +29,16 @@ def weight(I, lg):
     s = float(exp2_tab(kf - lg))
     kc = min(max(kf, -100000.0), 100000.0)
     return math.ldexp(I * s, -int(kc))
+
+
+def weight_many(I, lg):
+    """weight() over arrays: y = (I 2^(kf - log2 g)) 2^-kf, kf = floor(log2 g)."""
+    I = np.asarray(I, dtype=np.float64)
+    lg = np.asarray(lg, dtype=np.float64)
+    kf = np.floor(lg)
+    s = exp2_tab(kf - lg)
+    kc = np.clip(kf, -100000.0, 100000.0).astype(np.int64)
+    return np.ldexp(I * s, -kc)
 
 
 class GraphOracle:
@@ -62,6 +75,29 @@ class GraphOracle:
             I[k], K[k] = self.integrand.evaluate(z[k])
             y[k] = weight(I[k], lg[k])
         return dict(z=z, log2g=lg, I=I, K=K, y=y, comp=comp)
+
+
+    def samples_batched(self, first, count, seed=0, chunk=1 << 17):
+        """Per-sample y for a large range, for statistical pins only: the
+        integrand in the batched floating-point form (Integrand.evaluate_many)
+        in long double and in double; points where the two disagree by more
+        than 1e-3 relative, or are not finite, are evaluated exactly (the
+        long-double value is then accurate to about 1e-3/2^11 relative).
+        Returns (y, number of exactly re-evaluated points)."""
+        ys = []
+        n_exact = 0
+        for lo in range(first, first + count, chunk):
+            cnt = min(chunk, first + count - lo)
+            p = self.points(lo, cnt, seed)
+            I64, _ = self.integrand.evaluate_many(p["z"])
+            IL, _ = self.integrand.evaluate_many(p["z"], np.longdouble)
+            I = IL.astype(np.float64)
+            bad = ~np.isfinite(I64) | ~np.isfinite(I) | (np.abs(I64 - I) > 1e-3 * np.abs(I))
+            for k in np.nonzero(bad)[0]:
+                I[k] = self.integrand.evaluate(p["z"][k])[0]
+            n_exact += int(bad.sum())
+            ys.append(weight_many(I, p["log2g"]))
+        return np.concatenate(ys), n_exact
 
 
 def summarize(y, mult=1):

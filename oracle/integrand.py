@@ -47,11 +47,16 @@ point (fractions of the double-precision z), then rounded once; the Dirac
 part is expanded into monomials whose coefficients come from explicit
 numeric traces (``dirac.trace``), computed once per graph.
 
-Pinned by A_1^(2) = 1/2 (1-loop, deterministic quadrature), by the 2-loop
-no-lepton-loop sum -0.344166387438296 within 3 sigma, and by UV/IR finiteness
-of the subtracted integrands (scaling of every line subset: all 2-loop graphs
-and three-loop graphs 0, 12, 27).  3-, 4-, 5-loop values: parity unpinned
-beyond these properties.
+Pinned by A_1^(2) = 1/2 (1-loop, deterministic quadrature); by the 2-loop
+no-lepton-loop sum -0.344166387438296 within 3 sigma (the oracle's own sum,
+2^20 samples per graph, on the CPU; evaluate_many with exact re-evaluation
+where two precisions disagree); by UV/IR finiteness of the subtracted
+integrands (scaling of every line subset: all 2-loop graphs and three-loop
+graphs 0, 12, 27); by mirror invariance; and, for the closing projections
+(``project``), by textbook form factors of synthetic vertices (F2 of
+gamma_mu, i sigma q/2m, P_mu/m (Gordon), q_mu and on-shell-vanishing
+structures; a, b, c and u, v read off Eq. eq_gamma_general_q0 structures).
+3-, 4-, 5-loop values: parity unpinned beyond these properties.
 """
 from fractions import Fraction
 from itertools import product
@@ -132,9 +137,10 @@ class Factor:
         return ('ph', C.ext_photon) if C.ext_photon in self.photons else 'mu'
 
     # ----------------------------------------------------- graph functions --
-    def graph_functions(self, alpha):
+    def graph_functions(self, alpha, batch=False):
         """Exact U, Z (electron-line block), flows a, b and V.
-        alpha: dict line -> Fraction."""
+        alpha: dict line -> Fraction (or, batch=True, line -> array of
+        floating-point values over sample points)."""
         E = len(self.elines)
         Lp = self.loops
         ae = [alpha[l] for l in self.elines]
@@ -143,24 +149,27 @@ class Factor:
         for ph in self.photons:
             na, nb = self.node_of[ph[1]], self.node_of[ph[2]]
             spans.append((min(na, nb), max(na, nb)))
-        A = [[Fraction(0)] * Lp for _ in range(Lp)]
+        A = [[(alpha[self.photons[0]] * 0 if batch else Fraction(0))] * Lp for _ in range(Lp)]
+        # (x = x + y rather than x += y: batched entries are shared arrays)
         for c in range(Lp):
-            A[c][c] += alpha[self.photons[c]]
+            A[c][c] = A[c][c] + alpha[self.photons[c]]
             for c2 in range(Lp):
                 lo = max(spans[c][0], spans[c2][0])
                 hi = min(spans[c][1], spans[c2][1])
                 for k in range(lo, hi):
-                    A[c][c2] += ae[k]
+                    A[c][c2] = A[c][c2] + ae[k]
         # eta for electron lines: -1 on the span of each photon
         eta = [[(-1 if spans[c][0] <= k < spans[c][1] else 0) for c in range(Lp)] for k in range(E)]
-        det, Ainv = _det_inv(A)
+        det, Ainv = _det_inv_batch(A) if batch else _det_inv(A)
         Z = [[sum(eta[k][c] * Ainv[c][c2] * eta[k2][c2] for c in range(Lp) for c2 in range(Lp))
               for k2 in range(E)] for k in range(E)]
         # particular flow along the path: P on every electron line, q-part d_k
         d = []
         for k in range(E):
             if self.ext_node is None:
-                d.append(Fraction(0))
+                d.append(0.0 if batch else Fraction(0))
+            elif batch:
+                d.append(-0.5 if k < self.ext_node else 0.5)
             else:
                 d.append(Fraction(-1, 2) if k < self.ext_node else Fraction(1, 2))
         a = [1 - sum(Z[k][k2] * ae[k2] for k2 in range(E)) for k in range(E)]
@@ -203,6 +212,28 @@ def _det_inv(A):
         M[c] = [x / piv for x in M[c]]
         for r in range(n):
             if r != c and M[r][c] != 0:
+                f = M[r][c]
+                M[r] = [x - f * y for x, y in zip(M[r], M[c])]
+    return det, [row[n:] for row in M]
+
+
+def _det_inv_batch(A):
+    """Determinant and inverse by Gauss-Jordan elimination for matrices whose
+    entries are arrays over sample points (one matrix per point).  The
+    matrices here are positive definite (sums of alpha > 0 over the lines of
+    the cycles), so no pivot vanishes and rows are taken in order."""
+    n = len(A)
+    if n == 0:
+        return 1.0, []
+    one = A[0][0] * 0 + 1
+    M = [row[:] + [one * (i == j) for j in range(n)] for i, row in enumerate(A)]
+    det = one
+    for c in range(n):
+        piv = M[c][c]
+        det = det * piv
+        M[c] = [x / piv for x in M[c]]
+        for r in range(n):
+            if r != c:
                 f = M[r][c]
                 M[r] = [x - f * y for x, y in zip(M[r], M[c])]
     return det, [row[n:] for row in M]
@@ -295,14 +326,35 @@ def coefficient_table(factor, channel, child_chan):
 
 def _project(factor, channel, child_chan, el, qsite):
     """Apply the channel's closing projection to one configuration."""
+    def chain(q_elem=None, mu_repl=None):
+        e = el
+        if qsite is not None and q_elem is not None:
+            e = dict(el)
+            e[qsite] = q_elem
+        return _chain(factor, e, child_chan, mu_repl=mu_repl)
+    return project(channel, chain, qsite is not None)
+
+
+def project(channel, chain, has_q):
+    """Closing projection of one Dirac chain (linear in the chain).
+
+    chain(q_elem, mu_repl) returns the chain's elements with its q-slot (if
+    has_q) holding q_elem and its external gamma_mu replaced by mu_repl
+    (None: gamma_mu itself).  Channels (Eq. eq_gamma_general_q0, m = 1):
+      'u', 'v'          Sigma = u + v Pslash  ->  u, v;
+      'a', 'abc', 'bc'  Gamma_mu = a gamma_mu + b P_mu + c Pslash P_mu
+                        + d [Pslash, gamma_mu] at q = 0  ->  a, a+b+c, b+c;
+      'F2'              the magnetic form factor F2(0) of Gamma_mu(P+q/2,
+                        P-q/2) at linear order in q (the AMM projector A).
+    """
     if channel == 'u':
-        return (dirac.trace(_chain(factor, el, child_chan)) / 4).real
+        return (dirac.trace(chain()) / 4).real
     if channel == 'v':
-        return (dirac.trace([P] + _chain(factor, el, child_chan)) / 4).real
+        return (dirac.trace([P] + chain()) / 4).real
     if channel in ('a', 'abc', 'bc'):
-        E1 = dirac.trace(_chain(factor, el, child_chan) + [('g', 'mu')]).real
-        E2 = dirac.trace(_chain(factor, el, child_chan, mu_repl=P) + [P]).real
-        E3 = dirac.trace(_chain(factor, el, child_chan, mu_repl=P)).real
+        E1 = dirac.trace(chain() + [('g', 'mu')]).real
+        E2 = dirac.trace(chain(mu_repl=P) + [P]).real
+        E3 = dirac.trace(chain(mu_repl=P)).real
         if channel == 'a':
             return (E1 - E2) / 12
         if channel == 'abc':
@@ -324,21 +376,18 @@ def _project(factor, channel, child_chan, el, qsite):
         # the 3 g_mu^a part of Y: the q-slot contracts with the external gamma^mu
         qmu = ('g', 'mu') if part == 'g' else P
         mrep = None if part == 'g' else P
-        if qsite is not None:
-            e2 = dict(el)
-            e2[qsite] = qb
-            ch = _chain(factor, e2, child_chan)
+        if has_q:
+            ch = chain(qb)
             for Y, w in zip(Ys, wts):
                 tot += sgn * w * dirac.trace([Lam] + ch + [Lam] + Y).real
-            e2[qsite] = qmu
-            ch = _chain(factor, e2, child_chan, mu_repl=mrep)
+            ch = chain(qmu, mrep)
             tot += sgn * 3.0 * dirac.trace([Lam] + ch + [Lam]).real
         else:
-            ch = _chain(factor, el, child_chan)
+            ch = chain()
             for Y, w in zip(Ys, wts):
                 tot += sgn * w * 0.5 * dirac.trace([qb] + ch + [Lam] + Y).real
                 tot -= sgn * w * 0.5 * dirac.trace([Lam] + ch + [qb] + Y).real
-            ch = _chain(factor, el, child_chan, mu_repl=mrep)
+            ch = chain(mu_repl=mrep)
             tot += sgn * 3.0 * 0.5 * dirac.trace([qmu] + ch + [Lam]).real
             tot -= sgn * 3.0 * 0.5 * dirac.trace([Lam] + ch + [qmu]).real
     return -tot / 24.0
@@ -451,3 +500,65 @@ class Integrand:
             K += abs(tv)
         pref = Fraction(float(z[0])) * Fraction(1, 4 ** n) * (-1) ** n
         return float(pref * total), float(abs(pref) * K)
+
+    def evaluate_many(self, z, dtype=np.float64):
+        """(I, K) at many points z (array S x M) in floating point of the
+        given dtype: the same steps as evaluate(), every exact rational
+        operation replaced by the floating-point one, vectorised over the
+        points.  Coefficients of lambda powers j >= n are left out (evaluate()
+        asserts that they vanish exactly).  Not a parity reference: only the
+        statistical pin of the 2-loop sum uses it (with exact re-evaluation
+        of the points where two precisions disagree)."""
+        z = np.asarray(z, dtype=dtype)
+        al = {}
+        for key, i in self.idx.items():
+            zi = z[:, i]
+            if key[0] == 'e' and i == 0:
+                al[('e', key[1])] = zi / 2
+            elif key[0] == 'e':
+                al[('e', key[1])] = zi
+            else:
+                al[key] = zi
+        zero = z[:, 0] * 0
+        gf = {}
+        vals = {}
+        for key, (fac, table) in self.tables.items():
+            fk = (key[0], key[3])
+            if fk not in gf:
+                gf[fk] = fac.graph_functions(al, batch=True)
+            U, Z, a, b, V = gf[fk]
+            vec = {}
+            for coef, j, asites, qsite, pairs in table:
+                m = zero + dtype(coef)
+                for s_ in asites:
+                    m = m * a[s_]
+                if qsite is not None:
+                    m = m * b[qsite]
+                for (s1, s2) in pairs:
+                    m = m * Z[s1][s2]
+                vec[j] = vec.get(j, zero) + m
+            vals[key] = ({j: v / (U * U) for j, v in vec.items()}, V)
+        n = self.n
+        total = zero
+        K = zero
+        for sign, assigns in self.terms:
+            tv = zero
+            for parts in assigns:
+                conv = {0: zero + 1}
+                W = zero
+                for key in parts:
+                    fv, V = vals[key]
+                    W = W + V
+                    new = {}
+                    for j1, x1 in conv.items():
+                        for j2, x2 in fv.items():
+                            new[j1 + j2] = new.get(j1 + j2, zero) + x1 * x2
+                    conv = new
+                for j, x in conv.items():
+                    if j >= n:
+                        continue
+                    tv = tv + x * (dtype((-1) ** j * math.factorial(n - j - 1)) / dtype(2 ** j)) / (-W) ** (n - j)
+            total = total + sign * tv
+            K = K + np.abs(tv)
+        pref = z[:, 0] * (dtype((-1) ** n) / dtype(4 ** n))
+        return pref * total, np.abs(pref) * K

@@ -14,7 +14,7 @@ import pytest
 from oracle import dirac
 from oracle.forest import divergent_subgraphs, terms as forest_terms
 from oracle.graphs import Graph, enumerate_graphs, class_counts, perfect_matchings, is_1pi, word_of
-from oracle.integrand import Integrand
+from oracle.integrand import Integrand, project
 from oracle.philox import philox4x32_10, uniforms
 from oracle.sampler import Density, sample, log2_series, exp2_series, log2_tab, exp2_tab, deg_table, phi_table
 from oracle.estimate import GraphOracle, summarize, weight
@@ -195,6 +195,56 @@ def test_sector_probabilities_exact():
     assert chi2 < dof + 5 * math.sqrt(2 * dof)
 
 
+def _plain_form_points(dens, u):
+    """The sampler of Sec. III.A written in its plain form: log2 t =
+    log2(u)/Deg and z = 2^lz / sum by quotients, with numpy's log2/exp2
+    instead of the table-driven functions (component g1 only)."""
+    M = dens.M
+    deg, phi = dens.deg[0], dens.phi[0]
+    S = u.shape[0]
+    lz = np.zeros((S, M))
+    for s_ in range(S):
+        T = dens.full
+        cur = 0.0
+        for l in range(M - 1):
+            target = u[s_, 1 + 2 * l] * phi[T]
+            acc = 0.0
+            chosen = -1
+            last = 0
+            for j in range(M):
+                if T >> j & 1:
+                    acc = acc + phi[T ^ (1 << j)] / deg[T ^ (1 << j)]
+                    if chosen < 0 and target < acc:
+                        chosen = j
+                    last = j
+            chosen = last if chosen < 0 else chosen
+            lz[s_, chosen] = cur
+            T ^= 1 << chosen
+            cur = cur + np.log2(u[s_, 2 + 2 * l]) / deg[T]
+        lz[s_, int(math.log2(T))] = cur
+    e = np.exp2(lz)
+    ssum = e.sum(1)
+    return e / ssum[:, None]
+
+
+def test_sampler_rounding_order_is_a_rounding_choice():
+    """The oracle's sampler multiplies by tabulated reciprocals and uses
+    table-driven log2/exp2 (the same operation order as the device sampler,
+    so that z is reproducible bit for bit).  Written in its plain form
+    (quotients, numpy's log2/exp2) the same walk gives the same sector
+    choices and z within a few ulp: the order of operations is a rounding
+    choice, not a different sampler."""
+    g = enumerate_graphs(3)[7]
+    d = Density(g)
+    idx = np.arange(0, 3000, dtype=np.uint64)
+    u = uniforms(idx, 7, 0, d.M)
+    z, lg, comp = sample(d, u)
+    sel = np.nonzero(comp == 0)[0][:400]
+    zp = _plain_form_points(d, u[sel])
+    rel = np.abs(zp - z[sel]) / z[sel]
+    assert rel.max() < 64 * 2.0 ** -52, rel.max()
+
+
 # --------------------------------------------------------------- Dirac ----
 def test_dirac_identities():
     rng = np.random.default_rng(1)
@@ -208,6 +258,91 @@ def test_dirac_identities():
     lhs = dirac.trace([("g", 1), sl(a), sl(b), sl(c), ("g", 1), sl(d)])
     rhs = -2 * np.trace(sl(c) @ sl(b) @ sl(a) @ sl(d))
     assert abs(lhs - rhs) < 1e-9
+
+
+# ------------------------------------------------ projectors (Sec. II) ---
+def _chain_of(*els):
+    """A synthetic Dirac chain for oracle.integrand.project: 'mu' is the
+    external gamma_mu, 'q' the q-slot (qslash), anything else a matrix."""
+    def chain(q_elem=None, mu_repl=None):
+        out = []
+        for e in els:
+            if isinstance(e, str) and e == "mu":
+                out.append(mu_repl if mu_repl is not None else ("g", "mu"))
+            elif isinstance(e, str) and e == "q":
+                out.append(q_elem)
+            else:
+                out.append(e)
+        return out
+    return chain, any(isinstance(e, str) and e == "q" for e in els)
+
+
+def _proj(channel, parts):
+    """The projection is linear in Gamma: sum of coef * project(chain)."""
+    return sum(c * project(channel, *_chain_of(*els)) for c, els in parts)
+
+
+def test_amm_projector_on_synthetic_vertices():
+    """A = F2(0) (Sec. II, the projector of the anomalous magnetic moment),
+    with P = (p + p')/2, q = p' - p, m = 1, on structures whose form factors
+    are textbook facts:
+      gamma_mu -> F2 = 0;  i sigma_{mu nu} q^nu / 2m -> 1;
+      P_mu / m -> -1 (Gordon identity: gamma_mu = P_mu/m + i sigma q/2m);
+      q_mu -> 0 (the F3 structure, annihilated);
+      (pslash' - m) gamma_mu and gamma_mu (pslash - m) -> 0 (vanish on shell).
+    i sigma_{mu nu} q^nu = -(gamma_mu qslash - qslash gamma_mu)/2,
+    P_mu = (Pslash gamma_mu + gamma_mu Pslash)/2, likewise q_mu."""
+    P = dirac.PSLASH
+    assert abs(_proj("F2", [(1.0, ("mu",))])) < 1e-13
+    assert abs(_proj("F2", [(-0.25, ("mu", "q")), (0.25, ("q", "mu"))]) - 1.0) < 1e-13
+    assert abs(_proj("F2", [(0.5, (P, "mu")), (0.5, ("mu", P))]) + 1.0) < 1e-13
+    assert abs(_proj("F2", [(0.5, ("q", "mu")), (0.5, ("mu", "q"))])) < 1e-13
+    # pslash' = Pslash + qslash/2 on the left, pslash = Pslash - qslash/2 on the right
+    assert abs(_proj("F2", [(1.0, (P, "mu")), (-1.0, ("mu",)), (0.5, ("q", "mu"))])) < 1e-13
+    assert abs(_proj("F2", [(1.0, ("mu", P)), (-1.0, ("mu",)), (-0.5, ("mu", "q"))])) < 1e-13
+    # linearity across the two parts (q-independent and linear in q)
+    mix = [(0.3, ("mu",)), (-0.25 * 2.0, ("mu", "q")), (0.25 * 2.0, ("q", "mu")), (0.5 * 0.7, (P, "mu")),
+           (0.5 * 0.7, ("mu", P))]
+    assert abs(_proj("F2", mix) - (2.0 - 0.7)) < 1e-12
+
+
+def test_l_u_projectors_recover_abc_and_uv():
+    """U and L of Sec. II read a, b, c of Eq. eq_gamma_general_q0 (at q = 0,
+    m = 1) off Gamma_mu = a gamma_mu + b P_mu + c Pslash P_mu + d [Pslash,
+    gamma_mu]: channel 'a' gives a (U), 'abc' gives a + m b + m^2 c (L), 'bc'
+    gives m b + m^2 c (L - U), whatever d; a self-energy Sigma = u + v Pslash
+    gives u and v."""
+    P = dirac.PSLASH
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        a, b, c, d = rng.normal(size=4)
+        G = [(a, ("mu",)), (b / 2, (P, "mu")), (b / 2, ("mu", P)), (c / 2, (P, P, "mu")), (c / 2, (P, "mu", P)),
+             (d, (P, "mu")), (-d, ("mu", P))]
+        assert abs(_proj("a", G) - a) < 1e-12
+        assert abs(_proj("abc", G) - (a + b + c)) < 1e-12
+        assert abs(_proj("bc", G) - (b + c)) < 1e-12
+        u, v = rng.normal(size=2)
+        S = [(u, (dirac.ONE,)), (v, (P,))]
+        assert abs(_proj("u", S) - u) < 1e-12
+        assert abs(_proj("v", S) - v) < 1e-12
+
+
+# ------------------------------------------------------------ estimator ---
+def test_summarize_sigma_down_by_hand():
+    """Eq. eq_sigma_down on hand-computed cases: y = (1, 2, 3, 4): mean 5/2,
+    sigma_down^2 = 30/16 - 100/64 = 5/16; multiplicity scales value and
+    sigma; mean |y| of (-1, 3) is 2 with sigma_down^2 = 10/4 - 4/8 = 2."""
+    r = summarize([1.0, 2.0, 3.0, 4.0])
+    assert r["mean"] == 2.5 and r["n"] == 4
+    assert abs(r["sigma1"] - math.sqrt(5.0 / 16.0)) < 1e-15
+    assert r["sum_y"] == 10.0 and r["sum_y2"] == 30.0
+    r2 = summarize([1.0, 2.0, 3.0, 4.0], mult=2)
+    assert r2["value"] == 5.0 and abs(r2["sigma"] - 2 * math.sqrt(5.0 / 16.0)) < 1e-15
+    r3 = summarize([-1.0, 3.0])
+    assert r3["mean"] == 1.0 and r3["mean_abs"] == 2.0
+    assert abs(r3["sigma1"] - math.sqrt(2.0)) < 1e-15
+    # a constant sample (binary-exact value) has sigma_down exactly 0
+    assert summarize([0.375] * 1000)["sigma1"] == 0.0
 
 
 # ------------------------------------------------------------ integrand ---
@@ -302,6 +437,57 @@ def test_three_loop_finiteness():
                     vals.append(abs(I.evaluate(z)[0]) * lam ** r + 1e-300)
                 slope = math.log(vals[1] / vals[0]) / math.log(1e-8 / 1e-6)
                 assert slope > 0.5, (gi, s, slope)
+
+
+def _two_loop_graph_sums(gi, n):
+    """(sum y, sum y^2, N, exactly re-evaluated) of 2-loop graph gi over
+    samples 0..n-1 (seed 0): a spawned worker of the closed-form pin."""
+    from oracle.estimate import GraphOracle
+    g = enumerate_graphs(2)[gi]
+    y, n_exact = GraphOracle(g, gi).samples_batched(0, n, 0)
+    return math.fsum(y), math.fsum(y * y), len(y), n_exact
+
+
+def test_two_loop_sum_closed_form():
+    """The oracle's own 2-loop sum against the closed form (CPU, no GPU).
+
+    A_1^(4) = 197/144 + pi^2/12 - (pi^2/2) ln 2 + (3/4) zeta(3) (Petermann;
+    Sommerfield) = -0.328478965579...; the graphs without lepton loops give it
+    minus the vacuum-polarisation graph, 119/36 - pi^2/3, i.e.
+    -0.344166387438296.  2^20 samples per graph (Eqs. eq_integral_approx,
+    eq_sigma_down, eq_sigma_sum): the estimate must lie within 3 sigma_down,
+    with sigma_down below 0.01 (3 % of the value) so that a dropped or
+    mis-signed forest term (an O(0.1) change) cannot pass."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    zeta3 = 1.2020569031595942854
+    a4 = 197 / 144 + math.pi ** 2 / 12 - math.pi ** 2 / 2 * math.log(2) + 0.75 * zeta3
+    want = a4 - (119 / 36 - math.pi ** 2 / 3)
+    assert abs(want - (-0.344166387438296)) < 1e-14
+    gs = enumerate_graphs(2)
+    n = 1 << 20
+    with cf.ProcessPoolExecutor(max_workers=4, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_two_loop_graph_sums, range(len(gs)), [n] * len(gs)))
+    val = var = 0.0
+    for g, (sy, sy2, N, n_exact) in zip(gs, res):
+        assert n_exact < N // 100
+        val += g.mult * sy / N
+        var += g.mult ** 2 * max(sy2 / N ** 2 - sy ** 2 / N ** 3, 0.0)
+    sig = math.sqrt(var)
+    assert sig < 0.01, sig
+    assert abs(val - want) < 3 * sig, (val, sig, want)
+
+
+def test_batched_integrand_matches_exact():
+    """The batched floating-point integrand (statistical pins only) against
+    the exact one at 64 sampler points of every 2-loop graph."""
+    from oracle.estimate import GraphOracle
+    for gi, g in enumerate(enumerate_graphs(2)):
+        o = GraphOracle(g, gi)
+        r = o.samples(0, 64, 7)
+        I, K = o.integrand.evaluate_many(r["z"], np.longdouble)
+        assert np.all(np.abs(I.astype(np.float64) - r["I"]) <= 1e-8 * np.abs(r["I"]) + 1e-12 * r["K"])
+        assert np.allclose(K.astype(np.float64), r["K"], rtol=1e-12)
 
 
 def test_weight_range_safe():
