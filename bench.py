@@ -1,15 +1,25 @@
 """Benchmark: Monte Carlo samples/s and 1/(sigma^2 s) on a generated graph set,
-learned+batched against the plain density.
+learned+batched against the plain density at equal wall time.
 
-Workload (default): all 28 three-loop vertex graphs without lepton loops.
-Set-up (untimed, reported): compile the graphs; train one learned proposal
-per graph on 2^20 plain samples (the network's own GPU kernels).
-Timed step: every graph integrated over 2^24 fresh Philox samples in ONE
-persistent batched launch with the learned mixture density (seed = step
-number; under torchrun each rank adds rank * 1000003, so ranks draw disjoint
-streams: weak scaling, no data-path collective; per-graph sums are merged
-once at the end).  The plain density (one launch per graph, the same sample
-budget) is timed after the timed region for the comparison.
+Workload (default): 20 four-loop vertex graphs without lepton loops, chosen
+from the 269 by the library's Philox-seeded shuffle (ae_seeded_subset, seed
+0).  Set-up (untimed, reported): compile the graphs; an initialisation pass
+(plain density, 2^16 samples per graph) whose sigma_down sets the widths of
+the paper's acceptance test (Sec. IV.A, Eq. eq_interval_accept); train one
+learned proposal per graph on the GPU (its own kernels); a pilot that splits
+each step's budget over the graphs (n_j ~ sigma_j / sqrt(t_j), Sec. IV.C).
+
+Timed step: one block of a run (ae_run_step): every graph continues its own
+Philox stream by its allocated count, all in ONE persistent batched launch
+with the learned mixture density, captured in a CUDA graph.  Under torchrun
+each rank runs its own stream (seed offset by rank): weak scaling, no
+data-path collective; the per-graph sums are merged once at the end.
+
+After the timed region (rank 0): the plain density in the same batched,
+allocated form, with the step budget scaled so that the same number of
+steps takes the same device time (equal wall time); and a few learned steps
+under the other acceptance test (the library's relative one), so that both
+modes are reported.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -21,20 +31,19 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MC samples/s and 1/(σ²·s) per graph set, learned+batched vs plain pdf, 1 B300"
+N_GRAPHS = {1: 1, 2: 4, 3: 28, 4: 269, 5: 3213}
 
-# DRAM bytes (read + write) per batched_kernel launch in the default
-# workload's timed region: ncu dram__bytes_read.sum + dram__bytes_write.sum,
-# mean of the three launches of one step (53.4 MB read + 1206.8 MB write in
-# all; profiles/batched_kernel_3loop_learned_set.md).  Set to None whenever
-# the kernel changes until it is captured again.
-TRAFFIC_DEFAULT_BYTES = 420.09e6
-
+# DRAM bytes (read + write) per launch of the dominant kernel for the
+# default workload, from an ncu capture; None until the current kernel has
+# been captured.
+TRAFFIC_DEFAULT_BYTES = None
 
 # FP64 operations of the table-driven elementary functions (one division
 # counted as one operation): exp2 = range reduction (10) + degree-7 Horner
@@ -59,9 +68,8 @@ def sampler_flops(M, learned=False):
     Plain density: uniforms (4 ops each, 2M of them); M-1 walk steps
     (product, |T| additions, one log2, a product with 1/Deg and a sum);
     normalisation (M exp2 and sums, one log2, one reciprocal, M products and
-    differences); three sector
-    densities (3 ops per level) and the four-component mixture (4 exp2,
-    one log2).
+    differences); three sector densities (3 ops per level) and the
+    four-component mixture (4 exp2, one log2).
 
     Learned mixture: the same uniforms; M-1 walk steps of |T| additions, one
     log2, a product and a sum; normalisation (M exp2, M sums, one log2, one
@@ -82,24 +90,36 @@ def sampler_flops(M, learned=False):
     return 8 * M + 2 + walk + norm + pdf + ESTIMATOR_OPS
 
 
-def oracle_rate(n_loops, graph_ids, per_graph, seed=0):
+def workload_graphs(loops, graphs):
+    """Canonical ids of the workload's graphs (all, or the seeded subset)."""
+    import paper_1909_08015_b300 as ae
+    total = N_GRAPHS[loops]
+    if graphs <= 0 or graphs >= total:
+        return list(range(total))
+    return ae.seeded_subset(total, graphs, 0)
+
+
+def oracle_rate(n_loops, canon_ids, per_graph, seed=0):
     """Time the CPU oracle (as it stands) on a bounded sample: the listed
-    graphs, per_graph samples each, evaluation time after per-graph setup.
-    Runs one process per host core (spawned)."""
+    graphs, per_graph samples each (plain density), evaluation time after
+    each worker's per-graph set-up; one spawned process per host core."""
     import multiprocessing as mp
     cores = os.cpu_count() or 1
+    per_core = max(1, cores // max(1, len(canon_ids)))
+    chunk = max(1, (per_graph + per_core - 1) // per_core)
     jobs = []
-    chunk = max(1, per_graph // max(1, cores // max(1, len(graph_ids))))
-    for gi in graph_ids:
+    for gi in canon_ids:
         for lo in range(0, per_graph, chunk):
             jobs.append((n_loops, gi, lo, min(chunk, per_graph - lo), seed))
+    t0 = time.perf_counter()
     with mp.get_context("spawn").Pool(min(cores, len(jobs))) as pool:
         res = pool.map(_oracle_job, jobs)
+    wall_all = time.perf_counter() - t0
     evals = sum(r[0] for r in res)
-    eval_cpu_s = sum(r[1] for r in res)
     used = min(cores, len(jobs))
-    wall = eval_cpu_s / used
-    return evals / wall, used, evals, wall
+    eval_wall = sum(r[1] for r in res) / used
+    setup = max(r[2] for r in res)
+    return evals / eval_wall, used, evals, eval_wall, setup, wall_all
 
 
 def _oracle_job(args):
@@ -107,10 +127,12 @@ def _oracle_job(args):
     sys.path.insert(0, ROOT)
     from oracle.estimate import GraphOracle
     from oracle.graphs import enumerate_graphs
+    t = time.perf_counter()
     o = GraphOracle(enumerate_graphs(n_loops)[gi], gi)
+    setup = time.perf_counter() - t
     t = time.perf_counter()
     o.samples(lo, cnt, seed)
-    return cnt, time.perf_counter() - t
+    return cnt, time.perf_counter() - t, setup
 
 
 class Clocks:
@@ -157,42 +179,33 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def workload_name(loops, n, total, learned_vs_plain=True):
+    what = ("%d seeded %d-loop vertex graphs without lepton loops (Philox-seeded subset of the %d)"
+            % (n, loops, total)) if n < total else ("all %d %d-loop vertex graphs without lepton loops" % (n, loops))
+    return what + (", learned mixture density vs plain density at equal wall time, one batched persistent "
+                   "launch per step" if learned_vs_plain else ", plain density, one batched persistent launch per step")
+
+
 def run_reference(args, rank, world):
+    """The oracle (plain, unoptimised CPU restatement) on a bounded sample of
+    the same workload; rank 0 only."""
     if rank != 0:
         return
-    ids = [0, 13, 27]
-    rate, cores, evals, wall = oracle_rate(3, ids, args.oracle_samples)
+    canon = workload_graphs(args.loops, args.graphs)
+    cids = [canon[0], canon[len(canon) // 2], canon[-1]]
+    rate, cores, evals, wall, setup, wall_all = oracle_rate(args.loops, cids, args.oracle_samples)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "samples/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "3-loop vertex graphs without lepton loops, plain pdf",
-                       "graphs": len(ids), "samples_per_graph": args.oracle_samples},
+            "config": {"workload": workload_name(args.loops, len(canon), N_GRAPHS[args.loops]),
+                       "oracle_graphs": cids, "samples_per_graph": args.oracle_samples},
             "cpu_baseline": {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
-                             "sample": "graphs %s of the 3-loop set, %d samples each, evaluation after "
-                                       "per-graph setup, %.1f s" % (ids, args.oracle_samples, wall)},
+                             "sample": "canonical graphs %s of the %d-loop list, %d samples each, plain density; "
+                                       "evaluation %.1f s after a per-graph set-up of up to %.1f s"
+                                       % (cids, args.loops, args.oracle_samples, wall, setup)},
             "e2e": {"value": rate, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "vs_baseline": None}
     print(json.dumps(line))
-
-
-def merge(per_steps, ids, info):
-    """Per-graph (sum y, sum y^2, N) over steps -> (value, sigma_down)."""
-    import numpy as np
-    sums = np.zeros((len(ids), 3))
-    for per in per_steps:
-        for i, p in enumerate(per):
-            sums[i] += (p["sum_y"], p["sum_y2"], p["n"])
-    return sums
-
-
-def estimate(sums, info):
-    val = var = 0.0
-    for i in range(len(sums)):
-        sy, sy2, N = sums[i]
-        v1 = sy2 / N ** 2 - sy ** 2 / N ** 3
-        val += info[i]["mult"] * sy / N
-        var += info[i]["mult"] ** 2 * max(v1, 0.0)
-    return val, math.sqrt(var)
 
 
 def main():
@@ -201,20 +214,24 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--loops", type=int, default=3)
-    ap.add_argument("--graphs", type=int, default=0,
+    ap.add_argument("--loops", type=int, default=4)
+    ap.add_argument("--graphs", type=int, default=20,
                     help="seeded subset of this many graphs of the loop order (0: all of them)")
-    ap.add_argument("--samples", type=int, default=1 << 24, help="samples per graph per step")
+    ap.add_argument("--samples", type=int, default=1 << 21, help="mean samples per graph per step")
     ap.add_argument("--train", type=int, default=1 << 20, help="training samples per graph")
     ap.add_argument("--train-steps", type=int, default=150)
     ap.add_argument("--cost-ratio", type=float, default=0.0,
                     help="cost-aware proposal training: weight |y|/sqrt(1+R) for samples that need double-double")
-    ap.add_argument("--plain", action="store_true", help="time the plain density only, one launch per graph")
-    ap.add_argument("--plain-batched", action="store_true",
-                    help="time the plain density in the batched persistent launch with pilot allocation")
-    ap.add_argument("--no-alloc", action="store_true", help="equal samples per graph in the learned+batched form")
-    ap.add_argument("--oracle-samples", type=int, default=96)
+    ap.add_argument("--accept", default="paper", choices=["paper", "relative"],
+                    help="acceptance test of FP64 values: the paper's interval width (Eq. eq_interval_accept) "
+                         "or the library's relative 1e-10 test")
+    ap.add_argument("--plain", action="store_true", help="time the plain density only (no training)")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain and other-acceptance arms")
+    ap.add_argument("--init-samples", type=int, default=1 << 16)
+    ap.add_argument("--pilot", type=int, default=1 << 18)
+    ap.add_argument("--oracle-samples", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-file", default=None, help="where nvidia-smi samples go (default: a temp file)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -227,6 +244,7 @@ def main():
     import numpy as np
     import torch
     import paper_1909_08015_b300 as ae
+    from paper_1909_08015_b300.runstate import rank_seed
 
     torch.cuda.set_device(local)
     dist = None
@@ -238,28 +256,30 @@ def main():
     opts.stream = stream.cuda_stream
     ctx = ae.Context(local, opts)
     t0 = time.perf_counter()
-    canon = None
-    if args.graphs > 0:
-        total_graphs = {1: 1, 2: 4, 3: 28, 4: 269, 5: 3213}[args.loops]
-        canon = ae.seeded_subset(total_graphs, min(args.graphs, total_graphs), 0)
-        ngr = ctx.load_graph_subset(args.loops, canon)
-    else:
-        ngr = ctx.load_graphs(args.loops)
+    canon = workload_graphs(args.loops, args.graphs)
+    ngr = ctx.load_graph_subset(args.loops, canon)
     compile_s = time.perf_counter() - t0
     ids = list(range(ngr))
     info = [ctx.graph_info(i) for i in ids]
     M = info[0]["M"]
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MB > L2
-    learned = not args.plain and not args.plain_batched
-    batched = not args.plain
-    # initialisation pass (Sec. IV.A), plain density: 2^16 samples per graph; their mean |y|
-    # becomes the graph's floor in the acceptance test of FP64 values (a
-    # value is kept when its certified rounding bound, carried to y, is at
-    # most 1e-10 max(|y|, floor); the rest are re-evaluated in double-double)
+    learned = not args.plain
+
+    # initialisation pass (Sec. IV.A), plain density: sigma_down per graph
+    # sets the widths of the paper's acceptance test; mean |y| the floor of
+    # the library's relative test
     t0 = time.perf_counter()
-    _, _, per0 = ctx.integrate_batched(ids, [1 << 16] * ngr, seed=77 + rank)
-    for i in ids:
-        ctx.set_accept_floor(i, per0[i]["mean_abs"])
+    _, _, per0 = ctx.integrate_batched(ids, [args.init_samples] * ngr, seed=77 + rank)
+    widths = ae.accept_widths([p["sigma"] for p in per0])
+
+    def set_accept(mode):
+        for i in ids:
+            if mode == "paper":
+                ctx.set_accept_width(i, widths[i])
+            else:
+                ctx.set_accept_width(i, 0.0)
+                ctx.set_accept_floor(i, per0[i]["mean_abs"])
+    set_accept(args.accept)
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t0
 
@@ -272,96 +292,114 @@ def main():
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
 
-    # inter-graph allocation (Sec. IV.C) from a pilot, for the learned+batched
-    # form: the same total budget per step, split n_j ~ sigma_j / sqrt(t_j)
-    alloc = [args.samples] * ngr
-    pilot_s = 0.0
-    if batched and not args.no_alloc:
-        t0 = time.perf_counter()
-        n_j, _ = ctx.allocate(ids, 1 << 18, args.samples * ngr, seed=99 + rank, mode=0)
-        alloc = [int(x) for x in n_j]
-        torch.cuda.synchronize()
-        pilot_s = time.perf_counter() - t0
+    def allocate():
+        n_j, _ = ctx.allocate(ids, args.pilot, args.samples * ngr, seed=99 + rank, mode=0)
+        return [int(x) for x in n_j]
 
-    def step(seed):
-        if batched:
-            return ctx.integrate_batched(ids, alloc, seed=seed + rank * 1000003)
-        return ctx.integrate(ids, args.samples, seed=seed + rank * 1000003)
-
-    for w in range(args.warmup):
-        step(10 ** 6 + w)
+    t0 = time.perf_counter()
+    alloc = allocate()
     torch.cuda.synchronize()
+    pilot_s = time.perf_counter() - t0
+
+    def timed_steps(alloc_, steps, seed, flush_l2=True):
+        """steps run blocks timed with CUDA events on the launching stream;
+        returns (device seconds, host seconds, per-step results)."""
+        ctx.run_reset(seed)
+        dev_ms = 0.0
+        host_s = 0.0
+        per_steps = []
+        for _ in range(steps):
+            if flush_l2:
+                flush.zero_()
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            t = time.perf_counter()
+            ev0.record(stream)
+            per = ctx.run_step(ids, alloc_)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            host_s += time.perf_counter() - t
+            dev_ms += ev0.elapsed_time(ev1)
+            per_steps.append(per)
+        return dev_ms / 1e3, host_s, per_steps
+
+    # warm-up (tunes, captures the step's CUDA graph), then the timed region
+    timed_steps(alloc, args.warmup, 10 ** 6 + rank)
     if dist:
         dist.barrier()
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv")
+    torch.cuda.synchronize()
+    clocks_path = args.clocks_file or os.path.join(tempfile.gettempdir(), "bench_clocks_%d.csv" % os.getpid())
+    clocks = Clocks(clocks_path)
     clocks.start()
     torch.cuda.nvtx.range_push("timed")
-    dev_ms = 0.0
-    e2e_s = 0.0
-    per_all = []
-    for k in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        t0 = time.perf_counter()
-        ev0.record(stream)
-        v, s, per = step(k)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        e2e_s += time.perf_counter() - t0
-        dev_ms += ev0.elapsed_time(ev1)
-        per_all.append(per)
+    t_dev, e2e_s, per_all = timed_steps(alloc, args.steps, rank_seed(0, rank))
     torch.cuda.nvtx.range_pop()
     ck = clocks.stop(local)
-    t_dev = dev_ms / 1e3
     if dist:
         tt = torch.tensor([t_dev, e2e_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_dev, e2e_s = tt.tolist()
-    sums = merge(per_all, ids, info)
-    if dist:
-        ts = torch.tensor(sums, dtype=torch.float64, device="cuda")
-        dist.all_reduce(ts)
-        sums = ts.cpu().numpy()
-    val, sigma = estimate(sums, info)
-    total = args.samples * len(ids) * args.steps * world
+        from paper_1909_08015_b300.runstate import RunState
+        RunState.attach(ctx).merge_ranks()
+    val, sigma, sigma_up, per_run = ctx.run_estimate()
+    total = sum(alloc) * args.steps * world
     rate = total / t_dev
-    # roofline of the dominant kernel: FP64 integrand kernel (sampler + tape)
+    isps = 1.0 / (sigma ** 2 * t_dev) if sigma > 0 else None
+
+    # roofline of the dominant kernel: the FP64 integrand kernel (sampler + tape)
     kern_s = sum(p["kernel_seconds"] for per in per_all for p in per)
-    # device time of the whole step (FP64 kernels, queue sort, double-double
-    # pass, reduction): the part after the FP64 kernels is reported apart
     step_s = sum(p["seconds"] for per in per_all for p in per)
     flops_per = [info[i]["flops"] + sampler_flops(M, learned) for i in ids]
+    twin_per = [info[i]["flops_bound"] for i in ids]
     fl_total = sum(flops_per[i] * alloc[i] for i in ids) * args.steps
+    fl_method = sum((flops_per[i] - twin_per[i]) * alloc[i] for i in ids) * args.steps
     achieved = fl_total / kern_s / 1e12
     launches = sum(p["launches"] for per in per_all for p in per)
     d2h = sum(p["d2h_bytes"] for per in per_all for p in per) / args.steps
     h2d = sum(p["h2d_bytes"] for per in per_all for p in per) / args.steps
     n_dd = sum(p["n_dd"] for per in per_all for p in per)
     zeroed = sum(p["n_nonfinite"] for per in per_all for p in per)
-    # the plain density on the same budget, after the timed region
-    plain = None
-    if learned and rank == 0:
+
+    plain = other = None
+    if rank == 0 and learned and not args.no_compare:
+        # the other acceptance test, same learned proposal, a few steps
+        other_mode = "relative" if args.accept == "paper" else "paper"
+        set_accept(other_mode)
+        k2 = min(args.steps, 3)
+        timed_steps(alloc, 1, 2 * 10 ** 6)
+        o_dev, _, o_per = timed_steps(alloc, k2, 3 * 10 ** 6)
+        o_val, o_sig, _, _ = ctx.run_estimate()
+        o_steps = sum(p["seconds"] for per in o_per for p in per)
+        o_kern = sum(p["kernel_seconds"] for per in o_per for p in per)
+        other = {"accept": other_mode, "steps": k2, "samples_per_s": sum(alloc) * k2 / o_dev,
+                 "inv_sigma2_per_s": 1.0 / (o_sig ** 2 * o_dev) if o_sig > 0 else None,
+                 "value": o_val, "sigma_down": o_sig,
+                 "dd_reevaluated": int(sum(p["n_dd"] for per in o_per for p in per)),
+                 "dd_share_of_step": max(o_steps - o_kern, 0.0) / o_steps if o_steps > 0 else None}
+        set_accept(args.accept)
+        # the plain density in the same batched, allocated form, at equal
+        # device time: its own pilot allocation, the step budget scaled by
+        # the measured time per sample of one plain step
         for i in ids:
             ctx.set_proposal(i, 0)
-        pp = []
-        pt = 0.0
-        for k in range(args.steps):
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
-            _, _, per = ctx.integrate(ids, args.samples, seed=k)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            pt += ev0.elapsed_time(ev1) / 1e3
-            pp.append(per)
-        pv, ps = estimate(merge(pp, ids, info), info)
-        ptot = args.samples * len(ids) * args.steps
-        plain = {"samples_per_s": ptot / pt, "inv_sigma2_per_s": 1.0 / (ps * ps * pt),
-                 "value": pv, "sigma_down": ps, "seconds": pt,
-                 "dd_reevaluated": int(sum(p["n_dd"] for per in pp for p in per))}
+        alloc_p = allocate()
+        p_dev1, _, _ = timed_steps(alloc_p, 1, 4 * 10 ** 6)
+        scale = (t_dev / args.steps) / max(p_dev1, 1e-9)
+        alloc_p = [max(1, int(round(n * scale))) for n in alloc_p]
+        p_dev, _, p_per = timed_steps(alloc_p, args.steps, 5 * 10 ** 6)
+        p_val, p_sig, p_up, _ = ctx.run_estimate()
+        p_steps = sum(p["seconds"] for per in p_per for p in per)
+        p_kern = sum(p["kernel_seconds"] for per in p_per for p in per)
+        plain = {"samples_per_s": sum(alloc_p) * args.steps / p_dev,
+                 "inv_sigma2_per_s": 1.0 / (p_sig ** 2 * p_dev) if p_sig > 0 else None,
+                 "value": p_val, "sigma_down": p_sig, "sigma_up": p_up, "seconds": p_dev,
+                 "seconds_learned": t_dev, "samples": sum(alloc_p) * args.steps,
+                 "dd_reevaluated": int(sum(p["n_dd"] for per in p_per for p in per)),
+                 "dd_share_of_step": max(p_steps - p_kern, 0.0) / p_steps if p_steps > 0 else None,
+                 "form": "same batched launch, own pilot allocation, step budget scaled to equal device time"}
+        for i in ids:
+            ctx.set_proposal(i, 1, 0.1)
     peak = ctx.fp64_peak() if rank == 0 else 0.0
     if rank != 0:
         if dist:
@@ -369,46 +407,51 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cids = [0, ngr // 2, ngr - 1] if canon is None else [canon[0], canon[len(canon) // 2], canon[-1]]
-        crate, cores, evals, wall = oracle_rate(args.loops, cids, args.oracle_samples)
+        cids = [canon[0], canon[len(canon) // 2], canon[-1]]
+        crate, cores, evals, wall, setup, _ = oracle_rate(args.loops, cids, args.oracle_samples)
         cpu = {"value": crate, "unit": "samples/s", "cores": cores, "kind": "oracle",
-               "sample": "canonical graphs %s of the %d-loop list, %d samples each, plain density (evaluation "
-                         "after per-graph setup, %.1f s on %d processes)" % (cids, args.loops, args.oracle_samples,
-                                                                             wall, cores)}
-    isps = 1.0 / (sigma ** 2 * t_dev) if sigma > 0 else None
-    default_workload = (args.loops == 3 and args.graphs == 0 and args.samples == 1 << 24 and learned
-                        and not args.no_alloc)
-    traffic = TRAFFIC_DEFAULT_BYTES if default_workload else None
+               "sample": "canonical graphs %s of the %d-loop list, %d samples each, plain density; evaluation "
+                         "%.1f s on %d processes after a per-graph set-up of up to %.1f s"
+                         % (cids, args.loops, args.oracle_samples, wall, cores, setup)}
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    nominal = 2 * 2 * sms * (ck["sm_mhz"] if ck else 2032.0) * 1e6 / 1e12   # 2 DFMA/SM/clk, FMA = 2 flops
     line = {
         "metric": METRIC, "value": rate, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": t_dev * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "%s %d %d-loop vertex graphs without lepton loops, %s" % (
-                       "all" if canon is None else "seeded subset of", len(ids), args.loops,
-                       "learned mixture density, one batched persistent launch per step" if learned
-                       else "plain density, one batched persistent launch per step" if batched
-                       else "plain density, one launch per graph"),
-                   "samples_per_graph_per_step": args.samples, "seed": "step index (+ rank offset)",
-                   "train_samples_per_graph": args.train if learned else 0,
+        "config": {"workload": workload_name(args.loops, ngr, N_GRAPHS[args.loops], learned),
+                   "canonical_ids": canon if ngr < N_GRAPHS[args.loops] else "all",
+                   "samples_per_step": sum(alloc), "seed": "run seed (+ rank offset), counters continue",
+                   "acceptance": args.accept, "train_samples_per_graph": args.train if learned else 0,
+                   "train_steps": args.train_steps if learned else 0,
                    "train_cost_ratio": args.cost_ratio if learned else None,
+                   "init_samples_per_graph": args.init_samples, "pilot_samples_per_graph": args.pilot,
                    "l2": "256 MB buffer written between timed steps", "parallelism": "dp%d" % world},
         "inv_sigma2_per_s": isps,
-        "inv_sigma2_per_s_incl_training": (1.0 / (sigma ** 2 * (t_dev + train_s + pilot_s + init_s)) if sigma > 0 else None),
-        "estimate": {"value": val, "sigma_down": sigma, "samples": total, "dd_reevaluated": int(n_dd),
-                     "zeroed": int(zeroed)},
-        "dd_pass": {"reevaluated": int(n_dd), "zeroed": int(zeroed),
-                    "seconds": max(step_s - kern_s, 0.0),
+        "inv_sigma2_per_s_incl_setup": (1.0 / (sigma ** 2 * (t_dev + train_s + pilot_s + init_s))
+                                        if sigma > 0 else None),
+        "estimate": {"value": val, "sigma_down": sigma, "sigma_up": sigma_up, "samples": total,
+                     "dd_reevaluated": int(n_dd), "zeroed": int(zeroed)},
+        "dd_pass": {"reevaluated": int(n_dd), "zeroed": int(zeroed), "seconds": max(step_s - kern_s, 0.0),
                     "share_of_step": (max(step_s - kern_s, 0.0) / step_s) if step_s > 0 else None,
-                    "note": "double-double re-evaluation, queue sort and reduction; not credited to the FP64 fraction"},
+                    "note": "double-double re-evaluation, queue sort and reduction; not credited to the FP64 "
+                            "fraction"},
         "plain_pdf": plain,
+        "gain_vs_plain": ({"inv_sigma2_per_s": isps / plain["inv_sigma2_per_s"],
+                           "note": "learned+batched over plain+batched, equal device time"}
+                          if plain and isps and plain["inv_sigma2_per_s"] else None),
+        "other_acceptance": other,
         "setup_seconds": {"compile": compile_s, "train": train_s, "pilot_allocation": pilot_s,
                           "initialisation": init_s},
-        "allocation": {"min": min(alloc), "max": max(alloc), "mode": "pilot, n_j ~ sigma_j/sqrt(t_j)"}
-        if batched and not args.no_alloc else None,
+        "allocation": {"min": min(alloc), "max": max(alloc), "mode": "pilot, n_j ~ sigma_j/sqrt(t_j)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if peak else None, "traffic": traffic,
-                     "kernel": ("batched_kernel" if batched else "integrate_kernel") + " (sampler + FP64 tape)",
-                     "peak_source": "measured: own DFMA probe (ae_fp64_peak)"},
+                     "frac": achieved / peak if peak else None, "traffic": TRAFFIC_DEFAULT_BYTES,
+                     "kernel": "batched_kernel (sampler + FP64 tape)",
+                     "peak_source": "measured: own DFMA probe (ae_fp64_peak)",
+                     "peak_nominal": nominal, "frac_vs_nominal": achieved / nominal,
+                     "frac_method_only": fl_method / kern_s / 1e12 / peak if peak else None,
+                     "note": "nominal = 2 DFMA per SM per cycle at the median SM clock; method_only leaves out "
+                             "the certified bound's magnitude twins"},
         "e2e": {"value": total / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),

@@ -56,6 +56,12 @@ typedef struct ae_opts {
                                         g under seed s starts at output
                                         s 2^96 + g 2^80 + 64 i of the stream from
                                         the state (12345 x 6); set before loading */
+  int grid_ctas;                     /* CTAs per FP64 integration launch, 0 =
+                                        automatic (SMs x resident CTAs).  A small
+                                        value makes every CTA run many rounds of
+                                        samples (used by the parity tests); the
+                                        results do not depend on it beyond the
+                                        summation order */
 } ae_opts;
 
 /* The settings of the paper's second calculation (Sec. V, Calc 1):
@@ -92,6 +98,12 @@ int ae_load_graph_subset(ae_ctx *ctx, int loops, const int *canonical_ids, int n
  * arguments.  No context needed. */
 int ae_seeded_subset(uint64_t n_total, int k, uint64_t seed, int *out);
 
+/* The canonical list of `loops` loops without compiling: *n_out = number of
+ * graphs; klass (3 ints per graph: (k, m, m') of Sec. V, Table I) and mult
+ * (1 int per graph) are filled when non-NULL and cap >= *n_out.  Returns 0,
+ * or -1 on bad arguments.  No context needed. */
+int ae_graph_classes(int loops, int *klass, int *mult, int cap, int *n_out);
+
 typedef struct ae_graph_meta {
   int loops, M, mult;
   int klass[3];          /* (k, m, m') of Sec. V, Table I */
@@ -124,6 +136,14 @@ typedef struct ae_graph_result {
   uint64_t d2h_bytes;    /* bytes read back to the host for this graph's result     */
   uint64_t h2d_bytes;    /* bytes copied to the device for this call (batched: on
                             the first graph's entry)                                */
+  double sigma_up;       /* mult * sigma_up: heuristic upper estimate of the
+                            standard deviation (Sec. III.B; the paper's own
+                            heuristic is in a reference that is not available,
+                            this is the library's): sigma_up^2 = sigma_down^2 +
+                            max y^2 / N^2, i.e. room for one more sample as large
+                            as the largest seen.  sigma_up / sigma_down is near 1
+                            when many samples carry sum y^2 and grows when one
+                            sample dominates it                                 */
 } ae_graph_result;
 
 /* Integrate the listed graphs with n_samples samples each, Philox seed
@@ -221,6 +241,23 @@ int ae_set_proposal(ae_ctx *ctx, int graph_id, int mode, double beta);
  * 2 dd_tol N mean|y|.  yfloor finite and >= 0. */
 int ae_set_accept_floor(ae_ctx *ctx, int graph_id, double yfloor);
 
+/* The paper's acceptance of a value (Sec. IV.A, Eq. eq_interval_accept): a
+ * value of graph j is kept when the width of its certified interval on y,
+ * 2 * (rounding-error bound of I carried to y), is at most
+ *     width_j = (1/4) sigma_down_j sqrt(sum_l sigma_down_l^2) / sum_l sigma_down_l,
+ * sigma_down from an initialisation pass over the graph set, so that the
+ * summed round-off error of the set stays below a quarter of its sigma_down.
+ * Values that fail are re-evaluated in double-double under the same width;
+ * those failing again count as zero.  ae_accept_widths computes width_j from
+ * n sigma_down values (host, no context; sigma_down_l <= 0 or not finite
+ * contribute nothing and get width 0); ae_set_accept_width sets one graph's
+ * width (width > 0: this test replaces the relative test of ae_opts.dd_tol
+ * for the graph; 0: back to the relative test).  Widths and sigma_down are
+ * those of each graph's contribution, multiplicity included (ae_graph_result
+ * .sigma); the library tests y against width / mult. */
+int ae_accept_widths(const double *sigma_down, int n, double *width);
+int ae_set_accept_width(ae_ctx *ctx, int graph_id, double width);
+
 /* Cost-aware training weights of the learned proposal (library design; the
  * paper has no learned part): with ratio R > 0, a training sample that the
  * acceptance test would send to double-double has its weight |y| divided by
@@ -242,6 +279,15 @@ int ae_proposal_eval(ae_ctx *ctx, int M, const float *params, const double *deg,
                      const double *w, uint64_t n, double *loss, float *grad,
                      double *log2p_out, double *degt_out);
 int ae_proposal_nparams(void);
+
+/* The trained proposal of a graph, for checking it outside the library:
+ * params (ae_proposal_nparams() floats, nullable) = the FP32 master weights
+ * (layout as in ae_proposal_eval); outputs (2^M * 16 floats, nullable) = the
+ * network outputs o(T) for every state T from which the sampling tables were
+ * built (BF16 weights and activations, FP32 accumulation); *beta (nullable)
+ * = the weight of the plain density in the mixture.  AE_ERR_STATE if the
+ * graph has no trained proposal. */
+int ae_proposal_export(ae_ctx *ctx, int graph_id, float *params, float *outputs, double *beta);
 
 /* Inter-graph allocation (Sec. IV.C).  A pilot of n_pilot samples per graph
  * (independent stream) estimates sigma_j; n_total samples are split into
@@ -274,6 +320,64 @@ int ae_schedule_probabilities(const double *sigma, const uint64_t *N, const doub
 int ae_integrate_adaptive(ae_ctx *ctx, const int *graph_ids, int n_ids, uint64_t block_size,
                           int n_rounds, int blocks_per_round, double p_floor, uint64_t seed,
                           double *value, double *sigma, ae_graph_result *per_graph);
+
+/* ------------------------------------------------------------ run state
+ * A run (Sec. IV.C: integration in blocks over a long campaign) keeps, per
+ * loaded graph, the next sample index of the graph's stream and the running
+ * sums below, so that a run can be continued, checkpointed, resumed and
+ * merged across ranks.  Because the generator is counter-based, a resumed
+ * run draws exactly the samples of an uninterrupted one. */
+typedef struct ae_run_graph {
+  uint64_t next;             /* next sample index of the graph's stream        */
+  uint64_t n, n_dd, n_zero;  /* samples, re-evaluated, zeroed (failed twice)    */
+  double sum_y[2];           /* sum of y, double-double (hi, lo)               */
+  double sum_y2[2];          /* sum of y^2                                     */
+  double sum_abs[2];         /* sum of |y|                                     */
+  double max_y2;             /* largest single y^2                             */
+} ae_run_graph;
+
+/* Start a run over all loaded graphs with the given seed: zero sums, next
+ * sample index 0 for every graph.  Loading graphs clears the run. */
+int ae_run_reset(ae_ctx *ctx, uint64_t seed);
+
+/* One block of the run: graph_ids[i] gets samples next .. next+n_samples[i]-1
+ * of its stream, all graphs in one batched launch (ae_integrate_batched's
+ * kernels, captured in a CUDA graph that later steps of the same shape
+ * launch again); the sums are added to the run and next advances.  per
+ * (nullable, n_ids entries) receives this block's own per-graph results
+ * (device seconds, launches, bytes copied included). */
+int ae_run_step(ae_ctx *ctx, const int *graph_ids, int n_ids, const uint64_t *n_samples,
+                ae_graph_result *per);
+
+/* Add an integration result of `count` samples of one graph (e.g. from
+ * ae_integrate_range at the graph's next index) to the run; next advances by
+ * count.  Host only. */
+int ae_run_add(ae_ctx *ctx, int graph_id, const ae_graph_result *r, uint64_t count);
+
+/* Copy the run state of all loaded graphs into out (n = number of loaded
+ * graphs), and the seed (nullable). */
+int ae_run_get(ae_ctx *ctx, ae_run_graph *out, int n, uint64_t *seed);
+
+/* Add another run's sums (e.g. another rank's, on its own stream) to this
+ * run, graph by graph in order, double-double; this run's next indices stay.
+ * n = number of loaded graphs. */
+int ae_run_merge(ae_ctx *ctx, const ae_run_graph *other, int n);
+
+/* The run's estimate: value = sum_j mult_j mean_j, sigma^2 = sum_j (mult_j
+ * sigma_down_j)^2 (Eqs. eq_integral_approx, eq_sigma_down, eq_sigma_sum),
+ * sigma_up likewise with the heuristic sigma_up_j (nullable outputs).  per
+ * (nullable) receives one result per loaded graph (graphs with no samples:
+ * value 0, sigma 0). */
+int ae_run_estimate(ae_ctx *ctx, double *value, double *sigma, double *sigma_up, ae_graph_result *per);
+
+/* Write the run (graph set identity: loop order, canonical ids, generator;
+ * seed; per-graph state) to `path` as a binary file closed by a CRC-64
+ * checksum; written to path + ".tmp" and renamed, so a crash leaves the old
+ * file.  ae_resume reads it back into a context holding the same graph set:
+ * AE_ERR_STATE (nothing changed) if the file is truncated, corrupt (checksum),
+ * of another format or of another graph set or generator. */
+int ae_checkpoint(ae_ctx *ctx, const char *path);
+int ae_resume(ae_ctx *ctx, const char *path);
 
 /* Two independent calculations (e.g. Calc 1 and Calc 2) combined as in
  * Sec. V: per graph by inverse-variance weighting (v = sum w v / sum w,
@@ -325,6 +429,13 @@ int ae_terms(ae_ctx *ctx, int graph_id, int *buf, int cap, int *len);
  * machines without a GPU; no integration call uses it. */
 int aetest_tape_replay(ae_ctx *ctx, int graph_id, const double *z, size_t count,
                        double *I, double *K, double *E);
+
+/* Test hook (device): runs the FP64 integration kernel on one graph with
+ * the tape copy for the first segment left out and the bounded wait for it
+ * shortened to about `wait_cycles` clock cycles, so that the wait runs out
+ * (nothing is in flight).  Returns what the integration entry points return
+ * in that case: AE_ERR_TIMEOUT, with the context still usable. */
+int aetest_stage_timeout(ae_ctx *ctx, int graph_id, long long wait_cycles);
 
 /* Test hook (device): the learned sampler's fused-multiply-add exp2 and log2
  * next to the device library's exp2 and log2, on n arguments x (exp2) and y

@@ -78,3 +78,21 @@ def uniforms(sample_idx, graph_id, seed, nblocks):
             c = (w[2 * h + 1] >> np.uint64(6)).astype(np.float64)
             out[:, 2 * b + h] = (a * 67108864.0 + c + 0.5) * (2.0 ** -53)
     return out
+
+
+def uniforms_fine(sample_idx, graph_id, seed, nblocks):
+    """The learned sampler's uniforms from the same words: the 52 high-order
+    bits of (w0, w1) (all of w0, the top 20 of w1) form m, and
+    u = (2m + 1) 2^-53 in (0, 1) (midpoint of the m-th cell of width 2^-52).
+    Same layout as uniforms()."""
+    s = np.asarray(sample_idx, np.uint64)
+    lo = s & np.uint64(MASK)
+    hi = s >> np.uint64(32)
+    out = np.empty((s.shape[0], 2 * nblocks))
+    for b in range(nblocks):
+        w = philox_np(lo, hi, np.full_like(s, graph_id), np.full_like(s, b),
+                      seed & MASK, (seed >> 32) & MASK)
+        for h in range(2):
+            m = (w[2 * h] << np.uint64(20)) | (w[2 * h + 1] >> np.uint64(12))
+            out[:, 2 * b + h] = (2.0 * m.astype(np.float64) + 1.0) * (2.0 ** -53)
+    return out

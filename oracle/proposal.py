@@ -14,8 +14,22 @@ library's extension, see the design notes):
     + Deg_theta(S_l) ln t_l] - sum ln z;
   * loss = -sum_i w_i ln q_theta(z_i) / sum_i w_i (the -sum ln z term,
     independent of the network, is left out).
+Sampling with the trained network (learned_points): the defensive mixture
+q = (1 - beta) q_theta + beta g.  With u_0 < beta the plain density g is
+drawn (its component pick taken from u_0 / beta; the sector walk divides
+log2 u by Deg), otherwise the learned walk: remove from T the first j in T
+(ascending) whose cumulative P(j'|T) over j' <= j exceeds the uniform (the
+last j in T if none does), then t = u^(1/Deg_theta(T without j)).  Uniforms:
+philox.uniforms_fine.  The density is log2 q = log2((1 - beta) q_theta +
+beta g), g from sampler.log2_density.
+
 Gradients by explicit backpropagation in float64; pinned by central finite
-differences of the loss itself.
+differences of the loss itself.  forward()/loss_and_grad() round weights,
+activations and the backward signals to BF16 at the points where the
+device kernels do (FP32 accumulation there, float64 here);
+grad_unrounded()/loss_only() use unrounded float64 throughout.  Pins of the
+learned sampler: E_g[q/g] = 1 (q is a density on the simplex) and the
+zero-output identity.
 """
 import numpy as np
 
@@ -55,13 +69,15 @@ def features(M):
 
 
 def forward(params, M):
+    """Forward pass as the device runs it: BF16 weights and features, each
+    hidden activation rounded to BF16 after bias and ReLU, outputs kept."""
     w = unpack(params)
     W = {k: (bf16(v) if k.startswith("W") else np.asarray(v, dtype=np.float32).astype(np.float64))
          for k, v in w.items()}
     X = bf16(features(M))
-    z1 = X @ W["W1"].T + W["b1"]; h1 = np.maximum(z1, 0)
-    z2 = h1 @ W["W2"].T + W["b2"]; h2 = np.maximum(z2, 0)
-    z3 = h2 @ W["W3"].T + W["b3"]; h3 = np.maximum(z3, 0)
+    z1 = X @ W["W1"].T + W["b1"]; h1 = bf16(np.maximum(z1, 0))
+    z2 = h1 @ W["W2"].T + W["b2"]; h2 = bf16(np.maximum(z2, 0))
+    z3 = h2 @ W["W3"].T + W["b3"]; h3 = bf16(np.maximum(z3, 0))
     o = h3 @ W["W4"].T + W["b4"]
     return dict(W=W, X=X, h1=h1, h2=h2, h3=h3, o=o)
 
@@ -114,14 +130,17 @@ def loss_and_grad(params, deg, wplain, order, lt, w, M):
     dO = np.zeros_like(o)
     dO[:, :15] = dl[:, :15] * (1 - np.tanh(o[:, :15] / LAM) ** 2)
     dO[:, 15] = dl[:, 15] * (1 - np.tanh(o[:, 15] / KAP) ** 2)
+    # backward as the device runs it: the output signal and every hidden
+    # signal rounded to BF16 before they enter a product
+    dO = bf16(dO)
     W = f["W"]
     g = {}
     g["W4"] = dO.T @ f["h3"]; g["b4"] = dO.sum(0)
-    d3 = (dO @ W["W4"]) * (f["h3"] > 0)
+    d3 = bf16((dO @ W["W4"]) * (f["h3"] > 0))
     g["W3"] = d3.T @ f["h2"]; g["b3"] = d3.sum(0)
-    d2 = (d3 @ W["W3"]) * (f["h2"] > 0)
+    d2 = bf16((d3 @ W["W3"]) * (f["h2"] > 0))
     g["W2"] = d2.T @ f["h1"]; g["b2"] = d2.sum(0)
-    d1 = (d2 @ W["W2"]) * (f["h1"] > 0)
+    d1 = bf16((d2 @ W["W2"]) * (f["h1"] > 0))
     g["W1"] = d1.T @ f["X"]; g["b1"] = d1.sum(0)
     grad = np.concatenate([g[name].ravel() for name, _ in SIZES])
     return loss, grad, logp, degt
@@ -181,3 +200,94 @@ def grad_unrounded(params, deg, wplain, order, lt, w, M):
     d2 = (d3 @ wts["W3"]) * (z2 > 0); g["W2"] = d2.T @ h1; g["b2"] = d2.sum(0)
     d1 = (d2 @ wts["W2"]) * (z1 > 0); g["W1"] = d1.T @ X; g["b1"] = d1.sum(0)
     return np.concatenate([g[name].ravel() for name, _ in SIZES])
+
+
+def learned_points(dens, o, beta, u):
+    """Draw from the defensive mixture (1 - beta) q_theta + beta g of one
+    graph with network outputs o (2^M x 16, as exported by the library) and
+    uniforms u (S x 2M, philox.uniforms_fine).  Returns (z, log2 q, plain)
+    with plain = True where the plain density was drawn."""
+    from .sampler import log2_density
+    M = dens.M
+    full = (1 << M) - 1
+    deg1, phi1 = dens.deg[0], dens.phi[0]
+    wplain = np.ones(1 << M)
+    wplain[1:-1] = phi1[1:-1] / deg1[1:-1]
+    logp, degt = tables(o, deg1, wplain, M)
+    P = np.where(np.isfinite(logp), np.exp(logp), 0.0)
+    Pc = np.cumsum(P, axis=1)          # cumulative over j' <= j, in the order of j
+    S = u.shape[0]
+    lz = np.zeros((S, M))
+    plain = u[:, 0] < beta
+    for s in range(S):
+        T = full
+        cur = 0.0
+        if plain[s]:
+            pick = u[s, 0] / beta
+            c1, c3, c4 = dens.C
+            comp = 0 if pick < c1 else 1 if pick < c1 + dens.C2 else 2 if pick < c1 + dens.C2 + c3 else 3
+            if comp == 1:
+                lz[s] = np.log2(-np.log2(u[s, 1:1 + M]))
+                continue
+            k = 0 if comp == 0 else comp - 1
+            deg, phi = dens.deg[k], dens.phi[k]
+            for l in range(M - 1):
+                target = u[s, 1 + 2 * l] * phi[T]
+                acc = 0.0
+                chosen = -1
+                last = 0
+                for j in range(M):
+                    if T >> j & 1:
+                        acc = acc + phi[T ^ (1 << j)] / deg[T ^ (1 << j)]
+                        if chosen < 0 and target < acc:
+                            chosen = j
+                        last = j
+                chosen = last if chosen < 0 else chosen
+                lz[s, chosen] = cur
+                T ^= 1 << chosen
+                cur = cur + np.log2(u[s, 2 + 2 * l]) / deg[T]
+        else:
+            for l in range(M - 1):
+                uc = u[s, 1 + 2 * l]
+                js = [j for j in range(M) if T >> j & 1]
+                chosen = js[-1]
+                for j in js:
+                    if uc < Pc[T, j]:
+                        chosen = j
+                        break
+                lz[s, chosen] = cur
+                T ^= 1 << chosen
+                cur = cur + np.log2(u[s, 2 + 2 * l]) / degt[T]
+        lz[s, int(np.log2(T))] = cur
+    e = np.exp2(lz)
+    ssum = e.sum(1)
+    z = e / ssum[:, None]
+    lz = lz - np.log2(ssum)[:, None]
+    return z, log2_mixture(dens, logp, degt, beta, lz), plain
+
+
+def log2_learned(logp, degt, lz, M):
+    """log2 q_theta at points given by log2 z (S x M): the ordering's
+    probabilities times prod Deg_theta(S_l) t_l^Deg_theta(S_l) / prod z."""
+    order = np.argsort(-lz, axis=1, kind="stable")
+    full = (1 << M) - 1
+    out = np.empty(lz.shape[0])
+    for s in range(lz.shape[0]):
+        T = full
+        lq = 0.0
+        for l in range(M - 1):
+            j = order[s, l]
+            lq += logp[T, j] / np.log(2.0)
+            T ^= 1 << j
+            lq += np.log2(degt[T]) + degt[T] * (lz[s, order[s, l + 1]] - lz[s, j])
+        out[s] = lq - lz[s].sum()
+    return out
+
+
+def log2_mixture(dens, logp, degt, beta, lz):
+    """log2((1 - beta) q_theta + beta g) at points given by log2 z."""
+    from .sampler import log2_density
+    a = np.log2(beta) + log2_density(dens, lz)
+    b = np.log2(1.0 - beta) + log2_learned(logp, degt, lz, dens.M) if beta < 1 else np.full(lz.shape[0], -np.inf)
+    m = np.maximum(a, b)
+    return m + np.log2(np.exp2(a - m) + np.exp2(b - m))

@@ -25,7 +25,7 @@ class AeOpts(ctypes.Structure):
                 ("C_subO", ctypes.c_double), ("C_bigZ", ctypes.c_double), ("C_bigF", ctypes.c_double),
                 ("C_add", ctypes.c_double), ("deg_max", ctypes.c_double), ("dd_tol", ctypes.c_double),
                 ("block_size", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("rng", ctypes.c_int)]
+                ("rng", ctypes.c_int), ("grid_ctas", ctypes.c_int)]
 
 
 class AeGraphMeta(ctypes.Structure):
@@ -35,6 +35,12 @@ class AeGraphMeta(ctypes.Structure):
                 ("tape_len", ctypes.c_int), ("nslots", ctypes.c_int),
                 ("n_monomials", ctypes.c_int), ("flops", ctypes.c_double), ("canonical_id", ctypes.c_int),
                 ("bound_depth", ctypes.c_int), ("flops_bound", ctypes.c_double)]
+
+
+class AeRunGraph(ctypes.Structure):
+    _fields_ = [("next", ctypes.c_uint64), ("n", ctypes.c_uint64), ("n_dd", ctypes.c_uint64),
+                ("n_zero", ctypes.c_uint64), ("sum_y", ctypes.c_double * 2), ("sum_y2", ctypes.c_double * 2),
+                ("sum_abs", ctypes.c_double * 2), ("max_y2", ctypes.c_double)]
 
 
 class AeTrainReport(ctypes.Structure):
@@ -49,7 +55,7 @@ class AeGraphResult(ctypes.Structure):
                 ("n", ctypes.c_uint64), ("n_dd", ctypes.c_uint64), ("n_nonfinite", ctypes.c_uint64),
                 ("seconds", ctypes.c_double), ("launches", ctypes.c_uint64),
                 ("kernel_seconds", ctypes.c_double), ("d2h_bytes", ctypes.c_uint64),
-                ("h2d_bytes", ctypes.c_uint64)]
+                ("h2d_bytes", ctypes.c_uint64), ("sigma_up", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -98,6 +104,20 @@ def lib():
         L.ae_proposal_eval.argtypes = [vp, ctypes.c_int, P(ctypes.c_float), dp, dp, P(ctypes.c_uint8),
                                        P(ctypes.c_float), dp, ctypes.c_uint64, dp, P(ctypes.c_float), dp, dp]
         L.ae_proposal_nparams.restype = ctypes.c_int
+        L.ae_accept_widths.argtypes = [dp, ctypes.c_int, dp]
+        L.ae_graph_classes.argtypes = [ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int), ctypes.c_int,
+                                       P(ctypes.c_int)]
+        L.ae_set_accept_width.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+        L.ae_proposal_export.argtypes = [vp, ctypes.c_int, P(ctypes.c_float), P(ctypes.c_float), dp]
+        L.ae_run_reset.argtypes = [vp, ctypes.c_uint64]
+        L.ae_run_step.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_uint64), P(AeGraphResult)]
+        L.ae_run_add.argtypes = [vp, ctypes.c_int, P(AeGraphResult), ctypes.c_uint64]
+        L.ae_run_get.argtypes = [vp, P(AeRunGraph), ctypes.c_int, P(ctypes.c_uint64)]
+        L.ae_run_merge.argtypes = [vp, P(AeRunGraph), ctypes.c_int]
+        L.ae_run_estimate.argtypes = [vp, dp, dp, dp, P(AeGraphResult)]
+        L.ae_checkpoint.argtypes = [vp, ctypes.c_char_p]
+        L.ae_resume.argtypes = [vp, ctypes.c_char_p]
+        L.aetest_stage_timeout.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
         L.ae_integrate_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, P(AeGraphResult)]
         L.ae_eval_samples.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                       dp, dp, dp, dp, dp, dp]
@@ -143,6 +163,28 @@ def combine_runs(v1, s1, v2, s2):
     if rc != 0:
         raise AeError("ae_combine_runs: AE_ERR_ARG")
     return v, s, tot.value, ts.value
+
+
+def accept_widths(sigma_down):
+    """Host: widths of the paper's acceptance test (ae_accept_widths)."""
+    sig = np.ascontiguousarray(sigma_down, dtype=np.float64)
+    w = np.empty(len(sig))
+    if lib().ae_accept_widths(_ptr(sig), len(sig), _ptr(w)) != 0:
+        raise AeError("ae_accept_widths: AE_ERR_ARG")
+    return w
+
+
+def graph_classes(loops):
+    """(klass [n, 3], mult [n]) of the canonical list of `loops` loops."""
+    n = ctypes.c_int()
+    if lib().ae_graph_classes(int(loops), None, None, 0, ctypes.byref(n)) != 0:
+        raise AeError("ae_graph_classes: AE_ERR_ARG")
+    k = np.empty((n.value, 3), dtype=np.int32)
+    m = np.empty(n.value, dtype=np.int32)
+    if lib().ae_graph_classes(int(loops), _ptr(k, ctypes.c_int), _ptr(m, ctypes.c_int), n.value,
+                              ctypes.byref(n)) != 0:
+        raise AeError("ae_graph_classes: AE_ERR_ARG")
+    return k, m
 
 
 def seeded_subset(n_total, k, seed=0):
@@ -279,6 +321,69 @@ class Context:
         """Absolute floor on |y| in the acceptance test of the graph's FP64
         values (kept when bound <= dd_tol * max(|y|, yfloor))."""
         self._check(lib().ae_set_accept_floor(self._h, gid, float(yfloor)))
+
+    def set_accept_width(self, gid, width):
+        """The paper's acceptance test for the graph: keep a value when its
+        certified interval on y is at most `width` wide (0: relative test)."""
+        self._check(lib().ae_set_accept_width(self._h, gid, float(width)))
+
+    def proposal_export(self, gid):
+        """(FP32 master weights, network outputs o(T) [2^M, 16], beta) of the
+        graph's trained proposal."""
+        M = self.graph_info(gid)["M"]
+        p = np.empty(lib().ae_proposal_nparams(), dtype=np.float32)
+        o = np.empty((1 << M) * 16, dtype=np.float32)
+        b = ctypes.c_double()
+        self._check(lib().ae_proposal_export(self._h, gid, _ptr(p, ctypes.c_float), _ptr(o, ctypes.c_float),
+                                             ctypes.byref(b)))
+        return p, o.reshape(1 << M, 16), b.value
+
+    # ------------------------------------------------------- run state --
+    def run_reset(self, seed):
+        self._check(lib().ae_run_reset(self._h, int(seed)))
+
+    def run_step(self, ids, n_samples):
+        """One batched block of the run; returns this block's per-graph results."""
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        ns = np.ascontiguousarray(n_samples, dtype=np.uint64)
+        res = (AeGraphResult * len(ids))()
+        self._check(lib().ae_run_step(self._h, _ptr(ids, ctypes.c_int), len(ids), _ptr(ns, ctypes.c_uint64), res))
+        return [r.as_dict() for r in res]
+
+    def run_add(self, gid, result, count):
+        r = AeGraphResult()
+        for k, _ in AeGraphResult._fields_:
+            if k in result:
+                setattr(r, k, result[k])
+        self._check(lib().ae_run_add(self._h, gid, ctypes.byref(r), int(count)))
+
+    def run_get(self):
+        """(array of AeRunGraph, one per loaded graph; seed)."""
+        arr = (AeRunGraph * self.n_graphs)()
+        seed = ctypes.c_uint64()
+        self._check(lib().ae_run_get(self._h, arr, self.n_graphs, ctypes.byref(seed)))
+        return arr, seed.value
+
+    def run_merge(self, other):
+        self._check(lib().ae_run_merge(self._h, other, len(other)))
+
+    def run_estimate(self):
+        """(value, sigma_down, sigma_up, per-graph results) of the run."""
+        v = ctypes.c_double(); s = ctypes.c_double(); u = ctypes.c_double()
+        res = (AeGraphResult * self.n_graphs)()
+        self._check(lib().ae_run_estimate(self._h, ctypes.byref(v), ctypes.byref(s), ctypes.byref(u), res))
+        return v.value, s.value, u.value, [r.as_dict() for r in res]
+
+    def checkpoint(self, path):
+        self._check(lib().ae_checkpoint(self._h, os.fsencode(path)))
+
+    def resume(self, path):
+        self._check(lib().ae_resume(self._h, os.fsencode(path)))
+
+    def test_stage_timeout(self, gid, wait_cycles):
+        """Test hook: make the bounded tape-staging wait run out (returns the
+        error the integration would raise)."""
+        self._check(lib().aetest_stage_timeout(self._h, gid, int(wait_cycles)))
 
     def proposal_eval(self, M, params, deg, wplain, order, lt, w):
         params = np.ascontiguousarray(params, dtype=np.float32)

@@ -60,9 +60,21 @@ struct ae_ctx {
   size_t bbuf_bytes = 0;
   int last_tune_block = 0;
   unsigned long long last_tune_chunk = 0;
+  // the batched launch captured as a CUDA graph, kept for the next call with
+  // the same launch shape, buffers and scalar arguments (a run's steps)
+  std::string gkey;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t gev[3] = {nullptr, nullptr, nullptr};
+  // run state (ae_run_*): one entry per loaded graph
+  uint64_t run_seed = 0;
+  std::vector<ae_run_graph> run;
 };
 
 
 int ae_fail(ae_ctx *c, int code, const std::string &msg);
+// mean, sigma_down and sigma_up of a result from its sums (runtime.cu)
+void ae_result_finish(ae_graph_result *r, int mult, double sum_abs);
+// fold a result of `count` samples of one graph into the run (runstate.cu)
+void ae_run_fold(ae_ctx *c, int gid, const ae_graph_result &r, uint64_t count);
 // uploads the sampler's log2/exp2 tables into learned.cu's constant memory
 cudaError_t ae_learned_upload_tables();

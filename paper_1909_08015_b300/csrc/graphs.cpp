@@ -195,3 +195,23 @@ std::vector<Term> rnew_terms(const Graph &g, const std::vector<Sub> &subs) {
 }
 
 }  // namespace ae
+
+// The canonical list of one loop order without compiling anything: per graph
+// its class (k, m, m') of Sec. V, Table I, and its multiplicity.
+extern "C" int ae_graph_classes(int loops, int *klass, int *mult, int cap, int *n_out) {
+  if (loops < 1 || loops > 5 || !n_out) return -1;
+  try {
+    const std::vector<ae::Graph> gs = ae::enumerate_graphs(loops);
+    *n_out = (int)gs.size();
+    if (!klass && !mult) return 0;
+    if (cap < (int)gs.size()) return -1;
+    for (size_t i = 0; i < gs.size(); ++i) {
+      if (klass)
+        for (int k = 0; k < 3; ++k) klass[3 * i + k] = gs[i].klass[k];
+      if (mult) mult[i] = gs[i].mult;
+    }
+  } catch (...) {
+    return -1;
+  }
+  return 0;
+}

@@ -22,6 +22,7 @@ struct GraphDev {
   int M, ntape, nslots, outI, outK, outE;
   int graph_id;
   double yfloor = 0;      // absolute floor on |y| in the acceptance of a value
+  double ywidth = 0;      // > 0: the paper's acceptance, interval width on y <= ywidth
   double C1, C2, C3, C4, log2_fact;
   double log2C[4];        // log2 of C1..C4 (g1, g2, g3, g4 order)
   double log2phi_full[3];
@@ -169,18 +170,23 @@ __device__ __forceinline__ void weight2(double I, double E, double lg, double &y
   Ey = ldexp(__dmul_rn(E, s), -kc);
 }
 
-// Acceptance of a value (Sec. IV.A, Eq. eq_interval_accept, library
-// reading): the certified rounding-error bound of I, carried to y = I/g like
-// I, must not exceed tol * max(|y|, yfloor).  tol <= 0 accepts every finite
-// value.  For the double-double twin the bound is scaled from the FP64 unit
-// 2^-53 to 2^-100 (the double-double operations' unit with a margin for the
-// non-normalising additions).
+// Acceptance of a value (Sec. IV.A).  The certified rounding-error bound Ey
+// of y (the bound of I carried to y = I/g like I) gives the interval
+// [y - Ey, y + Ey].  With a graph width set (G.ywidth > 0) the paper's test
+// of Eq. eq_interval_accept applies: the interval's width 2 Ey must not
+// exceed ywidth.  Otherwise the library's relative test: Ey <= tol *
+// max(|y|, yfloor); tol <= 0 accepts every finite value.  For the
+// double-double twin the bound is scaled from the FP64 unit 2^-53 to 2^-100
+// (the double-double operations' unit with a margin for the non-normalising
+// additions).
 __device__ __forceinline__ bool fp64_rejected(const GraphDev &G, double y, double Ey, double tol) {
   if (!isfinite(y) || !isfinite(Ey)) return true;
+  if (G.ywidth > 0) return 2.0 * Ey > G.ywidth;
   return tol > 0 && Ey > tol * fmax(fabs(y), G.yfloor);
 }
 __device__ __forceinline__ bool dd_rejected(const GraphDev &G, double y, double Ey, double tol) {
   if (!isfinite(y) || !isfinite(Ey)) return true;
+  if (G.ywidth > 0) return 2.0 * (Ey * 0x1p-47) > G.ywidth;
   return tol > 0 && Ey * 0x1p-47 > tol * fmax(fabs(y), G.yfloor);
 }
 
@@ -377,6 +383,7 @@ struct Stage {
   uint64_t *bar;        // 2 mbarriers, shared memory
   uint32_t issued;      // segments issued (thread 0's view)
   uint32_t used;        // segments consumed (identical in every thread)
+  long long wait;       // bound of one wait in clock cycles (kWaitCycles)
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -403,18 +410,28 @@ __device__ __forceinline__ void stage_issue(Stage &st, const GraphDev &G, int se
   ++st.issued;
 }
 
-// every thread: wait until the next segment to consume has landed; false if
-// the bounded wait ran out
-__device__ __forceinline__ bool stage_wait(const Stage &st) {
-  const uint32_t bar = smem_addr(st.bar + (st.used & 1)), parity = (st.used >> 1) & 1;
+// wait (bounded by st.wait cycles) until segment number k has landed in its
+// buffer; false if the wait ran out
+__device__ __forceinline__ bool stage_wait_seg(const Stage &st, uint32_t k) {
+  const uint32_t bar = smem_addr(st.bar + (k & 1)), parity = (k >> 1) & 1;
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
     asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
     if (done) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > st.wait) return false;
   }
+}
+
+// every thread: wait until the next segment to consume has landed
+__device__ __forceinline__ bool stage_wait(const Stage &st) { return stage_wait_seg(st, st.used); }
+
+// thread 0, after a wait ran out: wait (again bounded) for the copies it
+// issued that were not consumed, so that none is still writing into the
+// CTA's shared memory when the CTA leaves
+__device__ __forceinline__ void stage_drain(const Stage &st) {
+  for (uint32_t k = st.used; k < st.issued; ++k) (void)stage_wait_seg(st, k);
 }
 
 // All threads of the CTA together: run G's tape on this thread's row (only
@@ -430,7 +447,7 @@ static __device__ bool run_tape_staged(Stage &st, const GraphDev &G, double *S, 
     // after this barrier every thread has finished segment s-1: its buffer
     // may be refilled
     if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicExch(err, 1);
+      if (threadIdx.x == 0) { atomicExch(err, 1); stage_drain(st); }
       return false;
     }
     if (threadIdx.x == 0) {
@@ -453,48 +470,86 @@ static __device__ bool run_tape_staged(Stage &st, const GraphDev &G, double *S, 
   return true;
 }
 
-// Double-double twin of run_tape (rows of hi/lo pairs; offsets scaled by 2;
-// constants with their low parts from the pool).  Magnitude twins stay in
-// FP64 (their low parts are zero); the compiler's hints I_KX, I_C0, I_B1
-// select the shorter exact forms of a product, a scaling and a sum.
+// One double-double tape instruction on this thread's row Sb (hi/lo pairs;
+// the instruction's byte offsets scaled by 2; constants with their low parts
+// from the pool).  Magnitude twins stay in FP64 (their low parts are zero);
+// the compiler's hints I_KX, I_C0, I_B1 select the shorter exact forms of a
+// product, a scaling and a sum.
+__device__ __forceinline__ void tape_step_dd(const uint4 &w0, const uint4 &w1, char *Sb, const double *khi,
+                                             const double *klo) {
+  const uint32_t op = w0.x & 0xffffu, d = (w0.x >> 16) * 2, a = (w0.y & 0xffffu) * 2, b = (w0.y >> 16) * 2,
+                 c = (w0.z & 0xffffu) * 2, kbi = w0.z >> 16, kci = w0.w & 0xffffu;
+  const dd va = *reinterpret_cast<const dd *>(Sb + a);
+  // exact constants (I_KX) come from the instruction's immediates, others
+  // with their low parts from the pool
+  const dd vb = !(op & I_BK) ? *reinterpret_cast<const dd *>(Sb + b)
+                : (op & I_KX) ? dd{__hiloint2double((int)w1.y, (int)w1.x), 0.0}
+                              : dd{__ldg(khi + kbi), __ldg(klo + kbi)};
+  const dd vc = !(op & I_CK) ? *reinterpret_cast<const dd *>(Sb + c)
+                : (op & I_KX) ? dd{__hiloint2double((int)w1.w, (int)w1.z), 0.0}
+                              : dd{__ldg(khi + kci), __ldg(klo + kci)};
+  dd r;
+  const uint32_t sp = op & 0xff00u;
+  if (op & I_AB) r = dd{__fma_rn(fabs(va.hi), fabs(vb.hi), fabs(vc.hi)), 0.0};   // magnitudes: FP64 is enough
+  else if (sp == 0) {
+    // the compiler's hints pick the shortest exact form of c + a*b
+    const bool bx = (op & (I_BK | I_KX)) == (I_BK | I_KX);   // b an exact constant
+    if (op & I_C0) r = bx ? dd_scale_x(vb.hi, va) : dd_mul_fast(va, vb);
+    else if (op & I_B1) r = dd_add_fast(vc, vb.hi > 0 ? va : dd{-va.hi, -va.lo});
+    else if (bx) r = dd_fma_x(vc, vb.hi, va);
+    else r = dd_fma_fast(vc, vb, va);
+  }
+  else if (sp == I_DIV) r = dd_div(va, vb);
+  else if (sp == I_ABS) r = dd_abs(va);
+  else r = dd_add_fast(vc, dd_abs(va));   // I_ADDABS
+  *reinterpret_cast<dd *>(Sb + d) = r;
+}
+
+// Double-double twin of run_tape, instructions read from global memory (next
+// one prefetched): the per-sample dumps.
 static __device__ void run_tape_dd(const GraphDev &G, dd *S) {
   char *Sb = reinterpret_cast<char *>(S);
   const uint4 *code = reinterpret_cast<const uint4 *>(G.code);
-  const double *khi = G.khi, *klo = G.klo;
   const int n = G.ntape;
   if (n <= 0) return;
-  uint4 w0 = __ldg(code), w1 = __ldg(code + 1);   // next instruction prefetched in the loop
+  uint4 w0 = __ldg(code), w1 = __ldg(code + 1);
   for (int pc = 0; pc < n; ++pc) {
     const int nx = 2 * min(pc + 1, n - 1);
     const uint4 n0 = __ldg(code + nx), n1 = __ldg(code + nx + 1);
-    const uint32_t op = w0.x & 0xffffu, d = (w0.x >> 16) * 2, a = (w0.y & 0xffffu) * 2, b = (w0.y >> 16) * 2,
-                   c = (w0.z & 0xffffu) * 2, kbi = w0.z >> 16, kci = w0.w & 0xffffu;
-    const dd va = *reinterpret_cast<const dd *>(Sb + a);
-    // exact constants (I_KX) come from the instruction's immediates, others
-    // with their low parts from the pool
-    const dd vb = !(op & I_BK) ? *reinterpret_cast<const dd *>(Sb + b)
-                  : (op & I_KX) ? dd{__hiloint2double((int)w1.y, (int)w1.x), 0.0}
-                                : dd{__ldg(khi + kbi), __ldg(klo + kbi)};
-    const dd vc = !(op & I_CK) ? *reinterpret_cast<const dd *>(Sb + c)
-                  : (op & I_KX) ? dd{__hiloint2double((int)w1.w, (int)w1.z), 0.0}
-                                : dd{__ldg(khi + kci), __ldg(klo + kci)};
-    dd r;
-    const uint32_t sp = op & 0xff00u;
-    if (op & I_AB) r = dd{__fma_rn(fabs(va.hi), fabs(vb.hi), fabs(vc.hi)), 0.0};   // magnitudes: FP64 is enough
-    else if (sp == 0) {
-      // the compiler's hints pick the shortest exact form of c + a*b
-      const bool bx = (op & (I_BK | I_KX)) == (I_BK | I_KX);   // b an exact constant
-      if (op & I_C0) r = bx ? dd_scale_x(vb.hi, va) : dd_mul_fast(va, vb);
-      else if (op & I_B1) r = dd_add_fast(vc, vb.hi > 0 ? va : dd{-va.hi, -va.lo});
-      else if (bx) r = dd_fma_x(vc, vb.hi, va);
-      else r = dd_fma_fast(vc, vb, va);
-    }
-    else if (sp == I_DIV) r = dd_div(va, vb);
-    else if (sp == I_ABS) r = dd_abs(va);
-    else r = dd_add_fast(vc, dd_abs(va));   // I_ADDABS
-    *reinterpret_cast<dd *>(Sb + d) = r;
+    tape_step_dd(w0, w1, Sb, G.khi, G.klo);
     w0 = n0; w1 = n1;
   }
+}
+
+// Double-double twin of run_tape_staged: all threads of the CTA step through
+// the same tape segments in shared memory (same staging, same bounded waits);
+// segment 0 must have been issued.  Returns false (in every thread) if a wait
+// ran out; *err is set and the caller must leave the kernel.
+static __device__ bool run_tape_dd_staged(Stage &st, const GraphDev &G, dd *S, bool active, int *err) {
+  char *Sb = reinterpret_cast<char *>(S);
+  const int nseg = (G.ntape + kSeg - 1) / kSeg;
+  const double *khi = G.khi, *klo = G.klo;
+  for (int s = 0; s < nseg; ++s) {
+    const bool ok = stage_wait(st);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) { atomicExch(err, 1); stage_drain(st); }
+      return false;
+    }
+    if (threadIdx.x == 0 && s + 1 < nseg) stage_issue(st, G, s + 1);
+    const uint4 *code = reinterpret_cast<const uint4 *>(st.buf + (st.used & 1) * kSeg);
+    const int cnt = min(kSeg, G.ntape - s * kSeg);
+    ++st.used;
+    if (!active) continue;
+    uint4 w0 = code[0], w1 = code[1];
+#pragma unroll 1
+    for (int k = 0; k < cnt; ++k) {
+      const int nx = 2 * min(k + 1, cnt - 1);
+      const uint4 n0 = code[nx], n1 = code[nx + 1];
+      tape_step_dd(w0, w1, Sb, khi, klo);
+      w0 = n0; w1 = n1;
+    }
+  }
+  return true;
 }
 
 __device__ __forceinline__ void dd_acc(double &hi, double &lo, double x) {

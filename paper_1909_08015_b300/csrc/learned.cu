@@ -41,7 +41,7 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NW1, OFF_W2 = OFF_B1 + HID, OFF_B2 =
 constexpr int OFF_W3 = OFF_B2 + HID, OFF_B3 = OFF_W3 + NW3, OFF_W4 = OFF_B3 + HID, OFF_B4 = OFF_W4 + NW4;
 constexpr int NPARAM = OFF_B4 + OUT;   // 11472
 constexpr double GSCALE = 1099511627776.0;   // 2^40 fixed point for gradient sums
-constexpr float LAM = 3.0f, KAP = 0.7f;
+constexpr double LAM = 3.0, KAP = 0.7;   // bounds of the logit and exponent corrections
 
 
 __device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {
@@ -693,6 +693,35 @@ extern "C" int ae_set_accept_floor(ae_ctx *c, int gid, double yfloor) {
   if (gid < 0 || gid >= (int)c->graphs.size()) return ae_fail(c, AE_ERR_ARG, "graph id out of range");
   if (!(yfloor >= 0) || !std::isfinite(yfloor)) return ae_fail(c, AE_ERR_ARG, "floor must be finite and >= 0");
   c->graphs[gid].dev.yfloor = yfloor;
+  return AE_OK;
+}
+
+extern "C" int ae_set_accept_width(ae_ctx *c, int gid, double width) {
+  if (!c) return AE_ERR_ARG;
+  if (gid < 0 || gid >= (int)c->graphs.size()) return ae_fail(c, AE_ERR_ARG, "graph id out of range");
+  if (!(width >= 0) || !std::isfinite(width)) return ae_fail(c, AE_ERR_ARG, "width must be finite and >= 0");
+  // the width is on the graph's contribution mult * y; the kernels test y
+  c->graphs[gid].dev.ywidth = width / c->graphs[gid].g.mult;
+  return AE_OK;
+}
+
+// The trained proposal: FP32 master weights and the network outputs the
+// sampling tables were built from (the last forward pass of training).
+extern "C" int ae_proposal_export(ae_ctx *c, int gid, float *params, float *outputs, double *beta) {
+  if (!c) return AE_ERR_ARG;
+  if (gid < 0 || gid >= (int)c->graphs.size()) return ae_fail(c, AE_ERR_ARG, "graph id out of range");
+  LoadedGraph &lg = c->graphs[gid];
+  if (!lg.learned.mem || lg.learned.master.size() != (size_t)NPARAM)
+    return ae_fail(c, AE_ERR_STATE, "no trained proposal for this graph");
+  if (params) std::memcpy(params, lg.learned.master.data(), NPARAM * sizeof(float));
+  if (outputs) {
+    Net n;
+    carve(n, lg.learned.mem, lg.g.M());
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaMemcpy(outputs, n.O, ((size_t)1 << lg.g.M()) * OUT * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return ae_fail(c, AE_ERR_CUDA, std::string("proposal_export: ") + cudaGetErrorString(e));
+  }
+  if (beta) *beta = lg.learned.beta;
   return AE_OK;
 }
 

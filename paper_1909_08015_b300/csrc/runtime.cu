@@ -52,14 +52,18 @@ static int fail(ae_ctx *c, int code, const std::string &msg) { return ae_fail(c,
 // Process samples [first, first + count) of one graph; CTA b takes a
 // contiguous chunk in rounds of blockDim.x samples (one per thread), each
 // round's tapes run together, staged through shared memory.
+// wait_cycles bounds every wait for a tape segment (kWaitCycles in normal
+// use); skip_first (test hook only) leaves out the copy of the first segment,
+// so that the first wait runs out with nothing in flight.
 __global__ void integrate_kernel(GraphDev Gp, uint64_t first, uint64_t count, uint64_t seed,
                                  double dd_tol, Partial *part, unsigned long long *queue,
-                                 unsigned long long qcap, unsigned long long *qcount, int *err) {
+                                 unsigned long long qcap, unsigned long long *qcount, int *err,
+                                 long long wait_cycles, int skip_first) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ __align__(16) unsigned char Gmem[sizeof(GraphDev)];   // raw: no dynamic initialisation
   GraphDev &G = *reinterpret_cast<GraphDev *>(Gmem);
   __shared__ uint64_t bars[2];
-  Stage st{reinterpret_cast<Ins *>(dsm), bars, 0, 0};
+  Stage st{reinterpret_cast<Ins *>(dsm), bars, 0, 0, wait_cycles};
   if (threadIdx.x == 0) { G = Gp; stage_init(st); }
   __syncthreads();
   double *S = reinterpret_cast<double *>(dsm + kStageBytes) + threadIdx.x * G.nslots;   // this thread's row
@@ -68,7 +72,7 @@ __global__ void integrate_kernel(GraphDev Gp, uint64_t first, uint64_t count, ui
   uint64_t hi = min(count, lo + chunk);
   Partial p = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   double z[14], lz[14];
-  if (threadIdx.x == 0 && lo < hi) stage_issue(st, G, 0);
+  if (threadIdx.x == 0 && lo < hi && !skip_first) stage_issue(st, G, 0);
   for (uint64_t base = lo; base < hi; base += blockDim.x) {
     const uint64_t i = base + threadIdx.x;
     const bool active = i < hi;
@@ -99,24 +103,41 @@ __global__ void integrate_kernel(GraphDev Gp, uint64_t first, uint64_t count, ui
   block_reduce(p, part + blockIdx.x);
 }
 
-// Double-double re-evaluation of queued samples, written to the sample's
-// dense slot (offset from `first`): y and a flag (1 re-evaluated, 2 still
-// failing -> the sample counts as zero).
-__global__ void dd_kernel(GraphDev G, uint64_t seed, const unsigned long long *queue, uint64_t nq,
-                          double dd_tol, uint64_t first, double *ydense, unsigned char *fdense) {
-  extern __shared__ dd dslots[];
-  dd *S = dslots + threadIdx.x * G.nslots;   // this thread's row of the slot file
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    double z[14], lz[14], lg;
-    draw_any(G, queue[i], seed, z, lz, lg);
-    for (int k = 0; k < G.M; ++k) S[k] = {z[k], 0.0};
-    run_tape_dd(G, S);
-    double y, Ey;
-    weight2(S[G.outI].hi + S[G.outI].lo, S[G.outE].hi, lg, y, Ey);
-    const bool bad = dd_rejected(G, y, Ey, dd_tol);
-    ydense[queue[i] - first] = bad ? 0.0 : y;
-    fdense[queue[i] - first] = bad ? 2 : 1;
+// Double-double re-evaluation of one graph's queued samples, written to the
+// sample's dense slot (offset from `first`): y and a flag (1 re-evaluated, 2
+// still failing -> the sample counts as zero).  CTA-synchronous with the
+// tape staged through shared memory: item k = entries k*blockDim ..
+// (k+1)*blockDim-1 of the queue, items taken in grid-stride order.
+__global__ void dd_staged_kernel(GraphDev Gp, uint64_t seed, const unsigned long long *queue, uint64_t nq,
+                                 double dd_tol, uint64_t first, double *ydense, unsigned char *fdense, int *err) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ __align__(16) unsigned char Gmem[sizeof(GraphDev)];   // raw: no dynamic initialisation
+  GraphDev &G = *reinterpret_cast<GraphDev *>(Gmem);
+  __shared__ uint64_t bars[2];
+  Stage st{reinterpret_cast<Ins *>(dsm), bars, 0, 0, kWaitCycles};
+  if (threadIdx.x == 0) { G = Gp; stage_init(st); }
+  __syncthreads();
+  dd *S = reinterpret_cast<dd *>(dsm + kStageBytes) + threadIdx.x * G.nslots;   // this thread's row
+  double z[14], lz[14];
+  const uint64_t items = (nq + blockDim.x - 1) / blockDim.x;
+  for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    if (threadIdx.x == 0) stage_issue(st, G, 0);
+    const uint64_t i = it * blockDim.x + threadIdx.x;
+    const bool active = i < nq;
+    double lg = 0.0;
+    if (active) {
+      draw_any(G, queue[i], seed, z, lz, lg);
+      for (int k = 0; k < G.M; ++k) S[k] = dd{z[k], 0.0};
+    }
+    if (!run_tape_dd_staged(st, G, S, active, err)) return;
+    if (active) {
+      double y, Ey;
+      weight2(S[G.outI].hi + S[G.outI].lo, S[G.outE].hi, lg, y, Ey);
+      const bool bad = dd_rejected(G, y, Ey, dd_tol);
+      ydense[queue[i] - first] = bad ? 0.0 : y;
+      fdense[queue[i] - first] = bad ? 2 : 1;
+    }
+    __syncthreads();   // every thread is done with the last segment's buffer
   }
 }
 
@@ -203,7 +224,7 @@ __global__ void batched_kernel(const GraphDev *graphs, const Chunk *chunks, int 
   __shared__ __align__(16) unsigned char Gmem[sizeof(GraphDev)];   // raw: no dynamic initialisation
   GraphDev &G = *reinterpret_cast<GraphDev *>(Gmem);               // descriptor of the current chunk's graph
   __shared__ uint64_t bars[2];
-  Stage st{reinterpret_cast<Ins *>(dsm), bars, 0, 0};
+  Stage st{reinterpret_cast<Ins *>(dsm), bars, 0, 0, kWaitCycles};
   double z[14], lz[14];
   if (threadIdx.x == 0) { curg = -1; stage_init(st); }
   for (;;) {
@@ -277,31 +298,88 @@ __global__ void queue_scatter_kernel(const unsigned long long *qi, const int *qg
   }
 }
 
-// Double-double re-evaluation of the batched queue (count read on the device,
-// so the launch shape is fixed and the pair can be captured in a graph).
-// The threads of a CTA may work on different graphs: every row has the pitch
-// of the launch (the largest of its bucket), not that of the thread's graph.
-__global__ void batched_dd_kernel(const GraphDev *graphs, uint64_t seed, const unsigned long long *queue_idx,
-                                  const int *queue_gi, const unsigned int *beg, const unsigned int *end,
-                                  const unsigned long long *gpos, double *ydense, unsigned char *fdense,
-                                  int pitch, double dd_tol) {
-  extern __shared__ dd bdsl[];
-  dd *S = bdsl + threadIdx.x * pitch;   // this thread's row of the slot file
-  uint64_t i0 = beg ? *beg : 0, i1 = *end;
-  for (uint64_t i = i0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < i1; i += (uint64_t)gridDim.x * blockDim.x) {
-    const GraphDev &G = graphs[queue_gi[i]];
-    double z[14], lz[14], lg;
-    draw_any(G, queue_idx[i], seed, z, lz, lg);
-    for (int k = 0; k < G.M; ++k) S[k] = {z[k], 0.0};
-    run_tape_dd(G, S);
-    double y, Ey;
-    weight2(S[G.outI].hi + S[G.outI].lo, S[G.outE].hi, lg, y, Ey);
-    const bool bad = dd_rejected(G, y, Ey, dd_tol);
-    // dense slot of the sample: the graph's base in this launch + offset
-    const int gq = queue_gi[i];
-    const unsigned long long pos = gpos[2 * gq] + (queue_idx[i] - gpos[2 * gq + 1]);
-    ydense[pos] = bad ? 0.0 : y;
-    fdense[pos] = bad ? 2 : 1;
+// Work plan of the staged double-double pass over the graph-sorted queue:
+// rank r (a graph, in bucket order) holds entries [end_{r-1}, end_r) and is
+// cut into work items of B_r consecutive entries (B_r = the block size of
+// its bucket's launch); wstart[r] = first item of rank r, wstart[nranks] =
+// the total.  One thread: at most a few thousand ranks.
+__global__ void dd_plan_kernel(const unsigned int *hist_end, const int *rank_bs, int nranks, unsigned int *wstart) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned int acc = 0;
+  for (int r = 0; r < nranks; ++r) {
+    const unsigned int beg = r ? hist_end[r - 1] : 0u, cnt = hist_end[r] - beg;
+    wstart[r] = acc;
+    acc += (cnt + (unsigned int)rank_bs[r] - 1) / (unsigned int)rank_bs[r];
+  }
+  wstart[nranks] = acc;
+}
+
+// Double-double re-evaluation of the batched queue, CTA-synchronous like the
+// FP64 kernel: a CTA takes a work item (blockDim consecutive entries of one
+// graph, ranks r0..r1 of this launch's bucket) through an atomic counter,
+// every thread draws its entry's sample, and all step through the graph's
+// tape together, the segments staged into shared memory by bulk copies.
+// Results go to the samples' dense slots (flag 1 = re-evaluated, 2 = failed
+// again -> counts as zero).  Counts are read on the device, so the launch
+// shape is fixed and the pass can be captured in a graph.
+__global__ void batched_dd_staged_kernel(const GraphDev *graphs, uint64_t seed, const unsigned long long *qi,
+                                         const int *qg, const unsigned int *hist_end, const unsigned int *wstart,
+                                         int r0, int r1, const unsigned long long *gpos, double *ydense,
+                                         unsigned char *fdense, int pitch, double dd_tol, int *next, int *err) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ unsigned int item_s;
+  __shared__ int rank_s;
+  __shared__ __align__(16) unsigned char Gmem[sizeof(GraphDev)];   // raw: no dynamic initialisation
+  GraphDev &G = *reinterpret_cast<GraphDev *>(Gmem);               // descriptor of the current item's graph
+  __shared__ uint64_t bars[2];
+  Stage st{reinterpret_cast<Ins *>(dsm), bars, 0, 0, kWaitCycles};
+  int curr = -1;   // thread 0: the rank whose descriptor is in G
+  if (threadIdx.x == 0) stage_init(st);
+  const unsigned int wbeg = wstart[r0], wend = wstart[r1 + 1];
+  dd *S = reinterpret_cast<dd *>(dsm + kStageBytes) + threadIdx.x * pitch;   // this thread's row
+  double z[14], lz[14];
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned int it = wbeg + (unsigned int)atomicAdd(next, 1);
+      int r = -1;
+      if (it < wend) {
+        // the largest rank r in [r0, r1] with wstart[r] <= it; it has items
+        int lo = r0, hi = r1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (wstart[mid] <= it) lo = mid; else hi = mid - 1;
+        }
+        r = lo;
+        const unsigned int beg = r ? hist_end[r - 1] : 0u;
+        if (r != curr) { G = graphs[qg[beg]]; curr = r; }
+        stage_issue(st, G, 0);
+      }
+      item_s = it;
+      rank_s = r;
+    }
+    __syncthreads();
+    const unsigned int it = item_s;
+    if (it >= wend) break;
+    const int r = rank_s;
+    const unsigned int beg = r ? hist_end[r - 1] : 0u, end = hist_end[r];
+    const unsigned long long i = (unsigned long long)beg + (unsigned long long)(it - wstart[r]) * blockDim.x + threadIdx.x;
+    const bool active = i < end;
+    double lg = 0.0;
+    if (active) {
+      draw_any(G, qi[i], seed, z, lz, lg);
+      for (int k = 0; k < G.M; ++k) S[k] = dd{z[k], 0.0};
+    }
+    if (!run_tape_dd_staged(st, G, S, active, err)) return;
+    if (active) {
+      double y, Ey;
+      weight2(S[G.outI].hi + S[G.outI].lo, S[G.outE].hi, lg, y, Ey);
+      const bool bad = dd_rejected(G, y, Ey, dd_tol);
+      const int gq = qg[i];
+      const unsigned long long pos = gpos[2 * gq] + (qi[i] - gpos[2 * gq + 1]);
+      ydense[pos] = bad ? 0.0 : y;
+      fdense[pos] = bad ? 2 : 1;
+    }
+    __syncthreads();   // the item's shared state is rewritten next
   }
 }
 
@@ -439,6 +517,7 @@ extern "C" void ae_default_opts(ae_opts *o) {
   o->ctas_per_sm = 0;
   o->stream = nullptr;
   o->rng = 0;
+  o->grid_ctas = 0;
 }
 
 extern "C" void ae_calc1_opts(ae_opts *o) {
@@ -453,7 +532,7 @@ extern "C" int ae_create(ae_ctx **out, int dev, const ae_opts *opts) {
   ae_ctx *c = new (std::nothrow) ae_ctx();
   if (!c) return AE_ERR_OOM;
   if (opts) c->opts = *opts; else ae_default_opts(&c->opts);
-  if (c->opts.rng != 0 && c->opts.rng != 1) { delete c; return AE_ERR_ARG; }
+  if ((c->opts.rng != 0 && c->opts.rng != 1) || c->opts.grid_ctas < 0) { delete c; return AE_ERR_ARG; }
   c->device = dev;
   if (dev >= 0) {
     cudaError_t e = cudaSetDevice(dev);
@@ -490,6 +569,9 @@ static void free_device(ae_ctx *c) {
   for (auto &lg : c->graphs)
     if (lg.learned.mem) { cudaFree(lg.learned.mem); lg.learned.mem = nullptr; lg.dev.lP = nullptr; }
   c->tune_cache.clear();
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->gkey.clear();
   c->arena = nullptr; c->d_part = nullptr; c->d_queue = nullptr; c->d_qcount = nullptr;
   c->d_yq = nullptr; c->d_qstat = nullptr; c->part_cap = c->queue_cap = 0;
 }
@@ -498,6 +580,8 @@ extern "C" void ae_destroy(ae_ctx *c) {
   if (!c) return;
   free_device(c);
   if (c->d_mrg) cudaFree(c->d_mrg);
+  for (auto &ev : c->gev)
+    if (ev) cudaEventDestroy(ev);
   if (c->stream && c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -564,6 +648,8 @@ static int load_impl(ae_ctx *c, int loops, const int *subset, int n_subset, int 
     free_device(c);
     c->graphs.swap(L);
     c->loops = loops;
+    c->run.assign(c->graphs.size(), ae_run_graph{});
+    c->run_seed = 0;
   } catch (std::exception &e) {
     return fail(c, AE_ERR_STATE, std::string("load_graphs: ") + e.what());
   }
@@ -700,10 +786,25 @@ static void host_dd_add(double &hi, double &lo, double x) {
   hi = r;
 }
 
+// Mean, sigma_down (Eq. eq_sigma_down) and the heuristic sigma_up of a
+// result from its sums: sigma_up^2 = sigma_down^2 + max y^2 / N^2.  A graph
+// with no samples gets value 0 and sigma 0.
+void ae_result_finish(ae_graph_result *r, int mult, double sum_abs) {
+  const double N = (double)r->n;
+  r->mean = r->n ? r->sum_y / N : 0.0;
+  const double var = r->n ? r->sum_y2 / (N * N) - r->sum_y * r->sum_y / (N * N * N) : 0.0;
+  r->sigma1 = var > 0 ? std::sqrt(var) : 0.0;
+  r->mean_abs = r->n ? sum_abs / N : 0.0;
+  r->value = mult * r->mean;
+  r->sigma = mult * r->sigma1;
+  const double up = r->n ? r->sigma1 * r->sigma1 + r->max_y2 / (N * N) : 0.0;
+  r->sigma_up = mult * std::sqrt(up);
+}
+
 // Integrate one graph in slices of at most 2^28 samples (bounds the
 // double-double queue); sums are combined in slice order, so the result is
 // independent of the schedule.
-static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_graph_result *res) {
+static int integrate_one(ae_ctx *c, int gid, uint64_t first, uint64_t nsamp, uint64_t seed, ae_graph_result *res) {
   LoadedGraph &lg = c->graphs[gid];
   GraphDev &G = lg.dev;
   int bs = pick_block_for(c, (const void *)integrate_kernel, G.nslots, 8, kStageBytes);
@@ -722,6 +823,7 @@ static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_g
   for (uint64_t start = 0; start < nsamp; start += SLICE) {
     uint64_t len = std::min(SLICE, nsamp - start);
     uint64_t grid = (uint64_t)c->sm_count * per_sm;
+    if (c->opts.grid_ctas > 0) grid = std::min<uint64_t>(grid, (uint64_t)c->opts.grid_ctas);
     if (grid * bs > len) grid = std::max<uint64_t>(1, (len + bs - 1) / bs);
     size_t qcap = (size_t)std::max<uint64_t>(len, 65536);   // every sample may need re-evaluation
     const uint64_t SEG = 1ull << 14;
@@ -737,9 +839,9 @@ static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_g
     cudaEvent_t e0, e1, ek;
     cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&ek);
     cudaEventRecord(e0, c->stream);
-    integrate_kernel<<<(unsigned)grid, bs, smem, c->stream>>>(G, start, len, seed, c->opts.dd_tol, c->d_part,
+    integrate_kernel<<<(unsigned)grid, bs, smem, c->stream>>>(G, first + start, len, seed, c->opts.dd_tol, c->d_part,
                                                               c->d_queue, c->queue_cap, c->d_qcount,
-                                                              (int *)(c->d_qcount + 1));
+                                                              (int *)(c->d_qcount + 1), kWaitCycles, 0);
     CUDA_TRY(c, cudaGetLastError());
     cudaEventRecord(ek, c->stream);
     ++launches;
@@ -756,12 +858,15 @@ static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_g
       return fail(c, AE_ERR_STATE, "double-double queue overflow");
     }
     if (nq) {
-      int bsd = pick_block_for(c, (const void *)dd_kernel, G.nslots, 16);
+      int bsd = pick_block_for(c, (const void *)dd_staged_kernel, G.nslots, 16, kStageBytes);
       if (bsd < 0) return fail(c, AE_ERR_STATE, "double-double slot file does not fit in shared memory");
-      size_t sm2 = (size_t)bsd * G.nslots * 16;
-      CUDA_TRY(c, cudaFuncSetAttribute(dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-      unsigned g2 = (unsigned)std::min<uint64_t>((nq + bsd - 1) / bsd, (uint64_t)c->sm_count * 8);
-      dd_kernel<<<g2, bsd, sm2, c->stream>>>(G, seed, c->d_queue, nq, c->opts.dd_tol, start, ydense, fdense);
+      size_t sm2 = kStageBytes + (size_t)bsd * G.nslots * 16;
+      CUDA_TRY(c, cudaFuncSetAttribute(dd_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+      int pm = 0;
+      CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pm, dd_staged_kernel, bsd, sm2));
+      unsigned g2 = (unsigned)std::min<uint64_t>((nq + bsd - 1) / bsd, (uint64_t)c->sm_count * std::max(pm, 1));
+      dd_staged_kernel<<<g2, bsd, sm2, c->stream>>>(G, seed, c->d_queue, nq, c->opts.dd_tol, first + start, ydense,
+                                                   fdense, (int *)(c->d_qcount + 1));
       CUDA_TRY(c, cudaGetLastError());
       dense_dd_reduce_kernel<<<(unsigned)std::min<uint64_t>((nseg + 7) / 8, (uint64_t)c->sm_count * 16), 256, 0,
                                c->stream>>>(len, SEG, ydense, fdense, c->d_part + grid);
@@ -772,7 +877,12 @@ static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_g
     const size_t np = nq ? grid + nseg : grid;
     std::vector<Partial> parts(np);
     CUDA_TRY(c, cudaMemcpyAsync(parts.data(), c->d_part, np * sizeof(Partial), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(hq, c->d_qcount, sizeof(hq), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (hq[1]) {
+      cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(ek);
+      return fail(c, AE_ERR_TIMEOUT, "integrate: a tape-staging wait ran out (double-double pass)");
+    }
     float ms = 0, mk = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventElapsedTime(&mk, e0, ek);
@@ -794,14 +904,8 @@ static int integrate_one(ae_ctx *c, int gid, uint64_t nsamp, uint64_t seed, ae_g
   }
   res->sum_y = sy + syl; res->sum_y2 = sy2 + sy2l;
   res->n = n; res->n_dd = ndd; res->n_nonfinite = nbad;
-  double N = (double)n;
-  res->mean = res->sum_y / N;
-  double var = res->sum_y2 / (N * N) - res->sum_y * res->sum_y / (N * N * N);
-  res->sigma1 = var > 0 ? std::sqrt(var) : 0.0;
-  res->mean_abs = (sa + sal) / N;
   res->max_y2 = mx;
-  res->value = lg.g.mult * res->mean;
-  res->sigma = lg.g.mult * res->sigma1;
+  ae_result_finish(res, lg.g.mult, sa + sal);
   res->seconds = secs;
   res->launches = launches;
   res->kernel_seconds = ksecs;
@@ -815,22 +919,20 @@ static int run_batched(ae_ctx *c, const std::vector<int> &ids, const std::vector
 
 // Samples [first, first + count) of one graph (resume / sharding by counter
 // range): the same Philox stream as ae_integrate, so ranges concatenate.
+// One launch of the per-graph kernel, which starts at `first`.
 extern "C" int ae_integrate_range(ae_ctx *c, int gid, uint64_t first, uint64_t count, uint64_t seed,
                                   ae_graph_result *out) {
   if (!c || !out) return AE_ERR_ARG;
   if (c->device < 0) return fail(c, AE_ERR_NODEV, "integration needs a CUDA device");
   if (gid < 0 || gid >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
   if (count == 0) return fail(c, AE_ERR_ARG, "zero samples");
+  if (first + count < first) return fail(c, AE_ERR_ARG, "sample index overflows 2^64");
   CUDA_TRY(c, cudaSetDevice(c->device));
-  std::vector<int> ids = {gid};
-  std::vector<uint64_t> ns = {count}, fs = {first};
-  std::vector<ae_graph_result> res;
-  double secs = 0;
-  int bs = pick_block_for(c, (const void *)batched_kernel, c->graphs[gid].dev.nslots, 8, kStageBytes);
-  if (bs < 0) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
-  int rc = run_batched(c, ids, ns, fs, seed, bs, 16384, false, res, &secs);
+  ae_graph_result r;
+  std::memset(&r, 0, sizeof(r));
+  int rc = integrate_one(c, gid, first, count, seed, &r);
   if (rc) return rc;
-  *out = res[0];
+  *out = r;
   return AE_OK;
 }
 
@@ -847,7 +949,7 @@ extern "C" int ae_integrate(ae_ctx *c, const int *ids, int n_ids, uint64_t nsamp
   for (int i = 0; i < n_ids; ++i) {
     ae_graph_result r;
     std::memset(&r, 0, sizeof(r));
-    int rc = integrate_one(c, ids[i], nsamp, seed, &r);
+    int rc = integrate_one(c, ids[i], 0, nsamp, seed, &r);
     if (rc) return rc;
     v += r.value;
     s2 += r.sigma * r.sigma;
@@ -923,6 +1025,7 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pm, batched_kernel, L.bs, L.smem));
     if (pm < 1) pm = 1;
     L.grid = (unsigned)(c->sm_count * pm);
+    if (c->opts.grid_ctas > 0) L.grid = std::min<unsigned>(L.grid, (unsigned)c->opts.grid_ctas);
     uint64_t res_b = (uint64_t)L.grid;
     for (size_t t = k; t < k1; ++t) {
       int oi = order[t];
@@ -945,7 +1048,7 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   // context and grown when a larger batch arrives
   // dense double-double results: one y and one flag byte per sample of the batch
   size_t need = ids.size() * sizeof(GraphDev) + nch * sizeof(Chunk) + 2 * nch * sizeof(Partial) +
-                qcap * (8 + 4 + 8 + 4) + ids.size() * (8 + 16) + total * 9 + 64 * 4 + 8 * 1024;
+                qcap * (8 + 4 + 8 + 4) + ids.size() * (8 + 16 + 8) + total * 9 + 64 * 4 + 12 * 1024;
   if (need > c->bbuf_bytes) {
     if (c->bbuf) cudaFree(c->bbuf);
     c->bbuf = nullptr;
@@ -969,8 +1072,10 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
   int *qg2 = (int *)p; p += al(qcap * 4);
   unsigned int *hist = (unsigned int *)p; p += al(ids.size() * 4);
   int *drank = (int *)p; p += al(ids.size() * 4);
+  unsigned int *wstart = (unsigned int *)p; p += al((ids.size() + 1) * 4);
+  int *rank_bs = (int *)p; p += al(ids.size() * 4);
   unsigned long long *qcount = (unsigned long long *)p; p += 256;
-  int *next = (int *)(qcount + 1);   // one counter per launch (up to 32)
+  int *next = (int *)(qcount + 1);   // one counter per launch (up to 16), then one per dd launch
   int *derr = (int *)((char *)qcount + 192);   // wait-timeout flag
   std::vector<GraphDev> hg;
   for (int g : ids) hg.push_back(c->graphs[g].dev);
@@ -998,26 +1103,40 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     for (size_t i = 0; i < ids.size(); ++i) { hgpos[2 * i] = base; hgpos[2 * i + 1] = firsts[i]; base += ns[i]; }
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(gpos, hgpos.data(), hgpos.size() * 8, cudaMemcpyHostToDevice, c->stream);
-  // one double-double launch per bucket, shaped for that bucket's slots
-  std::vector<int> dd_bs(launches.size()), dd_pitch(launches.size());
+  // one staged double-double launch per bucket, shaped for that bucket's
+  // slots (16-byte rows), persistent (SMs x resident CTAs)
+  std::vector<int> dd_bs(launches.size()), dd_pitch(launches.size()), dd_r0(launches.size());
+  std::vector<unsigned> dd_grid(launches.size());
   std::vector<size_t> dd_sm(launches.size());
+  std::vector<int> hrank_bs(ids.size());
   size_t ddmax = 0;
   {
     size_t r = 0;
     for (size_t l = 0; l < launches.size(); ++l) {
       int bslots = 0;
+      const size_t rb = r;
       int b = bucket_of(order[r]);
       while (r < order.size() && bucket_of(order[r]) == b) { bslots = std::max(bslots, c->graphs[ids[order[r]]].dev.nslots); ++r; }
-      int b16 = pick_block_for(c, (const void *)batched_dd_kernel, bslots, 16);
-      if (b16 < 0) b16 = 32;
+      int b16 = pick_block_for(c, (const void *)batched_dd_staged_kernel, bslots, 16, kStageBytes);
+      if (b16 < 0) return fail(c, AE_ERR_STATE, "double-double slot file does not fit in shared memory");
       dd_bs[l] = b16;
       dd_pitch[l] = bslots;
-      dd_sm[l] = (size_t)b16 * bslots * 16;
+      dd_r0[l] = (int)rb;
+      dd_sm[l] = kStageBytes + (size_t)b16 * bslots * 16;
+      for (size_t q = rb; q < r; ++q) hrank_bs[q] = b16;
+      int pm = 0;
+      CUDA_TRY(c, cudaFuncSetAttribute(batched_dd_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dd_sm[l]));
+      CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pm, batched_dd_staged_kernel, b16, dd_sm[l]));
+      dd_grid[l] = (unsigned)(c->sm_count * std::max(pm, 1));
       ddmax = std::max(ddmax, dd_sm[l]);
     }
   }
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ddmax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_dd_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ddmax);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rank_bs, hrank_bs.data(), hrank_bs.size() * 4, cudaMemcpyHostToDevice, c->stream);
   unsigned grid2 = (unsigned)(c->sm_count * 4);
+  if (use_graph)
+    for (auto &ev : c->gev)
+      if (!ev && e == cudaSuccess) e = cudaEventCreate(&ev);
   cudaEvent_t e0 = nullptr, e1 = nullptr, ek = nullptr;
   // events recorded with cudaEventRecordExternal so that, inside a captured
   // graph, they become event-record nodes readable after the launch
@@ -1039,31 +1158,49 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     queue_hist_kernel<<<grid2, 256, 0, c->stream>>>(qg, qcount, qcap, drank, hist);
     queue_scan_kernel<<<1, 32, 0, c->stream>>>(hist, (int)ids.size());
     queue_scatter_kernel<<<grid2, 256, 0, c->stream>>>(qi, qg, qcount, qcap, drank, hist, qi2, qg2);
-    // after the scatter hist[r] is the end of bin r: bucket l spans
-    // [hist[last of l-1], hist[last of l])
-    for (size_t l = 0; l < launches.size(); ++l) {
-      const unsigned int *bg = l == 0 ? nullptr : hist + bucket_last[l - 1];
-      batched_dd_kernel<<<grid2, dd_bs[l], dd_sm[l], c->stream>>>(dG, seed, qi2, qg2, bg, hist + bucket_last[l], gpos,
-                                                                  ydense, fdense, dd_pitch[l], c->opts.dd_tol);
-    }
+    // after the scatter hist[r] is the end of bin r; the plan cuts every
+    // rank into items of its bucket's block size
+    dd_plan_kernel<<<1, 32, 0, c->stream>>>(hist, rank_bs, (int)ids.size(), wstart);
+    for (size_t l = 0; l < launches.size(); ++l)
+      batched_dd_staged_kernel<<<dd_grid[l], dd_bs[l], dd_sm[l], c->stream>>>(
+          dG, seed, qi2, qg2, hist, wstart, dd_r0[l], bucket_last[l], gpos, ydense, fdense, dd_pitch[l],
+          c->opts.dd_tol, next + 16 + l, derr);
     chunk_dd_reduce_kernel<<<(unsigned)std::min<size_t>((nch + 7) / 8, (size_t)c->sm_count * 16), 256, 0,
                              c->stream>>>(dC, (int)nch, gpos, ydense, fdense, dP2);
     rec(e1);
   };
   cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
   if (e == cudaSuccess) {
-    cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&ek);
     if (use_graph) {
-      // the two launches and their timing events form one CUDA graph
-      e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-      if (e == cudaSuccess) {
-        enqueue();
-        e = cudaStreamEndCapture(c->stream, &graph);
+      // the launches and their timing events form one CUDA graph; it is kept
+      // and launched again while the launch shape, the buffers and the scalar
+      // arguments stay the same (the chunk list and graph descriptors are
+      // copied to the device before every launch)
+      e0 = c->gev[0]; e1 = c->gev[1]; ek = c->gev[2];
+      std::string key = std::to_string((uintptr_t)buf) + "/" + std::to_string(seed) + "/" +
+                        std::to_string(c->opts.dd_tol) + "/" + std::to_string(nch) + "/" + std::to_string(total) +
+                        "/" + std::to_string(qcap) + "/" + std::to_string(ids.size()) + "/" + std::to_string(grid2);
+      for (size_t l = 0; l < launches.size(); ++l)
+        key += "|" + std::to_string(launches[l].grid) + "," + std::to_string(launches[l].bs) + "," +
+               std::to_string(launches[l].smem) + "," + std::to_string(launches[l].c0) + "," +
+               std::to_string(launches[l].c1) + "," + std::to_string(dd_bs[l]) + "," + std::to_string(dd_sm[l]) +
+               "," + std::to_string(dd_pitch[l]) + "," + std::to_string(bucket_last[l]) + "," +
+               std::to_string(dd_grid[l]);
+      if (!(c->gexec && key == c->gkey)) {
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+        c->gkey.clear();
+        e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          enqueue();
+          e = cudaStreamEndCapture(c->stream, &graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, graph, 0);
+        if (e == cudaSuccess) c->gkey = key;
       }
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-      if (e == cudaSuccess) e = cudaGraphLaunch(exec, c->stream);
+      if (e == cudaSuccess) e = cudaGraphLaunch(c->gexec, c->stream);
     } else {
+      cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&ek);
       enqueue();
       e = cudaGetLastError();
     }
@@ -1082,12 +1219,16 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     if (t1 != cudaSuccess || t2 != cudaSuccess) e = t1 != cudaSuccess ? t1 : t2;
   }
   nq = std::min<unsigned long long>(nq, qcap);
-  if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
-  if (ek) cudaEventDestroy(ek);
-  if (e != cudaSuccess) return fail(c, AE_ERR_CUDA, std::string("batched: ") + cudaGetErrorString(e));
+  if (!use_graph) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ek) cudaEventDestroy(ek);
+  }
+  if (e != cudaSuccess) {
+    if (use_graph && c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; c->gkey.clear(); }
+    return fail(c, AE_ERR_CUDA, std::string("batched: ") + cudaGetErrorString(e));
+  }
   if (herr) return fail(c, AE_ERR_TIMEOUT, "batched: a tape-staging wait ran out");
   for (auto &pp : parts)
     if (pp.n_overflow) return fail(c, AE_ERR_STATE, "double-double queue overflow");
@@ -1118,19 +1259,12 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
     std::memset(&r, 0, sizeof(r));
     r.sum_y = sy[gi] + syl[gi]; r.sum_y2 = sy2[gi] + sy2l[gi];
     r.n = n[gi]; r.n_dd = ndd[gi]; r.n_nonfinite = nbad[gi];
-    double N = (double)r.n;
-    // a graph given no samples contributes value 0 and sigma 0
-    r.mean = r.n ? r.sum_y / N : 0.0;
-    double var = r.n ? r.sum_y2 / (N * N) - r.sum_y * r.sum_y / (N * N * N) : 0.0;
-    r.sigma1 = var > 0 ? std::sqrt(var) : 0.0;
-    r.mean_abs = r.n ? (sa[gi] + sal[gi]) / N : 0.0;
     r.max_y2 = mx[gi];
-    int mult = c->graphs[ids[gi]].g.mult;
-    r.value = mult * r.mean;
-    r.sigma = mult * r.sigma1;
+    // a graph given no samples contributes value 0 and sigma 0
+    ae_result_finish(&r, c->graphs[ids[gi]].g.mult, sa[gi] + sal[gi]);
     r.seconds = ms * 1e-3 * (double)ns[gi] / (double)total;   // share of the launch by samples
     r.kernel_seconds = mk * 1e-3 * (double)ns[gi] / (double)total;
-    r.launches = gi == 0 ? (uint64_t)(2 * launches.size() + 4) : 0;
+    r.launches = gi == 0 ? (uint64_t)(2 * launches.size() + 5) : 0;
     r.d2h_bytes = gi == 0 ? (8 + 4 + 2 * nch * sizeof(Partial)) : 0;
     r.h2d_bytes = gi == 0 ? (ids.size() * (sizeof(GraphDev) + 4 + 16) + nch * sizeof(Chunk)) : 0;
   }
@@ -1220,6 +1354,46 @@ extern "C" int ae_integrate_batched(ae_ctx *c, const int *ids, int n_ids, const 
   return AE_OK;
 }
 
+// One block of a run: every listed graph continues its own stream from the
+// run's next index, all in one batched launch; the sums go into the run.
+extern "C" int ae_run_step(ae_ctx *c, const int *ids, int n_ids, const uint64_t *ns, ae_graph_result *per) {
+  if (!c) return AE_ERR_ARG;
+  if (c->device < 0) return fail(c, AE_ERR_NODEV, "integration needs a CUDA device");
+  if (c->graphs.empty()) return fail(c, AE_ERR_STATE, "no graphs loaded");
+  if (!ids || !ns || n_ids <= 0) return fail(c, AE_ERR_ARG, "empty graph list");
+  std::vector<int> vid(ids, ids + n_ids);
+  std::vector<uint64_t> vn(ns, ns + n_ids), vf(n_ids);
+  std::vector<char> seen(c->graphs.size(), 0);
+  uint64_t total = 0;
+  for (int i = 0; i < n_ids; ++i) {
+    if (ids[i] < 0 || ids[i] >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
+    if (seen[ids[i]]) return fail(c, AE_ERR_ARG, "a graph listed twice in one run step");
+    seen[ids[i]] = 1;
+    vf[i] = c->run[ids[i]].next;
+    if (vf[i] + ns[i] < vf[i]) return fail(c, AE_ERR_ARG, "sample index overflows 2^64");
+    total += ns[i];
+  }
+  if (total == 0) return fail(c, AE_ERR_ARG, "no samples requested");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  BatchTune t;
+  if (c->opts.block_size > 0) { t.block = c->opts.block_size; t.chunk = 16384; }
+  else {
+    int rc = autotune_batched(c, vid, t);
+    if (rc) return rc;
+  }
+  std::vector<ae_graph_result> res;
+  double secs = 0;
+  int rc = run_batched(c, vid, vn, vf, c->run_seed, t.block, t.chunk, true, res, &secs);
+  if (rc) return rc;
+  for (int i = 0; i < n_ids; ++i) {
+    ae_run_fold(c, ids[i], res[i], ns[i]);
+    if (per) per[i] = res[i];
+  }
+  c->last_tune_block = t.block;
+  c->last_tune_chunk = t.chunk;
+  return AE_OK;
+}
+
 // Inter-graph allocation (Sec. IV.C): a pilot of n_pilot samples per graph
 // (seed ^ 0x9E3779B97F4A7C15, independent of the main run's stream) gives
 // sigma_j; with C_j = sigma_j sqrt(N_pilot) and t_j the cost of one sample
@@ -1268,9 +1442,10 @@ extern "C" int ae_integrate_adaptive(ae_ctx *c, const int *ids, int n_ids, uint6
     if (r == 0) {
       for (size_t i = 0; i < G; ++i) nb[i] = 1;
     } else {
+      // C_j = sigma_up_j sqrt(N_j) (Sec. IV.C)
       for (size_t i = 0; i < G; ++i) {
         double N = (double)Nj[i], var = (sy2[i] + sy2l[i]) / (N * N) - (sy[i] + syl[i]) * (sy[i] + syl[i]) / (N * N * N);
-        sig[i] = c->graphs[vid[i]].g.mult * std::sqrt(std::max(var, 0.0));
+        sig[i] = c->graphs[vid[i]].g.mult * std::sqrt(std::max(var, 0.0) + mx[i] / (N * N));
       }
       ae_schedule_probabilities(sig.data(), Nj.data(), tj.data(), n_ids, p_floor, p.data());
       std::vector<double> cdf(G);
@@ -1313,15 +1488,8 @@ extern "C" int ae_integrate_adaptive(ae_ctx *c, const int *ids, int n_ids, uint6
     std::memset(&r, 0, sizeof(r));
     r.sum_y = sy[i] + syl[i]; r.sum_y2 = sy2[i] + sy2l[i];
     r.n = Nj[i]; r.n_dd = ndd[i]; r.n_nonfinite = nbad[i];
-    double N = (double)r.n;
-    r.mean = r.sum_y / N;
-    double v1 = r.sum_y2 / (N * N) - r.sum_y * r.sum_y / (N * N * N);
-    r.sigma1 = v1 > 0 ? std::sqrt(v1) : 0.0;
-    r.mean_abs = (sa[i] + sal[i]) / N;
     r.max_y2 = mx[i];
-    int mult = c->graphs[vid[i]].g.mult;
-    r.value = mult * r.mean;
-    r.sigma = mult * r.sigma1;
+    ae_result_finish(&r, c->graphs[vid[i]].g.mult, sa[i] + sal[i]);
     r.seconds = secs[i]; r.kernel_seconds = ksecs[i]; r.launches = launches[i];
     r.d2h_bytes = d2h[i]; r.h2d_bytes = h2d[i];
     tot += r.value;
@@ -1455,7 +1623,7 @@ extern "C" int ae_integrate_noalloc(ae_ctx *c, int gid, uint64_t nsamp, uint64_t
   CUDA_TRY(c, cudaMemsetAsync(qcount, 0, 2 * sizeof(unsigned long long), c->stream));
   CUDA_TRY(c, cudaMemsetAsync(flag, 0, nsamp, c->stream));
   integrate_kernel<<<(unsigned)grid, bs, smem, c->stream>>>(G, 0, nsamp, seed, c->opts.dd_tol, part, queue,
-                                                            kNaMaxSamples, qcount, werr);
+                                                            kNaMaxSamples, qcount, werr, kWaitCycles, 0);
   CUDA_TRY(c, cudaGetLastError());
   int bsd = pick_block_for(c, (const void *)dd_dense_kernel, G.nslots, 16);
   if (bsd < 0) return fail(c, AE_ERR_STATE, "double-double slot file does not fit in shared memory");
@@ -1478,15 +1646,8 @@ extern "C" int ae_integrate_noalloc(ae_ctx *c, int gid, uint64_t nsamp, uint64_t
   out->n = r.n;
   out->n_dd = r.n_flag;
   out->n_nonfinite = r.n_overflow;
-  double N = (double)r.n;
-  out->mean = out->sum_y / N;
-  double var = out->sum_y2 / (N * N) - out->sum_y * out->sum_y / (N * N * N);
-  out->sigma1 = var > 0 ? std::sqrt(var) : 0.0;
-  out->mean_abs = (r.sa_hi + r.sa_lo) / N;
   out->max_y2 = r.max_y2;
-  int mult = c->graphs[gid].g.mult;
-  out->value = mult * out->mean;
-  out->sigma = mult * out->sigma1;
+  ae_result_finish(out, c->graphs[gid].g.mult, r.sa_hi + r.sa_lo);
   out->launches = 3;
   return AE_OK;
 }
@@ -1607,6 +1768,33 @@ extern "C" int ae_terms(ae_ctx *c, int gid, int *buf, int cap, int *len) {
   if (buf && cap >= (int)v.size()) std::copy(v.begin(), v.end(), buf);
   else if (buf) return fail(c, AE_ERR_ARG, "buffer too small");
   return AE_OK;
+}
+
+// Test hook: the FP64 integration kernel with its first tape copy left out
+// and a short bound on the wait for it; the wait runs out with nothing in
+// flight and the call fails the way a real timeout does.
+extern "C" int aetest_stage_timeout(ae_ctx *c, int gid, long long wait_cycles) {
+  if (!c) return AE_ERR_ARG;
+  if (c->device < 0) return fail(c, AE_ERR_NODEV, "needs a CUDA device");
+  if (gid < 0 || gid >= (int)c->graphs.size()) return fail(c, AE_ERR_ARG, "graph id out of range");
+  if (wait_cycles < 1 || wait_cycles > kWaitCycles) return fail(c, AE_ERR_ARG, "wait_cycles must be 1..4e9");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  GraphDev &G = c->graphs[gid].dev;
+  const int bs = 32;
+  const size_t smem = kStageBytes + (size_t)bs * G.nslots * 8;
+  if (smem > 224 * 1024) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
+  int rc = ensure_scratch(c, 1, 65536);
+  if (rc) return rc;
+  CUDA_TRY(c, cudaFuncSetAttribute(integrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_qcount, 0, 2 * sizeof(unsigned long long), c->stream));
+  integrate_kernel<<<1, bs, smem, c->stream>>>(G, 0, bs, 0, c->opts.dd_tol, c->d_part, c->d_queue, c->queue_cap,
+                                               c->d_qcount, (int *)(c->d_qcount + 1), wait_cycles, 1);
+  CUDA_TRY(c, cudaGetLastError());
+  unsigned long long hq[2] = {0, 0};
+  CUDA_TRY(c, cudaMemcpyAsync(hq, c->d_qcount, sizeof(hq), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (hq[1]) return fail(c, AE_ERR_TIMEOUT, "integrate: a tape-staging wait ran out");
+  return fail(c, AE_ERR_STATE, "the wait did not run out");
 }
 
 // Test hook: the learned sampler's fused-multiply-add exp2/log2 next to the

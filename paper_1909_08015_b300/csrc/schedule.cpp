@@ -62,3 +62,17 @@ extern "C" int ae_combine_runs(const double *v1, const double *s1, const double 
   if (total_sigma) *total_sigma = std::sqrt(var);
   return AE_OK;
 }
+
+// Widths of the paper's acceptance test (Sec. IV.A, Eq. eq_interval_accept):
+// width_j = (1/4) sigma_j sqrt(sum_l sigma_l^2) / sum_l sigma_l.  Summed
+// over the graphs the widths give (1/4) sqrt(sum_l sigma_l^2): the round-off
+// error of the set stays below a quarter of its sigma_down.
+extern "C" int ae_accept_widths(const double *sigma, int n, double *width) {
+  if (!sigma || !width || n <= 0) return AE_ERR_ARG;
+  double s1 = 0, s2 = 0;
+  for (int j = 0; j < n; ++j)
+    if (std::isfinite(sigma[j]) && sigma[j] > 0) { s1 += sigma[j]; s2 += sigma[j] * sigma[j]; }
+  for (int j = 0; j < n; ++j)
+    width[j] = (s1 > 0 && std::isfinite(sigma[j]) && sigma[j] > 0) ? 0.25 * sigma[j] * std::sqrt(s2) / s1 : 0.0;
+  return AE_OK;
+}

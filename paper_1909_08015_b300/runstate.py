@@ -1,20 +1,17 @@
-"""Run state of an integration: checkpoint/resume and multi-rank merging.
+"""Run state of an integration campaign: a thin wrapper over libae's run
+calls (ae_run_*, ae_checkpoint, ae_resume).
 
-The per-graph state is (N, sum y, sum y^2, sum |y|, re-evaluated, zeroed) plus
-the next Philox sample index.  Because the generator is counter-based,
-continuing from the stored index draws exactly the samples an uninterrupted
-run would have drawn.  Checkpoints are JSON with a SHA-256 of their payload,
-so a corrupt or truncated file is refused rather than silently merged.
-
-Under torch.distributed each rank integrates its own stream (seed offset by
-rank) and the per-graph sums are added once at the end: no collective on the
-data path.  Host logic only; the integration itself runs in libae.
+libae keeps, per loaded graph, the next sample index of its counter-based
+stream and the running sums; it computes the estimate, writes and reads
+checksummed checkpoints and merges runs.  This module only moves bytes:
+under torch.distributed every rank integrates its own stream (seed offset by
+rank, no collective on the data path) and merge_ranks() gathers the ranks'
+raw run states once, each rank then adding the others' sums in rank order
+through ae_run_merge.
 """
-import hashlib
-import json
-import math
+import ctypes
 
-FIELDS = ("n", "sum_y", "sum_y2", "mean_abs_sum", "n_dd", "n_nonfinite")
+from . import AeRunGraph
 
 
 def rank_seed(seed, rank):
@@ -23,79 +20,62 @@ def rank_seed(seed, rank):
 
 
 class RunState:
-    def __init__(self, graph_ids, mults, seed):
-        self.graph_ids = list(graph_ids)
-        self.mults = list(mults)
-        self.seed = int(seed)
-        self.next = [0] * len(self.graph_ids)
-        self.sums = [{f: 0.0 for f in FIELDS} for _ in self.graph_ids]
+    """A run over all graphs loaded in `ctx` (a paper_1909_08015_b300.Context)."""
 
-    def add(self, k, res, count):
-        """Fold one integration result of graph slot k covering `count` samples."""
-        s = self.sums[k]
-        s["n"] += res["n"]
-        s["sum_y"] += res["sum_y"]
-        s["sum_y2"] += res["sum_y2"]
-        s["mean_abs_sum"] += res["mean_abs"] * res["n"]
-        s["n_dd"] += res["n_dd"]
-        s["n_nonfinite"] += res["n_nonfinite"]
-        self.next[k] += int(count)
-
-    def estimate(self):
-        val = var = 0.0
-        for m, s in zip(self.mults, self.sums):
-            N = s["n"]
-            if N == 0:
-                continue
-            v1 = s["sum_y2"] / N ** 2 - s["sum_y"] ** 2 / N ** 3
-            val += m * s["sum_y"] / N
-            var += m * m * max(v1, 0.0)
-        return val, math.sqrt(var)
-
-    # -------------------------------------------------------- checkpoints --
-    def to_json(self):
-        payload = {"graph_ids": self.graph_ids, "mults": self.mults, "seed": self.seed,
-                   "next": self.next, "sums": self.sums}
-        body = json.dumps(payload, sort_keys=True)
-        return json.dumps({"sha256": hashlib.sha256(body.encode()).hexdigest(), "payload": payload},
-                          sort_keys=True)
-
-    def save(self, path):
-        with open(path, "w") as f:
-            f.write(self.to_json())
+    def __init__(self, ctx, seed):
+        self.ctx = ctx
+        ctx.run_reset(seed)
 
     @classmethod
-    def from_json(cls, text):
-        try:
-            obj = json.loads(text)
-            payload = obj["payload"]
-            want = obj["sha256"]
-        except (ValueError, KeyError, TypeError) as e:
-            raise ValueError("checkpoint unreadable: %s" % e)
-        body = json.dumps(payload, sort_keys=True)
-        if hashlib.sha256(body.encode()).hexdigest() != want:
-            raise ValueError("checkpoint checksum mismatch")
-        st = cls(payload["graph_ids"], payload["mults"], payload["seed"])
-        st.next = [int(x) for x in payload["next"]]
-        st.sums = payload["sums"]
-        if len(st.next) != len(st.graph_ids) or len(st.sums) != len(st.graph_ids):
-            raise ValueError("checkpoint inconsistent")
+    def attach(cls, ctx):
+        """Wrap the run the context already holds (no reset)."""
+        st = cls.__new__(cls)
+        st.ctx = ctx
         return st
 
-    @classmethod
-    def load(cls, path):
-        with open(path) as f:
-            return cls.from_json(f.read())
+    def step(self, ids, n_samples):
+        """One batched block: graph ids[i] continues its stream by n_samples[i]
+        (returns the block's per-graph results)."""
+        return self.ctx.run_step(ids, n_samples)
 
-    # ------------------------------------------------------------ ranks ----
+    def add(self, gid, result, count):
+        """Fold an integration result of `count` samples of graph gid."""
+        self.ctx.run_add(gid, result, count)
+
+    def state(self):
+        """(list of per-graph dicts, seed)."""
+        arr, seed = self.ctx.run_get()
+        out = []
+        for g in arr:
+            out.append({"next": g.next, "n": g.n, "n_dd": g.n_dd, "n_zero": g.n_zero,
+                        "sum_y": tuple(g.sum_y), "sum_y2": tuple(g.sum_y2), "sum_abs": tuple(g.sum_abs),
+                        "max_y2": g.max_y2})
+        return out, seed
+
+    def estimate(self):
+        """(value, sigma_down, sigma_up, per-graph results)."""
+        return self.ctx.run_estimate()
+
+    def save(self, path):
+        self.ctx.checkpoint(path)
+
+    def load(self, path):
+        self.ctx.resume(path)
+
     def merge_ranks(self, group=None):
-        """Add the per-graph sums of all ranks (torch.distributed, any
-        backend); every rank gets the merged state."""
+        """Every rank ends with the sums of all ranks (its own next indices)."""
         import torch
         import torch.distributed as dist
-        t = torch.tensor([[s[f] for f in FIELDS] for s in self.sums], dtype=torch.float64)
-        dist.all_reduce(t, group=group)
-        for s, row in zip(self.sums, t.tolist()):
-            for f, v in zip(FIELDS, row):
-                s[f] = v
+        arr, _ = self.ctx.run_get()
+        raw = bytes(arr)
+        t = torch.frombuffer(bytearray(raw), dtype=torch.uint8)
+        world = dist.get_world_size(group)
+        me = dist.get_rank(group)
+        parts = [torch.empty_like(t) for _ in range(world)]
+        dist.all_gather(parts, t, group=group)
+        for r in range(world):
+            if r == me:
+                continue
+            other = (AeRunGraph * len(arr)).from_buffer_copy(parts[r].numpy().tobytes())
+            self.ctx.run_merge(other)
         return self

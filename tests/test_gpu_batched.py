@@ -89,6 +89,75 @@ def test_adaptive_controller(ctx):
     for gi in (0, 3):
         r = ctx.integrate_range(gi, 0, per[gi]["n"], seed=21)
         assert abs(r["sum_y"] - per[gi]["sum_y"]) <= 1e-10 * abs(r["sum_y"])
+    # C_j = sigma_up_j sqrt(N_j), t_j = tape flops + 150 M (Sec. IV.C)
     info = [ctx.graph_info(i) for i in range(4)]
-    w = [per[i]["sigma"] * math.sqrt(per[i]["n"]) / math.sqrt(info[i]["flops"]) for i in range(4)]
+    w = [per[i]["sigma_up"] * math.sqrt(per[i]["n"]) / math.sqrt(info[i]["flops"] + 150 * info[i]["M"])
+         for i in range(4)]
     assert int(np.argmax([p["n"] for p in per])) == int(np.argmax(w))
+    assert all(p["sigma_up"] >= p["sigma"] for p in per)
+
+
+def test_allocation_follows_formula(ctx):
+    """n_j = floor + largest-remainder share of the rest, shares proportional
+    to C_j / sqrt(t_j) = sigma_j sqrt(N_pilot) / sqrt(t_j) (mode 0, Sec. IV.C)
+    or to sigma_j^2 (mode 1), from the returned pilot sigmas; floor =
+    min(1024, n_total / n_ids); t_j = tape flops + 150 M."""
+    ctx.load_graphs(3)
+    ids = list(range(28))
+    info = [ctx.graph_info(i) for i in ids]
+    t = np.array([m["flops"] + 150 * m["M"] for m in info])
+    n_pilot, n_total = 100000, 10 ** 7 + 13
+    for mode in (0, 1):
+        n, sig = ctx.allocate(ids, n_pilot, n_total, seed=2, mode=mode)
+        w = sig * math.sqrt(n_pilot) / np.sqrt(t) if mode == 0 else sig ** 2
+        floor = min(1024, n_total // len(ids))
+        want = floor + (n_total - floor * len(ids)) * w / w.sum()
+        assert int(n.sum()) == n_total
+        assert np.all(np.abs(n - want) < 1.0 + 1e-9 * want), np.max(np.abs(n - want))
+
+
+def test_run_steps_checkpoint_resume(ctx, tmp_path):
+    """A run of three batched blocks equals a run of two blocks, checkpointed,
+    resumed in a new context and continued by one block; and each graph's
+    sums equal one launch over [0, 3n) (counter continuity)."""
+    n = 100000
+    ctx.load_graphs(2)
+    ids = [0, 1, 2, 3]
+    ctx.run_reset(11)
+    for _ in range(3):
+        ctx.run_step(ids, [n] * 4)
+    v, s, su, whole = ctx.run_estimate()
+    ctx.run_reset(11)
+    for _ in range(2):
+        ctx.run_step(ids, [n] * 4)
+    p = str(tmp_path / "run.ckpt")
+    ctx.checkpoint(p)
+    c2 = ae.Context(0)
+    try:
+        c2.load_graphs(2)
+        c2.resume(p)
+        c2.run_step(ids, [n] * 4)
+        v2, s2, su2, res = c2.run_estimate()
+        st, _ = c2.run_get()
+        assert [g.next for g in st] == [3 * n] * 4
+    finally:
+        c2.close()
+    assert abs(v2 - v) <= 1e-10 * abs(v) and abs(s2 - s) <= 1e-9 * s
+    for gi in ids:
+        assert res[gi]["n"] == 3 * n and res[gi]["n_dd"] == whole[gi]["n_dd"]
+        r = ctx.integrate_range(gi, 0, 3 * n, seed=11)
+        assert abs(r["sum_y"] - res[gi]["sum_y"]) <= 1e-10 * abs(r["sum_y"])
+        assert abs(r["sum_y2"] - res[gi]["sum_y2"]) <= 1e-10 * r["sum_y2"]
+    assert su >= s
+
+
+def test_bounded_wait_runs_out(ctx):
+    """The bounded wait for a tape segment (about 2 s in normal use) made to
+    run out through the test hook (first copy left out, wait limit 2^20
+    cycles): the call returns AE_ERR_TIMEOUT and the context stays usable."""
+    ctx.load_graphs(2)
+    before = ctx.integrate([2], 50000, seed=3)
+    with pytest.raises(ae.AeError, match="AE_ERR_TIMEOUT"):
+        ctx.test_stage_timeout(2, 1 << 20)
+    after = ctx.integrate([2], 50000, seed=3)
+    assert after[0] == before[0] and after[1] == before[1]

@@ -14,6 +14,11 @@ from tests import proposal_inputs as pin
 
 pytestmark = pytest.mark.gpu
 
+# relative L2 error of each parameter block's gradient against the oracle's
+# (FP32 accumulation on the device, float64 in the oracle, both with BF16
+# operands at the same points)
+GRAD_TOL = {"W1": 2e-2, "b1": 2e-2, "W2": 2e-2, "b2": 2e-2, "W3": 2e-2, "b3": 2e-2, "W4": 1e-2, "b4": 1e-2}
+
 
 @pytest.fixture(scope="module")
 def ctx():
@@ -34,20 +39,34 @@ def test_gradient_matches_oracle(ctx, n, gi):
     order, lt, w = pin.records(7, 600, M)
     loss, grad, lp2, degt = ctx.proposal_eval(M, p, deg, wplain, order, lt, w)
     rl, rg, rlogp, rdegt = pr.loss_and_grad(p, deg, wplain, order, lt, w, M)
-    # BF16 activations on the device against float64 activations in the
-    # oracle: agreement to about a per cent.
-    assert abs(loss - rl) <= 5e-3 * abs(rl)
-    cos = float(np.dot(grad, rg) / (np.linalg.norm(grad) * np.linalg.norm(rg)))
-    assert cos > 0.998, cos
-    assert np.linalg.norm(grad - rg) <= 6e-2 * np.linalg.norm(rg)
+    # The oracle rounds weights, activations and backward signals to BF16 at
+    # the device's points; what remains is FP32 against float64 accumulation
+    # (and the rare BF16 rounding that this flips).  Checked layer by layer,
+    # weights and biases apart, so that an error confined to one block (a
+    # missing or scaled bias gradient) cannot hide in the total.
+    assert abs(loss - rl) <= 1e-4 * abs(rl), (loss, rl)
+    k = 0
+    for name, shp in pr.SIZES:
+        n_ = int(np.prod(shp))
+        a, b = grad[k:k + n_].astype(np.float64), rg[k:k + n_]
+        k += n_
+        nb = np.linalg.norm(b)
+        assert nb > 0, name
+        err = np.linalg.norm(a - b) / nb
+        cos = float(np.dot(a, b) / (np.linalg.norm(a) * nb))
+        assert err <= GRAD_TOL[name], (name, err, cos)
+        assert cos >= 1 - GRAD_TOL[name] ** 2, (name, err, cos)
     mask = np.isfinite(rlogp)
-    assert np.max(np.abs(lp2[mask] - rlogp[mask] / math.log(2))) < 0.05
-    assert np.max(np.abs(degt[1:-1] / rdegt[1:-1] - 1)) < 0.02
+    assert np.max(np.abs(lp2[mask] - rlogp[mask] / math.log(2))) < 1e-3
+    assert np.max(np.abs(degt[1:-1] / rdegt[1:-1] - 1)) < 1e-3
 
 
-def test_learned_mixture_normalised_and_unbiased(ctx):
+def test_learned_mixture_normalised_unbiased_and_better(ctx):
     """E_q[1/q] = 1/(M-1)! for the trained mixture; the learned estimate
-    agrees with the plain one; report the variance ratio."""
+    agrees with the plain one; and the trained network gains: on the same
+    number of samples its variance is at least 10x smaller and its
+    1/(sigma^2 s) at least 5x larger than the plain density's (one launch per
+    graph for both; measured gains on 3-loop graphs are 45-476x in variance)."""
     ctx.load_graphs(3)
     gid = 3
     rep = ctx.train_proposal(gid, 1 << 18, seed=1, steps=80, lr=3e-3, beta=0.1)
@@ -56,11 +75,49 @@ def test_learned_mixture_normalised_and_unbiased(ctx):
     wq = np.exp2(-d["log2g"]) * math.factorial(7)
     assert abs(wq.mean() - 1) < 4 * wq.std() / math.sqrt(len(wq))
     N = 1 << 22
+    ctx.integrate([gid], N, seed=30)             # warm-up of both launch shapes
     _, _, pl = ctx.integrate([gid], N, seed=3)
     ctx.set_proposal(gid, 0)
+    ctx.integrate([gid], N, seed=40)
     _, _, pp = ctx.integrate([gid], N, seed=4)
+    ctx.set_proposal(gid, 1, 0.1)
     a, b = pl[0], pp[0]
     assert abs(a["mean"] - b["mean"]) < 4 * math.hypot(a["sigma1"], b["sigma1"])
+    var_gain = (b["sigma1"] / a["sigma1"]) ** 2
+    rate_gain = (b["sigma1"] ** 2 * b["seconds"]) / (a["sigma1"] ** 2 * a["seconds"])
+    print("variance gain %.1f, 1/(sigma^2 s) gain %.1f" % (var_gain, rate_gain))
+    assert var_gain >= 10, var_gain
+    assert rate_gain >= 5, rate_gain
+
+
+def test_learned_mixture_samples_match_oracle(ctx):
+    """Per-sample parity of the learned mixture (z and log2 q) against the
+    oracle's sampler, fed the same Philox words and the network outputs the
+    library exports; indices on both sides of 2^32.  Tolerances: the
+    device's exp2/log2 are within 4 ulp of correctly rounded, its tables
+    within a few ulp of the oracle's, and a z carries M such roundings."""
+    from oracle import proposal as pr
+    from oracle.philox import uniforms_fine
+    ctx.load_graphs(3)
+    gs = enumerate_graphs(3)
+    for gid in (5, 21):
+        ctx.train_proposal(gid, 1 << 18, seed=2, steps=60, lr=3e-3, beta=0.1)
+        params, out, beta = ctx.proposal_export(gid)
+        assert beta == 0.1
+        # the exported outputs are what the oracle's forward pass gives for
+        # the exported weights (FP32 against float64 accumulation)
+        ref_o = pr.forward(params, 8)["o"]
+        assert np.max(np.abs(out - ref_o)) <= 2e-2 * max(1.0, np.max(np.abs(ref_o)))
+        d = Density(gs[gid])
+        for first in (0, 2 ** 32 - 1000):
+            cnt = 2000
+            got = ctx.eval_samples(gid, first, cnt, seed=9)
+            u = uniforms_fine(np.arange(first, first + cnt, dtype=np.uint64), gid, 9, d.M)
+            z, lq, plain = pr.learned_points(d, out.astype(np.float64), beta, u)
+            assert 0.05 < plain.mean() < 0.15
+            rel = np.abs(got["z"] - z) / z
+            assert np.max(rel) < 1e-12, np.max(rel)
+            assert np.max(np.abs(got["log2g"] - lq)) < 1e-10 * max(1.0, np.max(np.abs(lq)))
 
 
 def test_cost_aware_training_normalised_and_unbiased(ctx):

@@ -141,3 +141,25 @@ def test_error_bound_holds_at_worst_points(host, n, ids, worst):
         for k in np.argsort(-r)[:worst]:
             ex = It.evaluate(pts["z"][k])[0]
             assert abs(I[k] - ex) <= E[k] + 2.0 ** -52 * abs(ex), (gi, k, I[k], ex, E[k])
+
+
+def test_graph_classes_match_table_I_and_oracle():
+    """ae_graph_classes (no compilation): the library's class of every
+    5-loop graph against the oracle's, graph by graph, and the counts per
+    class against Table I's N_diag (Sec. V)."""
+    from oracle.graphs import enumerate_graphs as oracle_graphs
+    k, m = ae.graph_classes(5)
+    gs = oracle_graphs(5)
+    assert len(k) == 3213
+    assert [tuple(x) for x in k] == [g.klass() for g in gs]
+    assert list(m) == [g.mult for g in gs]
+    want = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "table1_ndiag.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        a, b, c, nd = map(int, line.split())
+        want[(a, b, c)] = nd
+    got = {}
+    for row in k:
+        got[tuple(row)] = got.get(tuple(row), 0) + 1
+    assert got == want

@@ -542,3 +542,58 @@ def test_proposal_zero_output_is_plain_walk():
             want = d.phi[0][T ^ (1 << j)] / d.deg[0][T ^ (1 << j)] / d.phi[0][T]
             assert abs(np.exp(logp[T, j]) - want) < 1e-12
     assert np.allclose(degt[1:-1], d.deg[0][1:-1])
+
+
+def _random_outputs(M, seed, scale=1.5):
+    return np.random.default_rng(seed).normal(0.0, scale, size=(1 << M, 16))
+
+
+def test_learned_mixture_is_a_density():
+    """The oracle's learned mixture density integrates to 1 over the simplex:
+    E_g[q/g] = 1 with points drawn from the plain density g (2-loop graph,
+    random network outputs); a missing Deg_theta factor or an unnormalised
+    choice probability fails it."""
+    from oracle import proposal as pr
+    g = enumerate_graphs(2)[2]
+    d = Density(g)
+    M = d.M
+    o = _random_outputs(M, 4)
+    wplain = np.ones(1 << M)
+    wplain[1:-1] = d.phi[0][1:-1] / d.deg[0][1:-1]
+    logp, degt = pr.tables(o, d.deg[0], wplain, M)
+    idx = np.arange(0, 40000, dtype=np.uint64)
+    z, lg, _ = sample(d, uniforms(idx, 2, 3, M))
+    lq = pr.log2_mixture(d, logp, degt, 0.1, np.log2(z))
+    r = np.exp2(lq - lg)
+    assert abs(r.mean() - 1.0) < 4 * r.std() / math.sqrt(len(r)), (r.mean(), r.std())
+
+
+def test_learned_sampler_matches_its_density():
+    """Points drawn by the oracle's learned sampler have E_q[1/q] = 1/(M-1)!
+    (the simplex volume): the walk and the density agree."""
+    from oracle import proposal as pr
+    from oracle.philox import uniforms_fine
+    g = enumerate_graphs(2)[1]
+    d = Density(g)
+    M = d.M
+    o = _random_outputs(M, 5)
+    u = uniforms_fine(np.arange(0, 20000, dtype=np.uint64), 1, 9, M)
+    z, lq, plain = pr.learned_points(d, o, 0.1, u)
+    assert np.allclose(z.sum(1), 1.0)
+    assert 0.05 < plain.mean() < 0.15
+    w = np.exp2(-lq) * math.factorial(M - 1)
+    assert abs(w.mean() - 1.0) < 4 * w.std() / math.sqrt(len(w)), (w.mean(), w.std())
+
+
+def test_fine_uniforms_layout():
+    """uniforms_fine: u = (2m + 1) 2^-53 with m the 52 high-order bits of
+    (w0, w1); strictly inside (0, 1)."""
+    from oracle.philox import philox4x32_10, uniforms_fine
+    u = uniforms_fine(np.array([5, 2 ** 33 + 7], dtype=np.uint64), 3, 11, 2)
+    for row, idx in enumerate((5, 2 ** 33 + 7)):
+        for b in range(2):
+            w = philox4x32_10([idx & 0xFFFFFFFF, idx >> 32, 3, b], [11, 0])
+            for h in range(2):
+                m = (w[2 * h] << 20) | (w[2 * h + 1] >> 12)
+                assert u[row, 2 * b + h] == (2 * m + 1) * 2.0 ** -53
+    assert np.all((u > 0) & (u < 1))

@@ -41,3 +41,16 @@ def test_probability_floor_and_degenerate_inputs():
     assert np.allclose(ae.schedule_probabilities([np.nan, 1.0], [5, 5], [1.0, 1.0], 0.0), [0.0, 1.0])
     with pytest.raises(ae.AeError):
         ae.schedule_probabilities([1.0], [1], [1.0], 1.5)
+
+
+def test_accept_widths_of_eq_interval_accept():
+    """width_j = (1/4) sigma_j sqrt(sum sigma^2) / sum sigma (Sec. IV.A):
+    the widths add up to a quarter of the set's sigma_down, are proportional
+    to sigma_j, and graphs without a positive finite sigma get 0."""
+    sig = np.array([3.0, 4.0, 0.0, float("nan"), 12.0])
+    w = ae.accept_widths(sig)
+    good = np.array([3.0, 4.0, 12.0])
+    assert w[2] == 0 and w[3] == 0
+    assert np.isclose(w[[0, 1, 4]].sum(), 0.25 * 13.0)           # sqrt(9 + 16 + 144) = 13
+    assert np.allclose(w[[0, 1, 4]], 0.25 * good * 13.0 / good.sum())
+    assert np.all(ae.accept_widths(np.zeros(3)) == 0)

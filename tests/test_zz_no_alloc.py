@@ -33,8 +33,10 @@ def _same(a, b):
 
 
 def test_two_calls_match_allocating_entry_point(ctx):
-    # two calls in a row: the second reuses the array the first one filled
-    for gid, n, seed in ((1, 300000, 3), (3, 524288, 4)):
+    # calls in a row: each reuses the array the previous one filled; the
+    # third is smaller than the second, so stale flags and values beyond its
+    # own samples are still in the array and must be ignored
+    for gid, n, seed in ((1, 300000, 3), (3, 524288, 4), (1, 100003, 5)):
         got = ctx.integrate_noalloc(gid, n, seed)
         _, _, per = ctx.integrate([gid], n, seed)
         _same(got, per[0])
