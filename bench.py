@@ -99,10 +99,32 @@ def workload_graphs(loops, graphs):
     return ae.seeded_subset(total, graphs, 0)
 
 
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def stored_tables(n_loops, gi):
+    """Path of the oracle's stored coefficient tables of a graph, or None
+    (written by tests/golden/make_oracle_tables.py: at four loops the
+    oracle's own set-up of one graph takes 8 to 30+ minutes)."""
+    p = os.path.join(GOLDEN, "oracle_tables_%dloop_%d.json.gz" % (n_loops, gi))
+    return p if os.path.exists(p) else None
+
+
+def baseline_graphs(n_loops, canon):
+    """Graphs of the workload the CPU baseline times: at four loops and more
+    those whose oracle tables are stored, else the first, middle and last."""
+    if n_loops >= 4:
+        have = [g for g in canon if stored_tables(n_loops, g)]
+        if have:
+            return have
+    return [canon[0], canon[len(canon) // 2], canon[-1]]
+
+
 def oracle_rate(n_loops, canon_ids, per_graph, seed=0):
     """Time the CPU oracle (as it stands) on a bounded sample: the listed
     graphs, per_graph samples each (plain density), evaluation time after
-    each worker's per-graph set-up; one spawned process per host core."""
+    each worker's per-graph set-up (stored coefficient tables where they
+    exist); one spawned process per host core."""
     import multiprocessing as mp
     cores = os.cpu_count() or 1
     per_core = max(1, cores // max(1, len(canon_ids)))
@@ -119,20 +141,44 @@ def oracle_rate(n_loops, canon_ids, per_graph, seed=0):
     used = min(cores, len(jobs))
     eval_wall = sum(r[1] for r in res) / used
     setup = max(r[2] for r in res)
-    return evals / eval_wall, used, evals, eval_wall, setup, wall_all
+    stored = [gi for gi in canon_ids if stored_tables(n_loops, gi)]
+    return evals / eval_wall, used, evals, eval_wall, setup, wall_all, stored
 
 
 def _oracle_job(args):
     n_loops, gi, lo, cnt, seed = args
     sys.path.insert(0, ROOT)
+    import gzip
     from oracle.estimate import GraphOracle
     from oracle.graphs import enumerate_graphs
+    from oracle.integrand import Integrand
     t = time.perf_counter()
-    o = GraphOracle(enumerate_graphs(n_loops)[gi], gi)
+    tables = None
+    path = stored_tables(n_loops, gi)
+    if path:
+        with gzip.open(path, "rt") as f:
+            tables = Integrand.tables_from_records(json.load(f)["tables"])
+    o = GraphOracle(enumerate_graphs(n_loops)[gi], gi, tables=tables)
     setup = time.perf_counter() - t
     t = time.perf_counter()
     o.samples(lo, cnt, seed)
     return cnt, time.perf_counter() - t, setup
+
+
+def oracle_samples_default(n_loops):
+    """Samples per graph for about 10-30 s of oracle evaluation on the host."""
+    cores = os.cpu_count() or 1
+    return {1: 4096, 2: 2048, 3: 96}.get(n_loops, 16 * cores)
+
+
+def cpu_sample_text(cids, n_loops, per_graph, wall, cores, setup, stored):
+    txt = ("canonical graphs %s of the %d-loop list, %d samples each, plain density, exact evaluation; "
+           "%.1f s on %d processes after a per-graph set-up of up to %.1f s" % (cids, n_loops, per_graph, wall,
+                                                                               cores, setup))
+    if stored:
+        txt += ("; the coefficient tables of %s are read from tests/golden (written by "
+                "tests/golden/make_oracle_tables.py: their own set-up takes 8 to 30+ minutes per graph)" % stored)
+    return txt
 
 
 class Clocks:
@@ -192,17 +238,16 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     canon = workload_graphs(args.loops, args.graphs)
-    cids = [canon[0], canon[len(canon) // 2], canon[-1]]
-    rate, cores, evals, wall, setup, wall_all = oracle_rate(args.loops, cids, args.oracle_samples)
+    cids = baseline_graphs(args.loops, canon)
+    per = args.oracle_samples or oracle_samples_default(args.loops)
+    rate, cores, evals, wall, setup, wall_all, stored = oracle_rate(args.loops, cids, per)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "samples/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.loops, len(canon), N_GRAPHS[args.loops]),
-                       "oracle_graphs": cids, "samples_per_graph": args.oracle_samples},
+                       "oracle_graphs": cids, "samples_per_graph": per},
             "cpu_baseline": {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
-                             "sample": "canonical graphs %s of the %d-loop list, %d samples each, plain density; "
-                                       "evaluation %.1f s after a per-graph set-up of up to %.1f s"
-                                       % (cids, args.loops, args.oracle_samples, wall, setup)},
+                             "sample": cpu_sample_text(cids, args.loops, per, wall, cores, setup, stored)},
             "e2e": {"value": rate, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "vs_baseline": None}
     print(json.dumps(line))
@@ -229,7 +274,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain and other-acceptance arms")
     ap.add_argument("--init-samples", type=int, default=1 << 16)
     ap.add_argument("--pilot", type=int, default=1 << 18)
-    ap.add_argument("--oracle-samples", type=int, default=24)
+    ap.add_argument("--oracle-samples", type=int, default=0, help="CPU baseline samples per graph (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-file", default=None, help="where nvidia-smi samples go (default: a temp file)")
     args = ap.parse_args()
@@ -407,12 +452,11 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cids = [canon[0], canon[len(canon) // 2], canon[-1]]
-        crate, cores, evals, wall, setup, _ = oracle_rate(args.loops, cids, args.oracle_samples)
+        cids = baseline_graphs(args.loops, canon)
+        per = args.oracle_samples or oracle_samples_default(args.loops)
+        crate, cores, evals, wall, setup, _, stored = oracle_rate(args.loops, cids, per)
         cpu = {"value": crate, "unit": "samples/s", "cores": cores, "kind": "oracle",
-               "sample": "canonical graphs %s of the %d-loop list, %d samples each, plain density; evaluation "
-                         "%.1f s on %d processes after a per-graph set-up of up to %.1f s"
-                         % (cids, args.loops, args.oracle_samples, wall, cores, setup)}
+               "sample": cpu_sample_text(cids, args.loops, per, wall, cores, setup, stored)}
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     nominal = 2 * 2 * sms * (ck["sm_mhz"] if ck else 2032.0) * 1e6 / 1e12   # 2 DFMA/SM/clk, FMA = 2 flops
     line = {

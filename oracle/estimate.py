@@ -45,12 +45,12 @@ class GraphOracle:
     """calc=2: Philox4x32-10 and the Calc 2 constants; calc=1: MRG32k3a and
     the Calc 1 constants (Sec. V)."""
 
-    def __init__(self, g, graph_id, calc=2, integrand=True):
+    def __init__(self, g, graph_id, calc=2, integrand=True, tables=None):
         self.g = g
         self.gid = graph_id
         self.calc = calc
         self.dens = Density(g, **(CALC1 if calc == 1 else CALC2))
-        self.integrand = Integrand(g) if integrand else None
+        self.integrand = Integrand(g, tables=tables) if integrand else None
 
     def uniforms(self, idx, seed):
         if self.calc == 1:

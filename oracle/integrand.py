@@ -393,15 +393,28 @@ def project(channel, chain, has_q):
     return -tot / 24.0
 
 
+def _listify(x):
+    return [_listify(v) for v in x] if isinstance(x, (tuple, list)) else x
+
+
+def _tuplify(x):
+    return tuple(_tuplify(v) for v in x) if isinstance(x, list) else x
+
+
 # --------------------------------------------------------- the integrand --
 
 CHANNEL_OF_OP = {'A': 'F2', 'L': 'abc', 'L-U': 'bc'}
 
 
 class Integrand:
-    """I(z) of one graph: terms, factors and their coefficient tables."""
+    """I(z) of one graph: terms, factors and their coefficient tables.
 
-    def __init__(self, g):
+    tables (optional): the coefficient tables of the factors, keyed as in
+    self.tables (as written by table_records()), to skip their computation
+    (minutes to hours per graph at four loops and more); the factors and
+    terms are rebuilt as usual."""
+
+    def __init__(self, g, tables=None):
         self.g = g
         self.n = g.n
         self.idx = g.line_index()
@@ -433,11 +446,26 @@ class Integrand:
                            tuple(sorted(tuple(sorted(C.verts)) for C in children)))
                     if key not in cache:
                         fac = Factor(g, S, children)
-                        cache[key] = (fac, coefficient_table(fac, channel, cc))
+                        tab = tables[key] if tables is not None else coefficient_table(fac, channel, cc)
+                        cache[key] = (fac, tab)
                     parts.append(key)
                 assigns.append(parts)
             self.terms.append((sign, assigns))
         self.tables = cache
+
+    def table_records(self):
+        """The coefficient tables as plain lists (for storing):
+        [[key, [[coef, j, asites, qsite, pairs], ...]], ...]."""
+        return [[list(_listify(k)), [[c, j, list(a), q, [list(p) for p in pr]] for c, j, a, q, pr in tab]]
+                for k, (_, tab) in self.tables.items()]
+
+    @staticmethod
+    def tables_from_records(records):
+        """Inverse of table_records()."""
+        out = {}
+        for k, tab in records:
+            out[_tuplify(k)] = [(c, j, tuple(a), q, tuple(tuple(p) for p in pr)) for c, j, a, q, pr in tab]
+        return out
 
     def alphas(self, z):
         """Exact Schwinger parameters of every original line at point z."""

@@ -76,3 +76,32 @@ def test_samples_match_stored_oracle(ctx, n):
         assert per[0]["n"] == count
         assert per[0]["n_dd"] == int(flag.sum()) and per[0]["n_nonfinite"] == int(zero.sum()), cid
         assert abs(per[0]["sum_y"] - sy) <= 1e-9 * abs(sy), cid
+
+
+def test_stored_tables_oracle_matches_gpu(ctx):
+    """Four-loop graph 23 (first of the bench's 20-graph workload) through the
+    oracle rebuilt from its stored coefficient tables
+    (tests/golden/oracle_tables_4loop_23.json.gz, written by
+    tests/golden/make_oracle_tables.py from oracle/ alone; the bench's CPU
+    baseline evaluates it this way): per-sample values against the GPU within
+    the certified bound, indices on both sides of 2^32.  Pins the stored
+    tables and extends the four-loop per-sample parity to this graph."""
+    import gzip
+    import json
+    from oracle.estimate import GraphOracle
+    from oracle.graphs import enumerate_graphs
+    from oracle.integrand import Integrand
+    path = os.path.join(HERE, "golden", "oracle_tables_4loop_23.json.gz")
+    with gzip.open(path, "rt") as f:
+        rec = json.load(f)
+    assert rec["loops"] == 4 and rec["graph"] == 23
+    o = GraphOracle(enumerate_graphs(4)[23], 23, tables=Integrand.tables_from_records(rec["tables"]))
+    ctx.load_graph_subset(4, [23])
+    for first in (0, 2 ** 32 - 4):
+        ref = o.samples(first, 8, seed=3)
+        d = ctx.eval_samples(0, first, 8, seed=3)
+        assert np.array_equal(d["z"], ref["z"])
+        assert np.array_equal(d["log2g"], ref["log2g"])
+        assert bound_holds(d["I"], d["E"], ref["I"])
+        flag = rejected(d["y"], d["E"], d["log2g"])
+        assert np.all(np.abs(d["I"] - ref["I"])[~flag] <= REL * np.abs(ref["I"][~flag]))
