@@ -348,41 +348,6 @@ __device__ __forceinline__ void tape_step(const uint4 &w0, const uint4 &w1, char
   *reinterpret_cast<double *>(Sb + d) = sp == 0 ? __fma_rn(va, vb, vc) : special_op(sp, va, vb, vc);
 }
 
-// One segment of the tape (cnt >= 1 instructions at `code`, shared memory) on
-// this thread's row, with the operand loads software-pipelined: the three
-// operands of instruction k+1 are read from the slot row while instruction k
-// executes, so that the shared-memory latency overlaps the FMA.  An operand
-// that names the slot instruction k writes takes k's result instead (its
-// store comes after the early load).  Same operations and results as
-// tape_step applied in order.
-__device__ __forceinline__ void run_segment(const uint4 *code, int cnt, char *Sb) {
-  uint4 w0 = code[0], w1 = code[1];
-  double A = *reinterpret_cast<const double *>(Sb + (w0.y & 0xffffu));
-  double B = *reinterpret_cast<const double *>(Sb + (w0.y >> 16));
-  double C = *reinterpret_cast<const double *>(Sb + (w0.z & 0xffffu));
-#pragma unroll 1
-  for (int k = 0; k < cnt; ++k) {
-    const int nx = 2 * min(k + 1, cnt - 1);
-    const uint4 n0 = code[nx], n1 = code[nx + 1];
-    const uint32_t na = n0.y & 0xffffu, nb = n0.y >> 16, nc = n0.z & 0xffffu;
-    double An = *reinterpret_cast<const double *>(Sb + na);
-    double Bn = *reinterpret_cast<const double *>(Sb + nb);
-    double Cn = *reinterpret_cast<const double *>(Sb + nc);
-    const uint32_t op = w0.x & 0xffffu, d = w0.x >> 16;
-    const uint32_t m = ~((op & I_AB) << 29);   // I_AB = 4: bit 31
-    const double va = absmask(A, m);
-    const double vb = absmask(sel64(op & I_BK, __hiloint2double((int)w1.y, (int)w1.x), B), m);
-    const double vc = absmask(sel64(op & I_CK, __hiloint2double((int)w1.w, (int)w1.z), C), m);
-    const uint32_t sp = op & 0xff00u;
-    const double r = sp == 0 ? __fma_rn(va, vb, vc) : special_op(sp, va, vb, vc);
-    *reinterpret_cast<double *>(Sb + d) = r;
-    A = sel64(na == d, r, An);
-    B = sel64(nb == d, r, Bn);
-    C = sel64(nc == d, r, Cn);
-    w0 = n0; w1 = n1;
-  }
-}
-
 // FP64 tape interpreter reading instructions from global memory (next one
 // prefetched).  Used by the kernels whose threads do not run the tape in step
 // (parity dumps, training samples); the integration kernels stream the tape
@@ -493,78 +458,51 @@ static __device__ bool run_tape_staged(Stage &st, const GraphDev &G, double *S, 
     const int cnt = min(kSeg, G.ntape - s * kSeg);
     ++st.used;
     if (!active) continue;
-    run_segment(code, cnt, Sb);
+    uint4 w0 = code[0], w1 = code[1];
+#pragma unroll 1
+    for (int k = 0; k < cnt; ++k) {
+      const int nx = 2 * min(k + 1, cnt - 1);
+      const uint4 n0 = code[nx], n1 = code[nx + 1];
+      tape_step(w0, w1, Sb);
+      w0 = n0; w1 = n1;
+    }
   }
   return true;
 }
 
-// One double-double tape instruction given its loaded slot operands A, B, C
-// (hi/lo pairs; the instruction's constants with their low parts from the
-// pool).  Magnitude twins stay in FP64 (their low parts are zero); the
-// compiler's hints I_KX, I_C0, I_B1 select the shorter exact forms of a
+// One double-double tape instruction on this thread's row Sb (hi/lo pairs;
+// the instruction's byte offsets scaled by 2; constants with their low parts
+// from the pool).  Magnitude twins stay in FP64 (their low parts are zero);
+// the compiler's hints I_KX, I_C0, I_B1 select the shorter exact forms of a
 // product, a scaling and a sum.
-__device__ __forceinline__ dd exec_dd(const uint4 &w0, const uint4 &w1, const dd &A, const dd &B, const dd &C,
-                                      const double *khi, const double *klo) {
-  const uint32_t op = w0.x & 0xffffu, kbi = w0.z >> 16, kci = w0.w & 0xffffu;
-  const dd va = A;
-  // exact constants (I_KX) come from the instruction's immediates, others
-  // with their low parts from the pool
-  const dd vb = !(op & I_BK) ? B
-                : (op & I_KX) ? dd{__hiloint2double((int)w1.y, (int)w1.x), 0.0}
-                              : dd{__ldg(khi + kbi), __ldg(klo + kbi)};
-  const dd vc = !(op & I_CK) ? C
-                : (op & I_KX) ? dd{__hiloint2double((int)w1.w, (int)w1.z), 0.0}
-                              : dd{__ldg(khi + kci), __ldg(klo + kci)};
-  const uint32_t sp = op & 0xff00u;
-  if (op & I_AB) return dd{__fma_rn(fabs(va.hi), fabs(vb.hi), fabs(vc.hi)), 0.0};   // magnitudes: FP64 is enough
-  if (sp == 0) {
-    // the compiler's hints pick the shortest exact form of c + a*b
-    const bool bx = (op & (I_BK | I_KX)) == (I_BK | I_KX);   // b an exact constant
-    if (op & I_C0) return bx ? dd_scale_x(vb.hi, va) : dd_mul_fast(va, vb);
-    if (op & I_B1) return dd_add_fast(vc, vb.hi > 0 ? va : dd{-va.hi, -va.lo});
-    if (bx) return dd_fma_x(vc, vb.hi, va);
-    return dd_fma_fast(vc, vb, va);
-  }
-  if (sp == I_DIV) return dd_div(va, vb);
-  if (sp == I_ABS) return dd_abs(va);
-  return dd_add_fast(vc, dd_abs(va));   // I_ADDABS
-}
-
-// One double-double tape instruction on this thread's row Sb (the
-// instruction's byte offsets scaled by 2).
 __device__ __forceinline__ void tape_step_dd(const uint4 &w0, const uint4 &w1, char *Sb, const double *khi,
                                              const double *klo) {
-  const uint32_t d = (w0.x >> 16) * 2, a = (w0.y & 0xffffu) * 2, b = (w0.y >> 16) * 2, c = (w0.z & 0xffffu) * 2;
-  const dd r = exec_dd(w0, w1, *reinterpret_cast<const dd *>(Sb + a), *reinterpret_cast<const dd *>(Sb + b),
-                       *reinterpret_cast<const dd *>(Sb + c), khi, klo);
-  *reinterpret_cast<dd *>(Sb + d) = r;
-}
-
-// One segment of the double-double tape with the operand loads
-// software-pipelined as in run_segment (an operand that names the slot the
-// previous instruction writes takes its result).
-__device__ __forceinline__ void run_segment_dd(const uint4 *code, int cnt, char *Sb, const double *khi,
-                                               const double *klo) {
-  uint4 w0 = code[0], w1 = code[1];
-  dd A = *reinterpret_cast<const dd *>(Sb + (w0.y & 0xffffu) * 2);
-  dd B = *reinterpret_cast<const dd *>(Sb + (w0.y >> 16) * 2);
-  dd C = *reinterpret_cast<const dd *>(Sb + (w0.z & 0xffffu) * 2);
-#pragma unroll 1
-  for (int k = 0; k < cnt; ++k) {
-    const int nx = 2 * min(k + 1, cnt - 1);
-    const uint4 n0 = code[nx], n1 = code[nx + 1];
-    const uint32_t na = n0.y & 0xffffu, nb = n0.y >> 16, nc = n0.z & 0xffffu;
-    const dd An = *reinterpret_cast<const dd *>(Sb + na * 2);
-    const dd Bn = *reinterpret_cast<const dd *>(Sb + nb * 2);
-    const dd Cn = *reinterpret_cast<const dd *>(Sb + nc * 2);
-    const uint32_t d = w0.x >> 16;
-    const dd r = exec_dd(w0, w1, A, B, C, khi, klo);
-    *reinterpret_cast<dd *>(Sb + d * 2) = r;
-    A = na == d ? r : An;
-    B = nb == d ? r : Bn;
-    C = nc == d ? r : Cn;
-    w0 = n0; w1 = n1;
+  const uint32_t op = w0.x & 0xffffu, d = (w0.x >> 16) * 2, a = (w0.y & 0xffffu) * 2, b = (w0.y >> 16) * 2,
+                 c = (w0.z & 0xffffu) * 2, kbi = w0.z >> 16, kci = w0.w & 0xffffu;
+  const dd va = *reinterpret_cast<const dd *>(Sb + a);
+  // exact constants (I_KX) come from the instruction's immediates, others
+  // with their low parts from the pool
+  const dd vb = !(op & I_BK) ? *reinterpret_cast<const dd *>(Sb + b)
+                : (op & I_KX) ? dd{__hiloint2double((int)w1.y, (int)w1.x), 0.0}
+                              : dd{__ldg(khi + kbi), __ldg(klo + kbi)};
+  const dd vc = !(op & I_CK) ? *reinterpret_cast<const dd *>(Sb + c)
+                : (op & I_KX) ? dd{__hiloint2double((int)w1.w, (int)w1.z), 0.0}
+                              : dd{__ldg(khi + kci), __ldg(klo + kci)};
+  dd r;
+  const uint32_t sp = op & 0xff00u;
+  if (op & I_AB) r = dd{__fma_rn(fabs(va.hi), fabs(vb.hi), fabs(vc.hi)), 0.0};   // magnitudes: FP64 is enough
+  else if (sp == 0) {
+    // the compiler's hints pick the shortest exact form of c + a*b
+    const bool bx = (op & (I_BK | I_KX)) == (I_BK | I_KX);   // b an exact constant
+    if (op & I_C0) r = bx ? dd_scale_x(vb.hi, va) : dd_mul_fast(va, vb);
+    else if (op & I_B1) r = dd_add_fast(vc, vb.hi > 0 ? va : dd{-va.hi, -va.lo});
+    else if (bx) r = dd_fma_x(vc, vb.hi, va);
+    else r = dd_fma_fast(vc, vb, va);
   }
+  else if (sp == I_DIV) r = dd_div(va, vb);
+  else if (sp == I_ABS) r = dd_abs(va);
+  else r = dd_add_fast(vc, dd_abs(va));   // I_ADDABS
+  *reinterpret_cast<dd *>(Sb + d) = r;
 }
 
 // Double-double twin of run_tape, instructions read from global memory (next
@@ -602,7 +540,14 @@ static __device__ bool run_tape_dd_staged(Stage &st, const GraphDev &G, dd *S, b
     const int cnt = min(kSeg, G.ntape - s * kSeg);
     ++st.used;
     if (!active) continue;
-    run_segment_dd(code, cnt, Sb, khi, klo);
+    uint4 w0 = code[0], w1 = code[1];
+#pragma unroll 1
+    for (int k = 0; k < cnt; ++k) {
+      const int nx = 2 * min(k + 1, cnt - 1);
+      const uint4 n0 = code[nx], n1 = code[nx + 1];
+      tape_step_dd(w0, w1, Sb, khi, klo);
+      w0 = n0; w1 = n1;
+    }
   }
   return true;
 }
