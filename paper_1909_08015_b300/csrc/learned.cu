@@ -264,11 +264,26 @@ __global__ void wsum_kernel(const double *w, uint64_t n, double *part) {
 // 2^40 fixed point (integer atomics: order-independent, hence
 // deterministic).  acc[T*16+j] (j < 15): d(-ln q)/d l(T,j); acc[T*16+15]:
 // d(-ln q)/d ln Deg_theta(T).  lossp: per-CTA partial of -sum wn ln q_theta.
+// Every sample passes through the full line set (level 0) and one of its M
+// subsets with one line removed (level 1), so those 1 + M states' 16 entries
+// are summed per CTA in shared memory first (integer atomics: the sums are
+// the same in any order) and added to the global table once per CTA.
+__device__ __forceinline__ void grad_add(unsigned long long *sacc, unsigned long long *acc, uint32_t full,
+                                         uint32_t T, int col, long long q) {
+  const uint32_t gone = full ^ T;
+  if (gone == 0) atomicAdd(sacc + col, (unsigned long long)q);
+  else if ((gone & (gone - 1)) == 0) atomicAdd(sacc + (1 + __ffs(gone) - 1) * 16 + col, (unsigned long long)q);
+  else atomicAdd(acc + (size_t)T * 16 + col, (unsigned long long)q);
+}
+
 __global__ void grad_kernel(int M, const uint8_t *order, const float *lt, const double *w, uint64_t n,
                             double inv_wsum, const double *lp, const double *lp2, const double *ld,
                             const double *ld2, unsigned long long *acc, double *lossp) {
   __shared__ double red[256];
+  __shared__ unsigned long long sacc[15 * 16];   // level-0 state (row 0) and level-1 states (row 1 + line)
   const uint32_t full = (1u << M) - 1;
+  for (int i = threadIdx.x; i < 15 * 16; i += blockDim.x) sacc[i] = 0;
+  __syncthreads();
   double lsum = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     double wn = w[i] * inv_wsum;
@@ -282,7 +297,7 @@ __global__ void grad_kernel(int M, const uint8_t *order, const float *lt, const 
         if (!(T >> jj & 1)) continue;
         double gsc = -wn * ((jj == j ? 1.0 : 0.0) - lp[(size_t)T * 16 + jj]);
         long long q = llrint(gsc * GSCALE);
-        if (q) atomicAdd(acc + (size_t)T * 16 + jj, (unsigned long long)q);
+        if (q) grad_add(sacc, acc, full, T, jj, q);
       }
       T ^= 1u << j;
       double lnt = lt[i * 16 + l + 1];
@@ -290,9 +305,17 @@ __global__ void grad_kernel(int M, const uint8_t *order, const float *lt, const 
       lq += ld2[T] * 0.6931471805599453 + dth * lnt;
       double ge = -wn * (1.0 + dth * lnt);
       long long q = llrint(ge * GSCALE);
-      if (q) atomicAdd(acc + (size_t)T * 16 + 15, (unsigned long long)q);
+      if (q) grad_add(sacc, acc, full, T, 15, q);
     }
     lsum += -wn * lq;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < (1 + M) * 16; i += blockDim.x) {
+    const unsigned long long v = sacc[i];
+    if (!v) continue;
+    const int row = i / 16, col = i % 16;
+    const uint32_t T = row == 0 ? full : full ^ (1u << (row - 1));
+    atomicAdd(acc + (size_t)T * 16 + col, v);
   }
   red[threadIdx.x] = lsum;
   __syncthreads();

@@ -105,3 +105,37 @@ def test_stored_tables_oracle_matches_gpu(ctx):
         assert bound_holds(d["I"], d["E"], ref["I"])
         flag = rejected(d["y"], d["E"], d["log2g"])
         assert np.all(np.abs(d["I"] - ref["I"])[~flag] <= REL * np.abs(ref["I"][~flag]))
+
+
+def test_three_loop_samples_24_to_279_match_stored_oracle(ctx):
+    """The next 256 samples (24..279, seed 0) of every three-loop graph
+    against the oracle's stored I and K (tests/golden/oracle_values_3loop.txt,
+    written by make_oracle_samples.py --compact from oracle/ alone; z and
+    log2 g recomputed by the oracle's sampler and compared bit for bit)."""
+    from oracle.estimate import GraphOracle
+    from oracle.graphs import enumerate_graphs
+    ref = {}
+    for line in open(os.path.join(HERE, "golden", "oracle_values_3loop.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        ref.setdefault(int(f[0]), []).append((int(f[1]), float.fromhex(f[2]), float.fromhex(f[3])))
+    assert sorted(ref) == list(range(28))
+    ctx.load_graphs(3)
+    gs = enumerate_graphs(3)
+    for gi in range(28):
+        rows = sorted(ref[gi])
+        first, count = rows[0][0], len(rows)
+        assert [r[0] for r in rows] == list(range(first, first + count))
+        I = np.array([r[1] for r in rows]); K = np.array([r[2] for r in rows])
+        pts = GraphOracle(gs[gi], gi, integrand=False).points(first, count, 0)
+        d = ctx.eval_samples(gi, first, count, seed=0)
+        assert np.array_equal(d["z"], pts["z"]), gi
+        assert np.array_equal(d["log2g"], pts["log2g"]), gi
+        assert bound_holds(d["I"], d["E"], I), gi
+        fin = np.isfinite(d["K"])
+        assert np.all(np.abs(d["K"] - K)[fin] <= d["E"][fin] + 1e-12 * K[fin]), gi
+        flag = rejected(d["y"], d["E"], d["log2g"])
+        assert np.all(np.abs(d["I"] - I)[~flag] <= REL * np.abs(I[~flag])), gi
+        dd = ctx.eval_samples_dd(gi, first, count, seed=0)
+        assert bound_holds(dd["I"], dd["E"], I), gi
