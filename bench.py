@@ -6,7 +6,8 @@ from the 269 by the library's Philox-seeded shuffle (ae_seeded_subset, seed
 0).  Set-up (untimed, reported): compile the graphs; an initialisation pass
 (plain density, 2^16 samples per graph) whose sigma_down sets the widths of
 the paper's acceptance test (Sec. IV.A, Eq. eq_interval_accept); train one
-learned proposal per graph on the GPU (its own kernels); a pilot that splits
+learned proposal per graph on the GPU (its own kernels; 2^22 plain samples,
+300 Adam steps); a pilot that splits
 each step's budget over the graphs (n_j ~ sigma_j / sqrt(t_j), Sec. IV.C).
 
 Timed step: one block of a run (ae_run_step): every graph continues its own
@@ -269,8 +270,10 @@ def main():
     ap.add_argument("--graphs", type=int, default=20,
                     help="seeded subset of this many graphs of the loop order (0: all of them)")
     ap.add_argument("--samples", type=int, default=1 << 21, help="mean samples per graph per step")
-    ap.add_argument("--train", type=int, default=1 << 20, help="training samples per graph")
-    ap.add_argument("--train-steps", type=int, default=150)
+    ap.add_argument("--train", type=int, default=1 << 22, help="training samples per graph")
+    ap.add_argument("--train-steps", type=int, default=300)
+    ap.add_argument("--beta", type=float, default=0.1, help="weight of the plain density in the learned mixture")
+    ap.add_argument("--seed", type=int, default=0, help="run seed of the timed steps (rank offsets added)")
     ap.add_argument("--cost-ratio", type=float, default=0.0,
                     help="cost-aware proposal training: weight |y|/sqrt(1+R) for samples that need double-double")
     ap.add_argument("--accept", default="paper", choices=["paper", "relative"],
@@ -339,7 +342,7 @@ def main():
         ctx.set_train_cost_ratio(args.cost_ratio)
         t0 = time.perf_counter()
         for i in ids:
-            ctx.train_proposal(i, args.train, seed=7 + rank, steps=args.train_steps, lr=3e-3, beta=0.1)
+            ctx.train_proposal(i, args.train, seed=7 + rank, steps=args.train_steps, lr=3e-3, beta=args.beta)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
 
@@ -384,7 +387,7 @@ def main():
     clocks = Clocks(clocks_path)
     clocks.start()
     torch.cuda.nvtx.range_push("timed")
-    t_dev, e2e_s, per_all = timed_steps(alloc, args.steps, rank_seed(0, rank))
+    t_dev, e2e_s, per_all = timed_steps(alloc, args.steps, rank_seed(args.seed, rank))
     torch.cuda.nvtx.range_pop()
     ck = clocks.stop(local)
     if dist:
@@ -450,7 +453,7 @@ def main():
                  "dd_share_of_step": max(p_steps - p_kern, 0.0) / p_steps if p_steps > 0 else None,
                  "form": "same batched launch, own pilot allocation, step budget scaled to equal device time"}
         for i in ids:
-            ctx.set_proposal(i, 1, 0.1)
+            ctx.set_proposal(i, 1, args.beta)
     peak = ctx.fp64_peak() if rank == 0 else 0.0
     if rank != 0:
         if dist:
@@ -479,6 +482,7 @@ def main():
                    "acceptance": args.accept, "train_samples_per_graph": args.train if learned else 0,
                    "train_steps": args.train_steps if learned else 0,
                    "train_cost_ratio": args.cost_ratio if learned else None,
+                   "beta": args.beta if learned else None,
                    "init_samples_per_graph": args.init_samples, "pilot_samples_per_graph": args.pilot,
                    "l2": "256 MB buffer written between timed steps", "parallelism": "dp%d" % world},
         "inv_sigma2_per_s": isps,
