@@ -262,42 +262,46 @@ __global__ void wsum_kernel(const double *w, uint64_t n, double *part) {
 
 // Loss and gradient with respect to the tabulated quantities, summed in
 // 2^40 fixed point (integer atomics: order-independent, hence
-// deterministic).  acc[T*16+j] (j < 15): d(-ln q)/d l(T,j); acc[T*16+15]:
-// d(-ln q)/d ln Deg_theta(T).  lossp: per-CTA partial of -sum wn ln q_theta.
-// Every sample passes through the full line set (level 0) and one of its M
-// subsets with one line removed (level 1), so those 1 + M states' 16 entries
-// are summed per CTA in shared memory first (integer atomics: the sums are
-// the same in any order) and added to the global table once per CTA.
-__device__ __forceinline__ void grad_add(unsigned long long *sacc, unsigned long long *acc, uint32_t full,
-                                         uint32_t T, int col, long long q) {
+// deterministic).  The choice part of d(-ln q)/d l(T,j) summed over the
+// samples is P(j|T) W_T - C_{T,j}, with W_T = sum of the weights of the
+// samples that choose a line at T and C_{T,j} = of those that choose j, so a
+// sample adds two numbers per level: accw[T] += w, acc[T*16+j] += w (j < 15).
+// acc[T*16+15] receives d(-ln q)/d ln Deg_theta(T) directly.  Every sample
+// passes through the full line set (level 0) and one of its M subsets with
+// one line removed (level 1): those 1 + M states are summed per CTA in
+// shared memory first and added to the global tables once per CTA.
+// lossp: per-CTA partial of -sum wn ln q_theta.
+__device__ __forceinline__ int hot_row(uint32_t full, uint32_t T) {
   const uint32_t gone = full ^ T;
-  if (gone == 0) atomicAdd(sacc + col, (unsigned long long)q);
-  else if ((gone & (gone - 1)) == 0) atomicAdd(sacc + (1 + __ffs(gone) - 1) * 16 + col, (unsigned long long)q);
-  else atomicAdd(acc + (size_t)T * 16 + col, (unsigned long long)q);
+  if (gone == 0) return 0;
+  if ((gone & (gone - 1)) == 0) return __ffs(gone);   // 1 + the removed line
+  return -1;
 }
 
 __global__ void grad_kernel(int M, const uint8_t *order, const float *lt, const double *w, uint64_t n,
-                            double inv_wsum, const double *lp, const double *lp2, const double *ld,
-                            const double *ld2, unsigned long long *acc, double *lossp) {
+                            double inv_wsum, const double *lp2, const double *ld, const double *ld2,
+                            unsigned long long *acc, unsigned long long *accw, double *lossp) {
   __shared__ double red[256];
   __shared__ unsigned long long sacc[15 * 16];   // level-0 state (row 0) and level-1 states (row 1 + line)
+  __shared__ unsigned long long sw[15];
   const uint32_t full = (1u << M) - 1;
   for (int i = threadIdx.x; i < 15 * 16; i += blockDim.x) sacc[i] = 0;
+  for (int i = threadIdx.x; i < 15; i += blockDim.x) sw[i] = 0;
   __syncthreads();
   double lsum = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     double wn = w[i] * inv_wsum;
     if (wn == 0) continue;
+    const unsigned long long qw = (unsigned long long)llrint(wn * GSCALE);
     uint32_t T = full;
     double lq = 0;
     for (int l = 0; l < M - 1; ++l) {
       int j = order[i * 16 + l];
       lq += lp2[(size_t)T * 16 + j] * 0.6931471805599453;
-      for (int jj = 0; jj < M; ++jj) {
-        if (!(T >> jj & 1)) continue;
-        double gsc = -wn * ((jj == j ? 1.0 : 0.0) - lp[(size_t)T * 16 + jj]);
-        long long q = llrint(gsc * GSCALE);
-        if (q) grad_add(sacc, acc, full, T, jj, q);
+      if (qw) {
+        const int r = hot_row(full, T);
+        if (r >= 0) { atomicAdd(sw + r, qw); atomicAdd(sacc + r * 16 + j, qw); }
+        else { atomicAdd(accw + T, qw); atomicAdd(acc + (size_t)T * 16 + j, qw); }
       }
       T ^= 1u << j;
       double lnt = lt[i * 16 + l + 1];
@@ -305,7 +309,11 @@ __global__ void grad_kernel(int M, const uint8_t *order, const float *lt, const 
       lq += ld2[T] * 0.6931471805599453 + dth * lnt;
       double ge = -wn * (1.0 + dth * lnt);
       long long q = llrint(ge * GSCALE);
-      if (q) grad_add(sacc, acc, full, T, 15, q);
+      if (q) {
+        const int r = hot_row(full, T);
+        if (r >= 0) atomicAdd(sacc + r * 16 + 15, (unsigned long long)q);
+        else atomicAdd(acc + (size_t)T * 16 + 15, (unsigned long long)q);
+      }
     }
     lsum += -wn * lq;
   }
@@ -317,6 +325,8 @@ __global__ void grad_kernel(int M, const uint8_t *order, const float *lt, const 
     const uint32_t T = row == 0 ? full : full ^ (1u << (row - 1));
     atomicAdd(acc + (size_t)T * 16 + col, v);
   }
+  for (int r = threadIdx.x; r < 1 + M; r += blockDim.x)
+    if (sw[r]) atomicAdd(accw + (r == 0 ? full : full ^ (1u << (r - 1))), sw[r]);
   red[threadIdx.x] = lsum;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -326,12 +336,16 @@ __global__ void grad_kernel(int M, const uint8_t *order, const float *lt, const 
   if (threadIdx.x == 0) lossp[blockIdx.x] = red[0];
 }
 
-// Fixed point -> dL/do (fp32) through the tanh bounds.
-__global__ void dout_kernel(int M, const unsigned long long *acc, const float *O, float *dO) {
+// Fixed point -> dL/do (fp32) through the tanh bounds: the choice logits
+// take P(j|T) W_T - C_{T,j}, the exponent its accumulated gradient.
+__global__ void dout_kernel(int M, const unsigned long long *acc, const unsigned long long *accw, const double *lp,
+                            const float *O, float *dO) {
   size_t S = (size_t)1 << M;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < S * 16; i += (size_t)gridDim.x * blockDim.x) {
-    double gq = (double)(long long)acc[i] / GSCALE;
     int j = (int)(i & 15);
+    double gq;
+    if (j == 15) gq = (double)(long long)acc[i] / GSCALE;
+    else gq = lp[i] * ((double)accw[i >> 4] / GSCALE) - (double)acc[i] / GSCALE;
     double o = O[i];
     double th = j == 15 ? tanh(o / KAP) : tanh(o / LAM);
     dO[i] = (float)(gq * (1.0 - th * th));
@@ -482,7 +496,7 @@ struct Net {
   __nv_bfloat16 *Wbf, *H1, *H2, *H3;
   float *P, *master, *m, *v, *grad, *O, *dO, *part;
   double *lp, *lp2, *lpc, *ld, *ld2, *ldi, *deg, *wplain, *wsum_part, *loss_part;
-  unsigned long long *acc;
+  unsigned long long *acc, *accw;
   int M;
   int ntiles;
 };
@@ -492,7 +506,7 @@ size_t net_bytes(int M) {
   size_t nt = (S + 63) / 64;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   return al(NPARAM * 2) + 3 * al(S * HID * 2) + al(NPARAM * 4) * 5 + al(S * OUT * 4) * 2 + al(nt * NPARAM * 4) +
-         al(S * 16 * 8) * 3 + al(S * 8) * 5 + al(1024 * 8) * 2 + al(S * 16 * 8);
+         al(S * 16 * 8) * 3 + al(S * 8) * 5 + al(1024 * 8) * 2 + al(S * 16 * 8) + al(S * 8);
 }
 
 void carve(Net &n, void *mem, int M) {
@@ -525,6 +539,7 @@ void carve(Net &n, void *mem, int M) {
   n.wsum_part = (double *)take(1024 * 8);
   n.loss_part = (double *)take(1024 * 8);
   n.acc = (unsigned long long *)take(S * 16 * 8);
+  n.accw = (unsigned long long *)take(S * 8);
 }
 
 // forward + tables for the current weights
@@ -541,9 +556,10 @@ cudaError_t net_loss_grad(Net &n, const uint8_t *order, const float *lt, const d
                           double inv_wsum, cudaStream_t st, double *loss) {
   size_t S = (size_t)1 << n.M;
   cudaMemsetAsync(n.acc, 0, S * 16 * 8, st);
+  cudaMemsetAsync(n.accw, 0, S * 8, st);
   const int gb = 1024;
-  grad_kernel<<<gb, 256, 0, st>>>(n.M, order, lt, w, ns, inv_wsum, n.lp, n.lp2, n.ld, n.ld2, n.acc, n.loss_part);
-  dout_kernel<<<(unsigned)((S * 16 + 255) / 256), 256, 0, st>>>(n.M, n.acc, n.O, n.dO);
+  grad_kernel<<<gb, 256, 0, st>>>(n.M, order, lt, w, ns, inv_wsum, n.lp2, n.ld, n.ld2, n.acc, n.accw, n.loss_part);
+  dout_kernel<<<(unsigned)((S * 16 + 255) / 256), 256, 0, st>>>(n.M, n.acc, n.accw, n.lp, n.O, n.dO);
   mlp_bwd_kernel<<<n.ntiles, 128, 0, st>>>(n.M, n.Wbf, n.H1, n.H2, n.H3, n.dO, n.part);
   grad_reduce_kernel<<<(NPARAM + 255) / 256, 256, 0, st>>>(n.part, n.ntiles, n.grad);
   cudaError_t e = cudaGetLastError();
