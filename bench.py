@@ -6,8 +6,8 @@ from the 269 by the library's Philox-seeded shuffle (ae_seeded_subset, seed
 0).  Set-up (untimed, reported): compile the graphs; an initialisation pass
 (plain density, 2^16 samples per graph) whose sigma_down sets the widths of
 the paper's acceptance test (Sec. IV.A, Eq. eq_interval_accept); train one
-learned proposal per graph on the GPU (its own kernels; 2^22 plain samples,
-300 Adam steps); a pilot that splits
+learned proposal per graph on the GPU (its own kernels; 2^24 plain samples,
+300 full-batch Adam steps); a pilot that splits
 each step's budget over the graphs (n_j ~ sigma_j / sqrt(t_j), Sec. IV.C).
 
 Timed step: one block of a run (ae_run_step): every graph continues its own
@@ -270,7 +270,7 @@ def main():
     ap.add_argument("--graphs", type=int, default=20,
                     help="seeded subset of this many graphs of the loop order (0: all of them)")
     ap.add_argument("--samples", type=int, default=1 << 21, help="mean samples per graph per step")
-    ap.add_argument("--train", type=int, default=1 << 22, help="training samples per graph")
+    ap.add_argument("--train", type=int, default=1 << 24, help="training samples per graph")
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--beta", type=float, default=0.1, help="weight of the plain density in the learned mixture")
     ap.add_argument("--seed", type=int, default=0, help="run seed of the timed steps (rank offsets added)")
