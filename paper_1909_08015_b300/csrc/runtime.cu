@@ -1177,8 +1177,10 @@ static int run_batched_q(ae_ctx *c, const std::vector<int> &ids, const std::vect
       // arguments stay the same (the chunk list and graph descriptors are
       // copied to the device before every launch)
       e0 = c->gev[0]; e1 = c->gev[1]; ek = c->gev[2];
+      uint64_t tol_bits;
+      std::memcpy(&tol_bits, &c->opts.dd_tol, sizeof(tol_bits));   // exact: any change of dd_tol recaptures
       std::string key = std::to_string((uintptr_t)buf) + "/" + std::to_string(seed) + "/" +
-                        std::to_string(c->opts.dd_tol) + "/" + std::to_string(nch) + "/" + std::to_string(total) +
+                        std::to_string(tol_bits) + "/" + std::to_string(nch) + "/" + std::to_string(total) +
                         "/" + std::to_string(qcap) + "/" + std::to_string(ids.size()) + "/" + std::to_string(grid2);
       for (size_t l = 0; l < launches.size(); ++l)
         key += "|" + std::to_string(launches[l].grid) + "," + std::to_string(launches[l].bs) + "," +
