@@ -69,6 +69,8 @@ class RunState:
         arr, _ = self.ctx.run_get()
         raw = bytes(arr)
         t = torch.frombuffer(bytearray(raw), dtype=torch.uint8)
+        if dist.get_backend(group) == "nccl":   # NCCL moves device tensors only
+            t = t.to(torch.device("cuda", torch.cuda.current_device()))
         world = dist.get_world_size(group)
         me = dist.get_rank(group)
         parts = [torch.empty_like(t) for _ in range(world)]
@@ -76,6 +78,6 @@ class RunState:
         for r in range(world):
             if r == me:
                 continue
-            other = (AeRunGraph * len(arr)).from_buffer_copy(parts[r].numpy().tobytes())
+            other = (AeRunGraph * len(arr)).from_buffer_copy(parts[r].cpu().numpy().tobytes())
             self.ctx.run_merge(other)
         return self
