@@ -11,8 +11,10 @@ value = (1/N) sum y, sigma_down^2 = sum y^2/N^2 - (sum y)^2/N^3
 (Eq. eq_sigma_down); set sums add mult_j value_j with sigma^2 = sum
 (mult_j sigma_j)^2 (Eq. eq_sigma_sum).  Sums are compensated (math.fsum).
 
-Pins: summarize() on hand-computed sigma_down; the 2-loop set sum against
-the closed form (samples_batched, a statistical pin).
+Pins: summarize() on hand-computed sigma_down; weight_many() against
+weight() element by element; samples_batched() through the 2-loop set sum
+against the closed form (a statistical pin) and its integrand against the
+exact one point by point.
 """
 import math
 import numpy as np

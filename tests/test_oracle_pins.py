@@ -494,6 +494,12 @@ def test_weight_range_safe():
     assert weight(3.0, 1.0) == 1.5
     assert weight(1.0, 2000.0) == 2.0 ** -2000 or weight(1.0, 2000.0) == 0.0
     assert weight(2.0 ** -1000, -1500.0) == 2.0 ** 500
+    # the array form used by the statistical pins is the same function
+    from oracle.estimate import weight_many
+    rng = np.random.default_rng(2)
+    lg = rng.uniform(-900.0, 3000.0, 500)
+    I = rng.normal(size=500) * 10.0 ** rng.uniform(-30, 30, 500)
+    assert np.array_equal(weight_many(I, lg), np.array([weight(a, b) for a, b in zip(I, lg)]))
 
 
 # ------------------------------------------------------ learned proposal ---
