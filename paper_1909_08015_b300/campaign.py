@@ -33,6 +33,7 @@ def main():
     ap.add_argument("--learned", type=int, default=1, help="1: learned proposals, 0: plain density")
     ap.add_argument("--train", type=int, default=1 << 20)
     ap.add_argument("--train-steps", type=int, default=150)
+    ap.add_argument("--deg-max", type=float, default=None, help="cap on Deg(s) (ae_opts.deg_max; default 1)")
     a = ap.parse_args()
 
     t_start = time.perf_counter()
@@ -40,7 +41,10 @@ def main():
     ids = [i for i, k in enumerate(klass.tolist()) if k == list(a.klass)]
     if not ids:
         raise SystemExit("no graph of class %s at %d loops" % (a.klass, a.loops))
-    ctx = Context(0, default_opts())
+    opts = default_opts()
+    if a.deg_max is not None:
+        opts.deg_max = a.deg_max
+    ctx = Context(0, opts)
     n = ctx.load_graph_subset(a.loops, ids)
     loc = list(range(n))
     t_load = time.perf_counter() - t_start
@@ -66,11 +70,13 @@ def main():
     t_run = time.perf_counter() - t0
     v, s, su, per = ctx.run_estimate()
     N = sum(p["n"] for p in per)
-    line = ("class %s loops %d graphs %d: N %d value %.6f sigma_down %.6f sigma_up %.6f re-evaluated %d "
-            "zeroed %d | this call: %d blocks in %.1f s (%.3g samples/s), set-up %.1f s (load %.1f s)"
-            % (tuple(a.klass), a.loops, n, N, v, s, su, sum(p["n_dd"] for p in per),
-               sum(p["n_nonfinite"] for p in per), blocks, t_run, blocks * a.block / max(t_run, 1e-9),
-               t_setup, t_load))
+    heavy = sum(1 for p in per if p["n"] and p["max_y2"] > 0.5 * p["sum_y2"])
+    line = ("class %s loops %d graphs %d (%s, deg_max %s): N %d value %.6f sigma_down %.6f sigma_up %.6f "
+            "re-evaluated %d zeroed %d, graphs with one sample over half of sum y^2: %d | this call: %d blocks "
+            "in %.1f s (%.3g samples/s), set-up %.1f s (load %.1f s)"
+            % (tuple(a.klass), a.loops, n, "learned" if a.learned else "plain", opts.deg_max, N, v, s, su,
+               sum(p["n_dd"] for p in per), sum(p["n_nonfinite"] for p in per), heavy, blocks, t_run,
+               blocks * a.block / max(t_run, 1e-9), t_setup, t_load))
     print(line)
     if a.summary:
         with open(a.summary, "a") as f:
