@@ -120,7 +120,7 @@ def baseline_graphs(n_loops, canon):
     return [canon[0], canon[len(canon) // 2], canon[-1]]
 
 
-NO_BASELINE = ("not measured: the oracle's own set-up of one graph of this workload takes from minutes "
+NO_ORACLE_SAMPLE = ("not measured: the oracle's own set-up of one graph of this workload takes from minutes "
                "(four loops) to hours (five loops), and no stored coefficient tables cover it")
 
 
@@ -244,7 +244,7 @@ def run_reference(args, rank, world):
     canon = workload_graphs(args.loops, args.graphs)
     cids = baseline_graphs(args.loops, canon)
     if not cids:
-        print(json.dumps({"impl": "reference", "unavailable": NO_BASELINE}))
+        print(json.dumps({"impl": "reference", "unavailable": NO_ORACLE_SAMPLE}))
         return
     per = args.oracle_samples or oracle_samples_default(args.loops)
     rate, cores, evals, wall, setup, wall_all, stored = oracle_rate(args.loops, cids, per)
@@ -469,7 +469,7 @@ def main():
                    "sample": cpu_sample_text(cids, args.loops, per, wall, cores, setup, stored)}
         else:
             cpu = {"value": None, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
-                   "sample": NO_BASELINE}
+                   "sample": NO_ORACLE_SAMPLE}
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     nominal = 2 * 2 * sms * (ck["sm_mhz"] if ck else 2032.0) * 1e6 / 1e12   # 2 DFMA/SM/clk, FMA = 2 flops
     line = {

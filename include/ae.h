@@ -37,8 +37,10 @@ typedef struct ae_opts {
   double C2, C3, C4, D;              /* mixture weights of g2, g3, g4; g3 flattening */
   double C_subI, C_subSE, C_subO;    /* Deg(s) constants used by the library      */
   double C_bigZ, C_bigF, C_add;      /* Deg(s) constants kept, not used           */
-  double deg_max;                    /* cap on Deg(s) (library reading, see the
-                                        design notes); <= 0 means no cap          */
+  double deg_max;                    /* cap on Deg(s) (library reading: power
+                                        counting sees only ultraviolet scaling,
+                                        and infrared-type sets decay like
+                                        lambda^1); <= 0 means no cap              */
   double dd_tol;                     /* acceptance of an FP64 value: its certified
                                         rounding-error bound, carried to y = I/g,
                                         at most dd_tol * max(|y|, the graph's

@@ -3,8 +3,8 @@ vertex graph (Sec. II; Sec. III.A, Eq. eq_feyn_integral).
 
 TEST INFRASTRUCTURE ONLY (see the package header).
 
-Reading of the construction (the paper defers it to its earlier work; the
-readings are listed with the design notes):
+Reading of the construction (the paper defers it to its earlier work; what
+follows is the reading this oracle and the library both implement):
 
 * Every term (F, G') of R^new factorises into one factor per forest element
   S: the reduced graph S/children(S), in which each maximal element of F
@@ -34,8 +34,7 @@ readings are listed with the design notes):
 * A = F2(0), extracted at linear order in q from Gamma(P +- q/2) with the
   projector F2 = -(1/24) (g_ab - P_a P_b) tau^ba, tau from
   Tr[(P+q/2+m) Gamma (P-q/2+m) q_a Y^a], Y_mu^a = [gamma_mu, gamma^a]
-  + 3 gamma_mu Pslash gamma^a + 3 g_mu^a (derived in the design notes; on
-  shell it returns F2 and annihilates the gamma^mu (F1) and q^mu (F3)
+  + 3 gamma_mu Pslash gamma^a + 3 g_mu^a (on shell it returns F2 and annihilates the gamma^mu (F1) and q^mu (F3)
   structures as well as every structure that vanishes on shell, so a graph
   and its mirror image give the same value).
 * a, b, c from traces: E1 = Tr[Gamma^mu gamma_mu] = 16a + 4c,

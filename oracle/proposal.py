@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see the package header).
 
 Definition restated (the paper has no learned component; this is the
-library's extension, see the design notes):
+library's extension):
   * state T = set of lines not yet ordered; features x(T) = 16 indicator
     bits, |T|/M, 1 (zero-padded to 32);
   * h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), h3 = relu(W3 h2 + b3),
