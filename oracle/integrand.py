@@ -34,9 +34,10 @@ follows is the reading this oracle and the library both implement):
 * A = F2(0), extracted at linear order in q from Gamma(P +- q/2) with the
   projector F2 = -(1/24) (g_ab - P_a P_b) tau^ba, tau from
   Tr[(P+q/2+m) Gamma (P-q/2+m) q_a Y^a], Y_mu^a = [gamma_mu, gamma^a]
-  + 3 gamma_mu Pslash gamma^a + 3 g_mu^a (on shell it returns F2 and annihilates the gamma^mu (F1) and q^mu (F3)
-  structures as well as every structure that vanishes on shell, so a graph
-  and its mirror image give the same value).
+  + 3 gamma_mu Pslash gamma^a + 3 g_mu^a (on shell it returns F2 and
+  annihilates the gamma^mu (F1) and q^mu (F3) structures as well as every
+  structure that vanishes on shell, so a graph and its mirror image give
+  the same value).
 * a, b, c from traces: E1 = Tr[Gamma^mu gamma_mu] = 16a + 4c,
   E2 = Tr[Gamma^mu P_mu Pslash] = 4a + 4c, E3 = Tr[Gamma^mu P_mu] = 4b;
   u = Tr[Sigma]/4, v = Tr[Pslash Sigma]/4.
