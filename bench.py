@@ -41,10 +41,14 @@ sys.path.insert(0, ROOT)
 METRIC = "MC samples/s and 1/(σ²·s) per graph set, learned+batched vs plain pdf, 1 B300"
 N_GRAPHS = {1: 1, 2: 4, 3: 28, 4: 269, 5: 3213}
 
-# DRAM bytes (read + write) per launch of the dominant kernel for the
-# default workload, from an ncu capture; None until the current kernel has
-# been captured.
-TRAFFIC_DEFAULT_BYTES = None
+# DRAM bytes (read + write) per launch of the dominant kernel (batched_kernel)
+# in the default workload's timed step: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of the step's three launches (13.9, 17.6 and 9.3 MB;
+# one-pass capture, profiles/bench_4loop_20graphs_launches.md), their mean.
+# Tapes, tables, chunk partials and the re-evaluation queue: about one byte
+# per sample against some 4e4 FP64 flops.  Set to None whenever the kernel
+# changes until it is captured again.
+TRAFFIC_DEFAULT_BYTES = 13.6e6
 
 # FP64 operations of the table-driven elementary functions (one division
 # counted as one operation): exp2 = range reduction (10) + degree-7 Horner
@@ -471,6 +475,8 @@ def main():
             cpu = {"value": None, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": NO_ORACLE_SAMPLE}
     sms = torch.cuda.get_device_properties(local).multi_processor_count
+    default_workload = (args.loops == 4 and args.graphs == 20 and args.samples == 1 << 21 and learned
+                        and args.accept == "paper")
     nominal = 2 * 2 * sms * (ck["sm_mhz"] if ck else 2032.0) * 1e6 / 1e12   # 2 DFMA/SM/clk, FMA = 2 flops
     line = {
         "metric": METRIC, "value": rate, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
@@ -503,7 +509,8 @@ def main():
                           "initialisation": init_s},
         "allocation": {"min": min(alloc), "max": max(alloc), "mode": "pilot, n_j ~ sigma_j/sqrt(t_j)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if peak else None, "traffic": TRAFFIC_DEFAULT_BYTES,
+                     "frac": achieved / peak if peak else None,
+                     "traffic": TRAFFIC_DEFAULT_BYTES if default_workload else None,
                      "kernel": "batched_kernel (sampler + FP64 tape)",
                      "peak_source": "measured: own DFMA probe (ae_fp64_peak)",
                      "peak_nominal": nominal, "frac_vs_nominal": achieved / nominal,
