@@ -161,3 +161,24 @@ def test_bounded_wait_runs_out(ctx):
         ctx.test_stage_timeout(2, 1 << 20)
     after = ctx.integrate([2], 50000, seed=3)
     assert after[0] == before[0] and after[1] == before[1]
+
+
+def test_run_step_argument_errors(ctx):
+    """A graph listed twice in one block, an empty block, an unknown graph and
+    a run step on a context without graphs are refused with AE_ERR_* codes."""
+    ctx.load_graphs(2)
+    ctx.run_reset(0)
+    with pytest.raises(ae.AeError, match="AE_ERR_ARG"):
+        ctx.run_step([1, 1], [100, 100])
+    with pytest.raises(ae.AeError, match="AE_ERR_ARG"):
+        ctx.run_step([0, 1], [0, 0])
+    with pytest.raises(ae.AeError, match="AE_ERR_ARG"):
+        ctx.run_step([7], [100])
+    fresh = ae.Context(0)
+    try:
+        with pytest.raises(ae.AeError, match="AE_ERR_STATE"):
+            fresh.run_step([0], [100])
+    finally:
+        fresh.close()
+    st, _ = ctx.run_get()
+    assert all(g.next == 0 and g.n == 0 for g in st)   # nothing was added

@@ -78,25 +78,31 @@ def test_samples_match_stored_oracle(ctx, n):
         assert abs(per[0]["sum_y"] - sy) <= 1e-9 * abs(sy), cid
 
 
-def test_stored_tables_oracle_matches_gpu(ctx):
-    """Four-loop graph 23 (first of the bench's 20-graph workload) through the
-    oracle rebuilt from its stored coefficient tables
-    (tests/golden/oracle_tables_4loop_23.json.gz, written by
+STORED_TABLES = sorted(int(f.split("_")[-1].split(".")[0]) for f in os.listdir(os.path.join(HERE, "golden"))
+                       if f.startswith("oracle_tables_4loop_") and f.endswith(".json.gz"))
+
+
+@pytest.mark.parametrize("cid", STORED_TABLES)
+def test_stored_tables_oracle_matches_gpu(ctx, cid):
+    """Four-loop graphs of the bench's 20-graph workload through the oracle
+    rebuilt from their stored coefficient tables
+    (tests/golden/oracle_tables_4loop_<id>.json.gz, written by
     tests/golden/make_oracle_tables.py from oracle/ alone; the bench's CPU
-    baseline evaluates it this way): per-sample values against the GPU within
-    the certified bound, indices on both sides of 2^32.  Pins the stored
-    tables and extends the four-loop per-sample parity to this graph."""
+    baseline evaluates them this way): per-sample values against the GPU
+    within the certified bound, indices on both sides of 2^32.  Pins the
+    stored tables and extends the four-loop per-sample parity to these
+    graphs."""
     import gzip
     import json
     from oracle.estimate import GraphOracle
     from oracle.graphs import enumerate_graphs
     from oracle.integrand import Integrand
-    path = os.path.join(HERE, "golden", "oracle_tables_4loop_23.json.gz")
+    path = os.path.join(HERE, "golden", "oracle_tables_4loop_%d.json.gz" % cid)
     with gzip.open(path, "rt") as f:
         rec = json.load(f)
-    assert rec["loops"] == 4 and rec["graph"] == 23
-    o = GraphOracle(enumerate_graphs(4)[23], 23, tables=Integrand.tables_from_records(rec["tables"]))
-    ctx.load_graph_subset(4, [23])
+    assert rec["loops"] == 4 and rec["graph"] == cid
+    o = GraphOracle(enumerate_graphs(4)[cid], cid, tables=Integrand.tables_from_records(rec["tables"]))
+    ctx.load_graph_subset(4, [cid])
     for first in (0, 2 ** 32 - 4):
         ref = o.samples(first, 8, seed=3)
         d = ctx.eval_samples(0, first, 8, seed=3)
