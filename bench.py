@@ -173,10 +173,10 @@ def _oracle_job(args):
     return cnt, time.perf_counter() - t, setup
 
 
-def oracle_samples_default(n_loops):
+def oracle_samples_default(n_loops, n_graphs=1):
     """Samples per graph for about 10-30 s of oracle evaluation on the host."""
     cores = os.cpu_count() or 1
-    return {1: 4096, 2: 2048, 3: 96}.get(n_loops, 16 * cores)
+    return {1: 4096, 2: 2048, 3: 96}.get(n_loops, max(1, 16 * cores // max(1, n_graphs)))
 
 
 def cpu_sample_text(cids, n_loops, per_graph, wall, cores, setup, stored):
@@ -250,7 +250,7 @@ def run_reference(args, rank, world):
     if not cids:
         print(json.dumps({"impl": "reference", "unavailable": NO_ORACLE_SAMPLE}))
         return
-    per = args.oracle_samples or oracle_samples_default(args.loops)
+    per = args.oracle_samples or oracle_samples_default(args.loops, len(cids))
     rate, cores, evals, wall, setup, wall_all, stored = oracle_rate(args.loops, cids, per)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "samples/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -467,7 +467,7 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cids = baseline_graphs(args.loops, canon)
         if cids:
-            per = args.oracle_samples or oracle_samples_default(args.loops)
+            per = args.oracle_samples or oracle_samples_default(args.loops, len(cids))
             crate, cores, evals, wall, setup, _, stored = oracle_rate(args.loops, cids, per)
             cpu = {"value": crate, "unit": "samples/s", "cores": cores, "kind": "oracle",
                    "sample": cpu_sample_text(cids, args.loops, per, wall, cores, setup, stored)}
