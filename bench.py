@@ -418,6 +418,10 @@ def main():
     h2d = sum(p["h2d_bytes"] for per in per_all for p in per) / args.steps
     n_dd = sum(p["n_dd"] for per in per_all for p in per)
     zeroed = sum(p["n_nonfinite"] for per in per_all for p in per)
+    # the double-double pass's own work: re-evaluated samples x (double-double
+    # tape flops + sampler), over the device time after the FP64 kernels
+    dd_s = max(step_s - kern_s, 0.0)
+    dd_fl = sum((info[i]["flops_dd"] + sampler_flops(M, learned)) * per[i]["n_dd"] for per in per_all for i in ids)
 
     plain = other = None
     if rank == 0 and learned and not args.no_compare:
@@ -496,10 +500,13 @@ def main():
                                         if sigma > 0 else None),
         "estimate": {"value": val, "sigma_down": sigma, "sigma_up": sigma_up, "samples": total,
                      "dd_reevaluated": int(n_dd), "zeroed": int(zeroed)},
-        "dd_pass": {"reevaluated": int(n_dd), "zeroed": int(zeroed), "seconds": max(step_s - kern_s, 0.0),
-                    "share_of_step": (max(step_s - kern_s, 0.0) / step_s) if step_s > 0 else None,
+        "dd_pass": {"reevaluated": int(n_dd), "zeroed": int(zeroed), "seconds": dd_s,
+                    "share_of_step": (dd_s / step_s) if step_s > 0 else None,
+                    "achieved_tflops": dd_fl / dd_s / 1e12 if dd_s > 0 else None,
+                    "frac": dd_fl / dd_s / 1e12 / peak if dd_s > 0 and peak else None,
                     "note": "double-double re-evaluation, queue sort and reduction; not credited to the FP64 "
-                            "fraction"},
+                            "fraction; its own frac counts the double-double tape's FP64 flops (FMA = 2) "
+                            "against the same measured peak"},
         "plain_pdf": plain,
         "gain_vs_plain": ({"inv_sigma2_per_s": isps / plain["inv_sigma2_per_s"],
                            "note": "learned+batched over plain+batched, equal device time"}

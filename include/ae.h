@@ -117,6 +117,8 @@ typedef struct ae_graph_meta {
   int bound_depth;       /* D: roundings on the deepest chain into I; the
                             bound is gamma_D M_I (Sec. IV.A, library reading) */
   double flops_bound;    /* of flops, those of the magnitude twins */
+  double flops_dd;       /* FP64 flops of one double-double evaluation of the
+                            tape (FMA = 2), by the form each instruction takes */
 } ae_graph_meta;
 int ae_graph_info(ae_ctx *ctx, int graph_id, ae_graph_meta *out);
 

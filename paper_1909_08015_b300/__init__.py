@@ -34,7 +34,7 @@ class AeGraphMeta(ctypes.Structure):
                 ("n_subgraphs", ctypes.c_int), ("n_terms", ctypes.c_int),
                 ("tape_len", ctypes.c_int), ("nslots", ctypes.c_int),
                 ("n_monomials", ctypes.c_int), ("flops", ctypes.c_double), ("canonical_id", ctypes.c_int),
-                ("bound_depth", ctypes.c_int), ("flops_bound", ctypes.c_double)]
+                ("bound_depth", ctypes.c_int), ("flops_bound", ctypes.c_double), ("flops_dd", ctypes.c_double)]
 
 
 class AeRunGraph(ctypes.Structure):

@@ -157,6 +157,7 @@ struct Tape {
   int depth = 0;                  // roundings along the deepest chain into I
   double flops = 0;               // FP64 flops per evaluation (FMA = 2)
   double flops_bound = 0;         // of which the error bound's magnitude twins
+  double flops_dd = 0;            // FP64 flops of one double-double evaluation (FMA = 2)
   int M = 0;
   int n_terms = 0;
 };

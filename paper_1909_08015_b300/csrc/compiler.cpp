@@ -1357,6 +1357,24 @@ Tape compile_integrand(const Graph &g, CompileStats *st) {
     o.c = (uint16_t)(cc * 8);
     tp.code.push_back(o);
   }
+  // FP64 flops of the double-double evaluation of every instruction, by the
+  // form its hints select (FMA = 2; two-sum 6, quick two-sum 3 operations):
+  // magnitude twin 2, exact scaling 8, product 10, sum 11, c + exact k*a 16,
+  // general 18, quotient 86, |a| 0, c + |a| 11
+  for (const Ins &o : tp.code) {
+    const uint16_t sp = o.op & 0xff00;
+    double f;
+    if (o.op & I_AB) f = 2;
+    else if (sp == 0) {
+      const bool bx = (o.op & (I_BK | I_KX)) == (I_BK | I_KX);
+      if (o.op & I_C0) f = bx ? 8 : 10;
+      else if (o.op & I_B1) f = 11;
+      else f = bx ? 16 : 18;
+    } else if (sp == I_DIV) f = 86;
+    else if (sp == I_ABS) f = 0;
+    else f = 11;
+    tp.flops_dd += f;
+  }
   tp.khi = B.khi; tp.klo = B.klo;
   tp.nslots = nslots | 1;   // odd row pitch: the rows of a warp fall in distinct banks
   tp.out_I = slot[outI]; tp.out_K = slot[outK]; tp.out_E = slot[outE];

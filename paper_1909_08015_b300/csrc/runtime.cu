@@ -717,7 +717,7 @@ extern "C" int ae_graph_info(ae_ctx *c, int id, ae_graph_meta *o) {
   o->tape_len = (int)lg.tape.code.size(); o->nslots = lg.tape.nslots;
   o->n_monomials = lg.st.n_monomials; o->flops = lg.tape.flops;
   o->canonical_id = lg.canonical_id;
-  o->bound_depth = lg.tape.depth; o->flops_bound = lg.tape.flops_bound;
+  o->bound_depth = lg.tape.depth; o->flops_bound = lg.tape.flops_bound; o->flops_dd = lg.tape.flops_dd;
   return AE_OK;
 }
 
