@@ -277,6 +277,9 @@ def main():
     ap.add_argument("--train", type=int, default=1 << 24, help="training samples per graph")
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--beta", type=float, default=0.1, help="weight of the plain density in the learned mixture")
+    ap.add_argument("--refine", type=int, default=0,
+                    help="rounds of proposal refinement on samples of the current mixture (--train samples each)")
+    ap.add_argument("--refine-steps", type=int, default=150)
     ap.add_argument("--seed", type=int, default=0, help="run seed of the timed steps (rank offsets added)")
     ap.add_argument("--cost-ratio", type=float, default=0.0,
                     help="cost-aware proposal training: weight |y|/sqrt(1+R) for samples that need double-double")
@@ -347,6 +350,8 @@ def main():
         t0 = time.perf_counter()
         for i in ids:
             ctx.train_proposal(i, args.train, seed=7 + rank, steps=args.train_steps, lr=3e-3, beta=args.beta)
+            for r in range(args.refine):
+                ctx.refine_proposal(i, args.train, seed=17 + r + rank, steps=args.refine_steps, lr=1e-3)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
 
@@ -491,6 +496,7 @@ def main():
                    "samples_per_step": sum(alloc), "seed": "run seed (+ rank offset), counters continue",
                    "acceptance": args.accept, "train_samples_per_graph": args.train if learned else 0,
                    "train_steps": args.train_steps if learned else 0,
+                   "refine_rounds": args.refine if learned else 0,
                    "train_cost_ratio": args.cost_ratio if learned else None,
                    "beta": args.beta if learned else None,
                    "init_samples_per_graph": args.init_samples, "pilot_samples_per_graph": args.pilot,

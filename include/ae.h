@@ -231,6 +231,16 @@ typedef struct ae_train_report {
 int ae_train_proposal(ae_ctx *ctx, int graph_id, uint64_t n_train, uint64_t seed, int steps,
                       double lr, double beta, ae_train_report *report);
 
+/* Refine a graph's trained proposal (library extension, like the proposal
+ * itself): the current weights go on training for `steps` Adam steps on
+ * n_train samples drawn from the current mixture (indices from 2^41 on),
+ * weighted w = |I|/q with q the mixture's density, so that the training data
+ * concentrate where |I| is large; the loss and its estimate of the forward
+ * Kullback-Leibler divergence to |I| stay the same.  beta is kept.
+ * AE_ERR_STATE if the graph has no active trained proposal. */
+int ae_refine_proposal(ae_ctx *ctx, int graph_id, uint64_t n_train, uint64_t seed, int steps, double lr,
+                       ae_train_report *report);
+
 /* Select a graph's density: mode 0 = plain g, 1 = learned mixture with weight
  * beta on g (needs a trained proposal). */
 int ae_set_proposal(ae_ctx *ctx, int graph_id, int mode, double beta);

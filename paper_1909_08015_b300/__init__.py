@@ -99,6 +99,8 @@ def lib():
         L.ae_train_proposal.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_double, P(AeTrainReport)]
         L.ae_set_proposal.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        L.ae_refine_proposal.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                         ctypes.c_double, P(AeTrainReport)]
         L.ae_set_accept_floor.argtypes = [vp, ctypes.c_int, ctypes.c_double]
         L.ae_set_train_cost_ratio.argtypes = [vp, ctypes.c_double]
         L.ae_proposal_eval.argtypes = [vp, ctypes.c_int, P(ctypes.c_float), dp, dp, P(ctypes.c_uint8),
@@ -307,6 +309,13 @@ class Context:
         r = AeTrainReport()
         self._check(lib().ae_train_proposal(self._h, gid, int(n_train), int(seed), int(steps), float(lr),
                                             float(beta), ctypes.byref(r)))
+        return {k: getattr(r, k) for k, _ in r._fields_}
+
+    def refine_proposal(self, gid, n_train, seed=0, steps=100, lr=1e-3):
+        """Continue training the graph's proposal on samples of its current mixture."""
+        r = AeTrainReport()
+        self._check(lib().ae_refine_proposal(self._h, gid, int(n_train), int(seed), int(steps), float(lr),
+                                             ctypes.byref(r)))
         return {k: getattr(r, k) for k, _ in r._fields_}
 
     def set_proposal(self, gid, mode, beta=0.1):

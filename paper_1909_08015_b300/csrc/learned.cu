@@ -211,9 +211,11 @@ __global__ void tables_kernel(int M, const float *O, const double *deg, const do
   }
 }
 
-// Training samples from the plain density: order[16] (descending z),
-// ln t at levels 1..M-1, and w = |I|/g, divided by sqrt(1 + R) for samples
-// the acceptance test sends to double-double (R = 0: the plain weights).
+// Training samples from the graph's density (the plain one; the current
+// learned mixture when a proposal is refined): order[16] (descending z),
+// ln t at levels 1..M-1, and w = |I|/q (q the sampling density), divided by
+// sqrt(1 + R) for samples the acceptance test sends to double-double (R = 0:
+// the plain weights).
 // With per-sample cost c, the density minimising variance x expected cost
 // is proportional to |f| / sqrt(c) rather than to |f|.
 __global__ void train_gen_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t seed, uint8_t *order,
@@ -224,7 +226,7 @@ __global__ void train_gen_kernel(GraphDev G, uint64_t first, uint64_t count, uin
     uint64_t i = base + threadIdx.x;
     if (i >= count) continue;
     double z[14], lz[14], lg;
-    draw_sample(G, first + i, seed, z, lz, lg);
+    draw_any(G, first + i, seed, z, lz, lg);   // plain density, or the current mixture when refining
     for (int k = 0; k < G.M; ++k) Sl[k] = z[k];
     run_tape(G, Sl);
     double y, Ey;
@@ -610,8 +612,12 @@ static void attach_tables(LoadedGraph &lg, Net &n) {
   lg.dev.lPc = n.lpc;
 }
 
-extern "C" int ae_train_proposal(ae_ctx *c, int gid, uint64_t n_train, uint64_t seed, int steps, double lr,
-                                 double beta, ae_train_report *rep) {
+// Training of a graph's proposal.  refine = false: fresh weights, samples of
+// the plain density (indices from 2^40 on).  refine = true: the current
+// weights go on training on samples of the current mixture (indices from
+// 2^41 on), weighted |I|/q, which concentrates the data where |I| is large.
+static int train_impl(ae_ctx *c, int gid, uint64_t n_train, uint64_t seed, int steps, double lr, double beta,
+                      ae_train_report *rep, bool refine) {
   if (!c) return AE_ERR_ARG;
   if (c->device < 0) return ae_fail(c, AE_ERR_NODEV, "training needs a CUDA device");
   if (gid < 0 || gid >= (int)c->graphs.size()) return ae_fail(c, AE_ERR_ARG, "graph id out of range");
@@ -619,24 +625,31 @@ extern "C" int ae_train_proposal(ae_ctx *c, int gid, uint64_t n_train, uint64_t 
     return ae_fail(c, AE_ERR_ARG, "need n_train >= 1024, steps >= 0, lr > 0, 0 < beta <= 1");
   cudaSetDevice(c->device);
   LoadedGraph &lg = c->graphs[gid];
+  if (refine && (!lg.learned.mem || !lg.learned.active || lg.learned.master.size() != (size_t)NPARAM))
+    return ae_fail(c, AE_ERR_STATE, "refining needs an active trained proposal");
   int M = lg.g.M();
   size_t S = (size_t)1 << M;
   cudaStream_t st = c->stream;
   auto t0 = std::chrono::steady_clock::now();
   // network and tables
-  if (lg.learned.mem) { cudaFree(lg.learned.mem); lg.learned.mem = nullptr; }
-  lg.dev.lP = nullptr;
-  size_t nb = net_bytes(M);
-  if (cudaMalloc(&lg.learned.mem, nb) != cudaSuccess) return ae_fail(c, AE_ERR_OOM, "proposal buffers");
-  lg.learned.bytes = nb;
+  if (!refine) {
+    if (lg.learned.mem) { cudaFree(lg.learned.mem); lg.learned.mem = nullptr; }
+    lg.dev.lP = nullptr;
+    size_t nb = net_bytes(M);
+    if (cudaMalloc(&lg.learned.mem, nb) != cudaSuccess) return ae_fail(c, AE_ERR_OOM, "proposal buffers");
+    lg.learned.bytes = nb;
+  }
   Net n;
   carve(n, lg.learned.mem, M);
-  std::vector<double> wpl(S, 1.0), dg(S, 1.0);
-  for (size_t R = 1; R + 1 < S; ++R) { dg[R] = lg.dens.deg[0][R]; wpl[R] = lg.dens.phi[0][R] / lg.dens.deg[0][R]; }
-  cudaMemcpyAsync(n.deg, dg.data(), S * 8, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(n.wplain, wpl.data(), S * 8, cudaMemcpyHostToDevice, st);
+  if (!refine) {
+    std::vector<double> wpl(S, 1.0), dg(S, 1.0);
+    for (size_t R = 1; R + 1 < S; ++R) { dg[R] = lg.dens.deg[0][R]; wpl[R] = lg.dens.phi[0][R] / lg.dens.deg[0][R]; }
+    cudaMemcpyAsync(n.deg, dg.data(), S * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(n.wplain, wpl.data(), S * 8, cudaMemcpyHostToDevice, st);
+  }
   std::vector<float> p;
-  init_params(p, seed);
+  if (refine) p = lg.learned.master;
+  else init_params(p, seed);
   cudaMemcpyAsync(n.master, p.data(), NPARAM * 4, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(n.P, p.data(), NPARAM * 4, cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(n.m, 0, NPARAM * 4, st);
@@ -651,14 +664,14 @@ extern "C" int ae_train_proposal(ae_ctx *c, int gid, uint64_t n_train, uint64_t 
     cudaFree(d_order); cudaFree(d_lt); cudaFree(d_w);
     return ae_fail(c, AE_ERR_OOM, "training sample buffers");
   }
-  GraphDev G = lg.dev;
-  G.lP = nullptr;
+  GraphDev G = lg.dev;   // refining: the current mixture's tables are attached
+  if (!refine) G.lP = nullptr;
   int bs = 64;
   while (bs < 256 && (size_t)bs * 2 * G.nslots * 8 <= 96 * 1024) bs *= 2;
   size_t smem = (size_t)bs * G.nslots * 8;
   cudaFuncSetAttribute(train_gen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   train_gen_kernel<<<(unsigned)std::min<uint64_t>((n_train + bs - 1) / bs, (uint64_t)c->sm_count * 8), bs, smem, st>>>(
-      G, 1ull << 40, n_train, seed, d_order, d_lt, d_w, c->opts.dd_tol, c->train_cost_ratio);
+      G, refine ? 1ull << 41 : 1ull << 40, n_train, seed, d_order, d_lt, d_w, c->opts.dd_tol, c->train_cost_ratio);
   wsum_kernel<<<1024, 256, 0, st>>>(d_w, n_train, n.wsum_part);
   std::vector<double> wp(1024);
   cudaMemcpyAsync(wp.data(), n.wsum_part, 1024 * 8, cudaMemcpyDeviceToHost, st);
@@ -699,6 +712,18 @@ extern "C" int ae_train_proposal(ae_ctx *c, int gid, uint64_t n_train, uint64_t 
     rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return AE_OK;
+}
+
+extern "C" int ae_train_proposal(ae_ctx *c, int gid, uint64_t n_train, uint64_t seed, int steps, double lr,
+                                 double beta, ae_train_report *rep) {
+  return train_impl(c, gid, n_train, seed, steps, lr, beta, rep, false);
+}
+
+extern "C" int ae_refine_proposal(ae_ctx *c, int gid, uint64_t n_train, uint64_t seed, int steps, double lr,
+                                  ae_train_report *rep) {
+  if (!c) return AE_ERR_ARG;
+  if (gid < 0 || gid >= (int)c->graphs.size()) return ae_fail(c, AE_ERR_ARG, "graph id out of range");
+  return train_impl(c, gid, n_train, seed, steps, lr, c->graphs[gid].learned.beta, rep, true);
 }
 
 extern "C" int ae_set_proposal(ae_ctx *c, int gid, int mode, double beta) {

@@ -159,3 +159,36 @@ def test_fast_exp2_log2_against_device_library(ctx):
     err = np.abs(out[:, 2] - out[:, 3]) / np.spacing(np.abs(out[:, 3]))
     assert err.max() <= 4, err.max()
     assert list(out[-4:, 2]) == [0.0, 1.0, -1.0, -2.0]
+
+
+def test_refined_proposal_normalised_unbiased_and_matches_oracle(ctx):
+    """Refinement (more Adam steps on samples of the current mixture): the
+    mixture stays normalised (E_q[1/q] = 1/(M-1)!), its estimate agrees with
+    the plain density's, and its samples still match the oracle's learned
+    sampler fed with the exported outputs."""
+    from oracle import proposal as pr
+    from oracle.philox import uniforms_fine
+    ctx.load_graphs(3)
+    gs = enumerate_graphs(3)
+    gid = 9
+    with pytest.raises(ae.AeError, match="AE_ERR_STATE"):
+        ctx.refine_proposal(gid, 1 << 16, seed=1, steps=5)
+    ctx.train_proposal(gid, 1 << 18, seed=1, steps=60, lr=3e-3, beta=0.1)
+    rep = ctx.refine_proposal(gid, 1 << 18, seed=2, steps=40, lr=1e-3)
+    assert rep["steps"] == 40 and math.isfinite(rep["loss_final"])
+    d = ctx.eval_samples(gid, 0, 1 << 20, seed=3)
+    wq = np.exp2(-d["log2g"]) * math.factorial(7)
+    assert abs(wq.mean() - 1) < 4 * wq.std() / math.sqrt(len(wq))
+    N = 1 << 22
+    _, _, pl = ctx.integrate([gid], N, seed=4)
+    ctx.set_proposal(gid, 0)
+    _, _, pp = ctx.integrate([gid], N, seed=5)
+    ctx.set_proposal(gid, 1, 0.1)
+    assert abs(pl[0]["mean"] - pp[0]["mean"]) < 4 * math.hypot(pl[0]["sigma1"], pp[0]["sigma1"])
+    params, out, beta = ctx.proposal_export(gid)
+    dens = Density(gs[gid])
+    got = ctx.eval_samples(gid, 0, 1000, seed=6)
+    u = uniforms_fine(np.arange(0, 1000, dtype=np.uint64), gid, 6, dens.M)
+    z, lq, _ = pr.learned_points(dens, out.astype(np.float64), beta, u)
+    assert np.max(np.abs(got["z"] - z) / z) < 1e-12
+    assert np.max(np.abs(got["log2g"] - lq)) < 1e-10 * max(1.0, np.max(np.abs(lq)))
