@@ -269,8 +269,9 @@ int ae_set_accept_floor(ae_ctx *ctx, int graph_id, double yfloor);
  * for the graph; 0: back to the relative test).  Widths and sigma_down are
  * those of each graph's contribution, multiplicity included (ae_graph_result
  * .sigma); the library tests y against width / mult. */
-int ae_accept_widths(const double *sigma_down, int n, double *width);
-int ae_set_accept_width(ae_ctx *ctx, int graph_id, double width);
+int ae_accept_widths(const double *sigma_down, int n, double *width);   /* AE_ERR_ARG: NULL or n <= 0 */
+int ae_set_accept_width(ae_ctx *ctx, int graph_id, double width);   /* AE_ERR_ARG: unknown graph,
+                                                                       width < 0 or not finite */
 
 /* Cost-aware training weights of the learned proposal (library design; the
  * paper has no learned part): with ratio R > 0, a training sample that the
@@ -351,7 +352,8 @@ typedef struct ae_run_graph {
 } ae_run_graph;
 
 /* Start a run over all loaded graphs with the given seed: zero sums, next
- * sample index 0 for every graph.  Loading graphs clears the run. */
+ * sample index 0 for every graph.  Loading graphs clears the run.
+ * AE_ERR_STATE if no graphs are loaded. */
 int ae_run_reset(ae_ctx *ctx, uint64_t seed);
 
 /* One block of the run: graph_ids[i] gets samples next .. next+n_samples[i]-1
@@ -359,29 +361,34 @@ int ae_run_reset(ae_ctx *ctx, uint64_t seed);
  * kernels, captured in a CUDA graph that later steps of the same shape
  * launch again); the sums are added to the run and next advances.  per
  * (nullable, n_ids entries) receives this block's own per-graph results
- * (device seconds, launches, bytes copied included). */
+ * (device seconds, launches, bytes copied included).  Errors (the run is
+ * then unchanged): AE_ERR_ARG for an unknown graph, a graph listed twice, no
+ * samples at all or a sample index past 2^64; AE_ERR_NODEV on a host-only
+ * context; AE_ERR_STATE with no graphs loaded; AE_ERR_CUDA / AE_ERR_TIMEOUT
+ * from the launch. */
 int ae_run_step(ae_ctx *ctx, const int *graph_ids, int n_ids, const uint64_t *n_samples,
                 ae_graph_result *per);
 
 /* Add an integration result of `count` samples of one graph (e.g. from
  * ae_integrate_range at the graph's next index) to the run; next advances by
- * count.  Host only. */
+ * count.  Host only.  AE_ERR_ARG for an unknown graph or an index past 2^64,
+ * AE_ERR_NONFINITE if r's sums are not finite. */
 int ae_run_add(ae_ctx *ctx, int graph_id, const ae_graph_result *r, uint64_t count);
 
-/* Copy the run state of all loaded graphs into out (n = number of loaded
- * graphs), and the seed (nullable). */
+/* Copy the run state of all loaded graphs into out (caller-owned, n = the
+ * number of loaded graphs, else AE_ERR_ARG), and the seed (nullable). */
 int ae_run_get(ae_ctx *ctx, ae_run_graph *out, int n, uint64_t *seed);
 
 /* Add another run's sums (e.g. another rank's, on its own stream) to this
  * run, graph by graph in order, double-double; this run's next indices stay.
- * n = number of loaded graphs. */
+ * n = number of loaded graphs, else AE_ERR_ARG. */
 int ae_run_merge(ae_ctx *ctx, const ae_run_graph *other, int n);
 
 /* The run's estimate: value = sum_j mult_j mean_j, sigma^2 = sum_j (mult_j
  * sigma_down_j)^2 (Eqs. eq_integral_approx, eq_sigma_down, eq_sigma_sum),
  * sigma_up likewise with the heuristic sigma_up_j (nullable outputs).  per
  * (nullable) receives one result per loaded graph (graphs with no samples:
- * value 0, sigma 0). */
+ * value 0, sigma 0).  AE_ERR_STATE if no graphs are loaded. */
 int ae_run_estimate(ae_ctx *ctx, double *value, double *sigma, double *sigma_up, ae_graph_result *per);
 
 /* Write the run (graph set identity: loop order, canonical ids, generator;
