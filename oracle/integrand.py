@@ -217,6 +217,18 @@ def _det_inv(A):
     return det, [row[n:] for row in M]
 
 
+def _rational_in(dtype, q):
+    """The rational q (int or Fraction) in the floating type dtype.  numpy
+    converts a Fraction through a Python float, which would leave a long
+    double evaluation with double-rounded coefficients; for wider types the
+    numerator and denominator are read from their decimal strings (exact up
+    to 64 bits, else rounded once) and divided."""
+    q = Fraction(q)
+    if np.dtype(dtype) == np.float64:
+        return np.float64(float(q))   # correctly rounded
+    return dtype(str(q.numerator)) / dtype(str(q.denominator))
+
+
 def _det_inv_batch(A):
     """Determinant and inverse by Gauss-Jordan elimination for matrices whose
     entries are arrays over sample points (one matrix per point).  The
@@ -536,7 +548,8 @@ class Integrand:
         points.  Coefficients of lambda powers j >= n are left out (evaluate()
         asserts that they vanish exactly).  Not a parity reference: only the
         statistical pin of the 2-loop sum uses it (with exact re-evaluation
-        of the points where two precisions disagree)."""
+        of the points where two precisions disagree).  The rational
+        coefficients enter rounded once to the dtype (_rational_in)."""
         z = np.asarray(z, dtype=dtype)
         al = {}
         for key, i in self.idx.items():
@@ -557,7 +570,7 @@ class Integrand:
             U, Z, a, b, V = gf[fk]
             vec = {}
             for coef, j, asites, qsite, pairs in table:
-                m = zero + dtype(coef)
+                m = zero + _rational_in(dtype, coef)
                 for s_ in asites:
                     m = m * a[s_]
                 if qsite is not None:
