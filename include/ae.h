@@ -410,17 +410,22 @@ int ae_combine_runs(const double *v1, const double *s1, const double *v2, const 
                     double *v_out, double *s_out, double *total, double *total_sigma);
 
 /* Per-sample dump for parity tests: samples first .. first+count-1 of
- * graph_id under `seed`, evaluated in FP64.  z: count*M, log2g, I, K, y, E:
+ * graph_id under `seed`, evaluated in FP64 by the same staged tape
+ * interpreter as the integration kernels (each CTA takes a contiguous chunk
+ * in rounds of one sample per thread; ae_opts.grid_ctas caps the grid, so a
+ * small cap makes many rounds per CTA).  z: count*M, log2g, I, K, y, E:
  * count each (any may be NULL); E is the certified bound on |I - exact I|
  * (rounding only: gamma_D times the magnitude evaluation of I).  Host
- * buffers. */
+ * buffers.  AE_ERR_TIMEOUT if a tape-staging wait ran out (outputs then
+ * undefined); AE_ERR_CUDA on a CUDA error. */
 int ae_eval_samples(ae_ctx *ctx, int graph_id, uint64_t first, uint64_t count,
                     uint64_t seed, double *z, double *log2g, double *I, double *K,
                     double *y, double *E);
 
 /* Same samples, every one evaluated by the double-double (about 106-bit)
- * twin of the integrand tape.  I, K, y, E: count each (any may be NULL); E
- * is the bound at the double-double unit. */
+ * twin of the integrand tape, through the staged interpreter of the
+ * re-evaluation pass.  I, K, y, E: count each (any may be NULL); E is the
+ * bound at the double-double unit.  Errors as ae_eval_samples. */
 int ae_eval_samples_dd(ae_ctx *ctx, int graph_id, uint64_t first, uint64_t count,
                        uint64_t seed, double *I, double *K, double *y, double *E);
 

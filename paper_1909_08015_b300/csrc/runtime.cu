@@ -141,41 +141,72 @@ __global__ void dd_staged_kernel(GraphDev Gp, uint64_t seed, const unsigned long
   }
 }
 
-// Per-sample dump for parity tests.
-__global__ void eval_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t seed, double *z_out,
-                            double *lg_out, double *I_out, double *K_out, double *y_out, double *E_out) {
-  extern __shared__ double slots[];
-  double *S = slots + threadIdx.x * G.nslots;   // this thread's row of the slot file
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < count;
-       base += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t i = base + threadIdx.x;
-    if (i >= count) continue;
-    double z[14], lz[14], lg;
-    draw_any(G, first + i, seed, z, lz, lg);
-    for (int k = 0; k < G.M; ++k) { S[k] = z[k]; z_out[i * G.M + k] = z[k]; }
-    run_tape(G, S);
-    double I = S[G.outI], Kv = S[G.outK];
-    lg_out[i] = lg; I_out[i] = I; K_out[i] = Kv; y_out[i] = weight(I, lg); E_out[i] = S[G.outE];
+// Per-sample dump for parity tests, through the same CTA-synchronous staged
+// interpreter as integrate_kernel and batched_kernel: CTA b takes the b-th
+// contiguous chunk of [0, count) and steps through it blockDim samples at a
+// time, so that a small grid runs several rounds per CTA (segment 0 of the
+// next round issued while the last segment of this one executes).
+__global__ void eval_kernel(GraphDev Gp, uint64_t first, uint64_t count, uint64_t seed, double *z_out,
+                            double *lg_out, double *I_out, double *K_out, double *y_out, double *E_out, int *err) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ __align__(16) unsigned char Gmem[sizeof(GraphDev)];   // raw: no dynamic initialisation
+  GraphDev &G = *reinterpret_cast<GraphDev *>(Gmem);
+  __shared__ uint64_t bars[2];
+  Stage st{reinterpret_cast<Ins *>(dsm), bars, 0, 0, kWaitCycles};
+  if (threadIdx.x == 0) { G = Gp; stage_init(st); }
+  __syncthreads();
+  double *S = reinterpret_cast<double *>(dsm + kStageBytes) + threadIdx.x * G.nslots;   // this thread's row
+  const uint64_t chunk = (count + gridDim.x - 1) / gridDim.x;
+  const uint64_t lo = (uint64_t)blockIdx.x * chunk;
+  const uint64_t hi = min(count, lo + chunk);
+  double z[14], lz[14];
+  if (threadIdx.x == 0 && lo < hi) stage_issue(st, G, 0);
+  for (uint64_t base = lo; base < hi; base += blockDim.x) {
+    const uint64_t i = base + threadIdx.x;
+    const bool active = i < hi;
+    double lg = 0.0;
+    if (active) {
+      draw_any(G, first + i, seed, z, lz, lg);
+      for (int k = 0; k < G.M; ++k) { S[k] = z[k]; z_out[i * G.M + k] = z[k]; }
+    }
+    if (!run_tape_staged(st, G, S, active, base + blockDim.x < hi, err)) return;
+    if (!active) continue;
+    const double I = S[G.outI];
+    lg_out[i] = lg; I_out[i] = I; K_out[i] = S[G.outK]; y_out[i] = weight(I, lg); E_out[i] = S[G.outE];
   }
 }
 
-// Per-sample dump with every sample evaluated in double-double.
-__global__ void eval_dd_kernel(GraphDev G, uint64_t first, uint64_t count, uint64_t seed,
-                               double *I_out, double *K_out, double *y_out, double *E_out) {
-  extern __shared__ dd dslots2[];
-  dd *S = dslots2 + threadIdx.x * G.nslots;   // this thread's row of the slot file
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < count;
-       base += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t i = base + threadIdx.x;
-    if (i >= count) continue;
-    double z[14], lz[14], lg;
-    draw_any(G, first + i, seed, z, lz, lg);
-    for (int k = 0; k < G.M; ++k) S[k] = {z[k], 0.0};
-    run_tape_dd(G, S);
-    dd I = S[G.outI], K = S[G.outK];
-    double Iv = I.hi + I.lo;
-    I_out[i] = Iv; K_out[i] = K.hi + K.lo; y_out[i] = weight(Iv, lg);
-    E_out[i] = S[G.outE].hi * 0x1p-47;   // bound at the double-double unit
+// Per-sample dump with every sample evaluated in double-double, through the
+// staged double-double interpreter of the re-evaluation pass: item k =
+// samples k*blockDim .. (k+1)*blockDim-1, items taken in grid-stride order.
+__global__ void eval_dd_kernel(GraphDev Gp, uint64_t first, uint64_t count, uint64_t seed, double *I_out,
+                               double *K_out, double *y_out, double *E_out, int *err) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ __align__(16) unsigned char Gmem[sizeof(GraphDev)];   // raw: no dynamic initialisation
+  GraphDev &G = *reinterpret_cast<GraphDev *>(Gmem);
+  __shared__ uint64_t bars[2];
+  Stage st{reinterpret_cast<Ins *>(dsm), bars, 0, 0, kWaitCycles};
+  if (threadIdx.x == 0) { G = Gp; stage_init(st); }
+  __syncthreads();
+  dd *S = reinterpret_cast<dd *>(dsm + kStageBytes) + threadIdx.x * G.nslots;   // this thread's row
+  double z[14], lz[14];
+  const uint64_t items = (count + blockDim.x - 1) / blockDim.x;
+  for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    if (threadIdx.x == 0) stage_issue(st, G, 0);
+    const uint64_t i = it * blockDim.x + threadIdx.x;
+    const bool active = i < count;
+    double lg = 0.0;
+    if (active) {
+      draw_any(G, first + i, seed, z, lz, lg);
+      for (int k = 0; k < G.M; ++k) S[k] = dd{z[k], 0.0};
+    }
+    if (!run_tape_dd_staged(st, G, S, active, err)) return;
+    if (active) {
+      const double Iv = S[G.outI].hi + S[G.outI].lo;
+      I_out[i] = Iv; K_out[i] = S[G.outK].hi + S[G.outK].lo; y_out[i] = weight(Iv, lg);
+      E_out[i] = S[G.outE].hi * 0x1p-47;   // bound at the double-double unit
+    }
+    __syncthreads();   // every thread is done with the last segment's buffer
   }
 }
 
@@ -1542,6 +1573,18 @@ extern "C" int ae_allocate(ae_ctx *c, const int *ids, int n_ids, uint64_t n_pilo
   return AE_OK;
 }
 
+// Grid of a per-sample dump: as many CTAs as are resident on the device
+// (ae_opts.ctas_per_sm, else the occupancy calculator), capped by
+// ae_opts.grid_ctas and by one CTA per blockDim samples.
+static unsigned dump_grid(const ae_ctx *c, const void *kernel, int bs, size_t smem, uint64_t count) {
+  int per_sm = c->opts.ctas_per_sm;
+  if (per_sm <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, bs, smem) != cudaSuccess)
+    per_sm = 1;
+  uint64_t grid = (uint64_t)c->sm_count * (uint64_t)std::max(per_sm, 1);
+  if (c->opts.grid_ctas > 0) grid = std::min<uint64_t>(grid, (uint64_t)c->opts.grid_ctas);
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(grid, (count + bs - 1) / bs));
+}
+
 extern "C" int ae_eval_samples(ae_ctx *c, int gid, uint64_t first, uint64_t count, uint64_t seed,
                                double *z, double *log2g, double *I, double *K, double *y, double *E) {
   if (!c) return AE_ERR_ARG;
@@ -1550,18 +1593,24 @@ extern "C" int ae_eval_samples(ae_ctx *c, int gid, uint64_t first, uint64_t coun
   if (count == 0) return AE_OK;
   CUDA_TRY(c, cudaSetDevice(c->device));
   GraphDev &G = c->graphs[gid].dev;
-  int bs = pick_block_for(c, (const void *)eval_kernel, G.nslots, 8);
+  int bs = pick_block_for(c, (const void *)eval_kernel, G.nslots, 8, kStageBytes);
   if (bs < 0) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
-  size_t smem = (size_t)bs * G.nslots * 8;
+  size_t smem = kStageBytes + (size_t)bs * G.nslots * 8;
   CUDA_TRY(c, cudaFuncSetAttribute(eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const unsigned grid = dump_grid(c, (const void *)eval_kernel, bs, smem, count);
   double *d = nullptr;
   size_t per = (size_t)G.M + 5;
-  CUDA_TRY(c, cudaMalloc(&d, count * per * 8));
+  CUDA_TRY(c, cudaMalloc(&d, count * per * 8 + 16));
   double *dz = d, *dl = d + count * G.M, *dI = dl + count, *dK = dI + count, *dy = dK + count, *dE = dy + count;
-  unsigned grid = (unsigned)std::min<uint64_t>((count + bs - 1) / bs, (uint64_t)c->sm_count * 8);
-  eval_kernel<<<grid, bs, smem, c->stream>>>(G, first, count, seed, dz, dl, dI, dK, dy, dE);
-  cudaError_t e = cudaGetLastError();
+  int *derr = reinterpret_cast<int *>(dE + count);
+  cudaError_t e = cudaMemsetAsync(derr, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) {
+    eval_kernel<<<grid, bs, smem, c->stream>>>(G, first, count, seed, dz, dl, dI, dK, dy, dE, derr);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && z) e = cudaMemcpy(z, dz, count * G.M * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && log2g) e = cudaMemcpy(log2g, dl, count * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && I) e = cudaMemcpy(I, dI, count * 8, cudaMemcpyDeviceToHost);
@@ -1569,6 +1618,7 @@ extern "C" int ae_eval_samples(ae_ctx *c, int gid, uint64_t first, uint64_t coun
   if (e == cudaSuccess && y) e = cudaMemcpy(y, dy, count * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && E) e = cudaMemcpy(E, dE, count * 8, cudaMemcpyDeviceToHost);
   cudaFree(d);
+  if (e == cudaSuccess && herr) return fail(c, AE_ERR_TIMEOUT, "eval_samples: a tape-staging wait ran out");
   if (e != cudaSuccess) return fail(c, AE_ERR_CUDA, std::string("eval_samples: ") + cudaGetErrorString(e));
   return AE_OK;
 }
@@ -1662,21 +1712,29 @@ extern "C" int ae_eval_samples_dd(ae_ctx *c, int gid, uint64_t first, uint64_t c
   if (count == 0) return AE_OK;
   CUDA_TRY(c, cudaSetDevice(c->device));
   GraphDev &G = c->graphs[gid].dev;
-  int bs = pick_block_for(c, (const void *)eval_dd_kernel, G.nslots, 16);
+  int bs = pick_block_for(c, (const void *)eval_dd_kernel, G.nslots, 16, kStageBytes);
   if (bs < 0) return fail(c, AE_ERR_STATE, "tape slot file does not fit in shared memory");
-  size_t smem = (size_t)bs * G.nslots * 16;
+  size_t smem = kStageBytes + (size_t)bs * G.nslots * 16;
   CUDA_TRY(c, cudaFuncSetAttribute(eval_dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const unsigned grid = dump_grid(c, (const void *)eval_dd_kernel, bs, smem, count);
   double *d = nullptr;
-  CUDA_TRY(c, cudaMalloc(&d, count * 4 * 8));
-  unsigned grid = (unsigned)std::min<uint64_t>((count + bs - 1) / bs, (uint64_t)c->sm_count * 8);
-  eval_dd_kernel<<<grid, bs, smem, c->stream>>>(G, first, count, seed, d, d + count, d + 2 * count, d + 3 * count);
-  cudaError_t e = cudaGetLastError();
+  CUDA_TRY(c, cudaMalloc(&d, count * 4 * 8 + 16));
+  int *derr = reinterpret_cast<int *>(d + 4 * count);
+  cudaError_t e = cudaMemsetAsync(derr, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) {
+    eval_dd_kernel<<<grid, bs, smem, c->stream>>>(G, first, count, seed, d, d + count, d + 2 * count, d + 3 * count,
+                                                  derr);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && I) e = cudaMemcpy(I, d, count * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && K) e = cudaMemcpy(K, d + count, count * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && y) e = cudaMemcpy(y, d + 2 * count, count * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && E) e = cudaMemcpy(E, d + 3 * count, count * 8, cudaMemcpyDeviceToHost);
   cudaFree(d);
+  if (e == cudaSuccess && herr) return fail(c, AE_ERR_TIMEOUT, "eval_samples_dd: a tape-staging wait ran out");
   if (e != cudaSuccess) return fail(c, AE_ERR_CUDA, std::string("eval_samples_dd: ") + cudaGetErrorString(e));
   return AE_OK;
 }
