@@ -490,6 +490,22 @@ def test_batched_integrand_matches_exact():
         assert np.allclose(K.astype(np.float64), r["K"], rtol=1e-12)
 
 
+def test_batched_long_double_coefficients_are_long_double():
+    """The rational coefficients enter the long-double form rounded once to
+    long double (numpy would take a Fraction through double); large
+    numerators and denominators included."""
+    from fractions import Fraction
+    from oracle.integrand import _rational_in
+    ld = np.longdouble
+    assert _rational_in(ld, Fraction(1, 3)) == ld(1) / ld(3)
+    assert _rational_in(ld, Fraction(1, 3)) != ld(float(Fraction(1, 3)))
+    assert _rational_in(ld, Fraction(-7, 10)) == -ld(7) / ld(10)
+    assert _rational_in(ld, 12345) == ld(12345)
+    big = Fraction(3 ** 40 + 1, 2 ** 70 + 3)   # parts wider than 64 bits: rounded, not truncated to double
+    assert abs(float((Fraction(str(_rational_in(ld, big))) - big) / big)) < 2.0 ** -60
+    assert _rational_in(np.float64, Fraction(1, 3)) == 1.0 / 3.0
+
+
 def test_weight_range_safe():
     assert weight(3.0, 1.0) == 1.5
     assert weight(1.0, 2000.0) == 2.0 ** -2000 or weight(1.0, 2000.0) == 0.0
