@@ -262,17 +262,20 @@ __global__ void wsum_kernel(const double *w, uint64_t n, double *part) {
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-// Loss and gradient with respect to the tabulated quantities, summed in
-// 2^40 fixed point (integer atomics: order-independent, hence
-// deterministic).  The choice part of d(-ln q)/d l(T,j) summed over the
-// samples is P(j|T) W_T - C_{T,j}, with W_T = sum of the weights of the
-// samples that choose a line at T and C_{T,j} = of those that choose j, so a
-// sample adds two numbers per level: accw[T] += w, acc[T*16+j] += w (j < 15).
-// acc[T*16+15] receives d(-ln q)/d ln Deg_theta(T) directly.  Every sample
-// passes through the full line set (level 0) and one of its M subsets with
-// one line removed (level 1): those 1 + M states are summed per CTA in
-// shared memory first and added to the global tables once per CTA.
-// lossp: per-CTA partial of -sum wn ln q_theta.
+// The forward-KL loss -sum_i wn_i ln q_theta(z_i) over fixed training
+// samples depends on them only through per-state sums (fixed point, 2^40;
+// integer atomics: order-independent, hence deterministic), gathered once
+// per training call:
+//   acc[T*16+j]  (j < 15)  weight of the samples that choose line j at T,
+//   accw[T]                weight of the samples that choose a line at T,
+//   bpost[T]               weight of the samples that reach T by a choice,
+//   acc[T*16+15]           sum of wn ln t over those samples (signed),
+// since ln q_theta(z) = sum over the walk's levels of ln P(j|T) (choice) +
+// ln Deg_theta(T') + Deg_theta(T') ln t (the ratio t = u^(1/Deg) drawn at the
+// state T' the choice leads to).  Every sample passes through the full line
+// set (level 0) and one of its M subsets with one line removed (level 1):
+// those 1 + M states are summed per CTA in shared memory first and added to
+// the global tables once per CTA.
 __device__ __forceinline__ int hot_row(uint32_t full, uint32_t T) {
   const uint32_t gone = full ^ T;
   if (gone == 0) return 0;
@@ -280,44 +283,39 @@ __device__ __forceinline__ int hot_row(uint32_t full, uint32_t T) {
   return -1;
 }
 
-__global__ void grad_kernel(int M, const uint8_t *order, const float *lt, const double *w, uint64_t n,
-                            double inv_wsum, const double *lp2, const double *ld, const double *ld2,
-                            unsigned long long *acc, unsigned long long *accw, double *lossp) {
-  __shared__ double red[256];
+__global__ void stats_kernel(int M, const uint8_t *order, const float *lt, const double *w, uint64_t n,
+                             double inv_wsum, unsigned long long *acc, unsigned long long *accw,
+                             unsigned long long *bpost) {
   __shared__ unsigned long long sacc[15 * 16];   // level-0 state (row 0) and level-1 states (row 1 + line)
-  __shared__ unsigned long long sw[15];
+  __shared__ unsigned long long sw[15], sb[15];
   const uint32_t full = (1u << M) - 1;
   for (int i = threadIdx.x; i < 15 * 16; i += blockDim.x) sacc[i] = 0;
-  for (int i = threadIdx.x; i < 15; i += blockDim.x) sw[i] = 0;
+  for (int i = threadIdx.x; i < 15; i += blockDim.x) { sw[i] = 0; sb[i] = 0; }
   __syncthreads();
-  double lsum = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    double wn = w[i] * inv_wsum;
+    const double wn = w[i] * inv_wsum;
     if (wn == 0) continue;
     const unsigned long long qw = (unsigned long long)llrint(wn * GSCALE);
     uint32_t T = full;
-    double lq = 0;
     for (int l = 0; l < M - 1; ++l) {
-      int j = order[i * 16 + l];
-      lq += lp2[(size_t)T * 16 + j] * 0.6931471805599453;
+      const int j = order[i * 16 + l];
       if (qw) {
         const int r = hot_row(full, T);
         if (r >= 0) { atomicAdd(sw + r, qw); atomicAdd(sacc + r * 16 + j, qw); }
         else { atomicAdd(accw + T, qw); atomicAdd(acc + (size_t)T * 16 + j, qw); }
       }
       T ^= 1u << j;
-      double lnt = lt[i * 16 + l + 1];
-      double dth = ld[T];
-      lq += ld2[T] * 0.6931471805599453 + dth * lnt;
-      double ge = -wn * (1.0 + dth * lnt);
-      long long q = llrint(ge * GSCALE);
-      if (q) {
-        const int r = hot_row(full, T);
-        if (r >= 0) atomicAdd(sacc + r * 16 + 15, (unsigned long long)q);
-        else atomicAdd(acc + (size_t)T * 16 + 15, (unsigned long long)q);
+      const long long qc = llrint(wn * (double)lt[i * 16 + l + 1] * GSCALE);
+      const int r = hot_row(full, T);
+      if (qw) {
+        if (r >= 0) atomicAdd(sb + r, qw);
+        else atomicAdd(bpost + T, qw);
+      }
+      if (qc) {
+        if (r >= 0) atomicAdd(sacc + r * 16 + 15, (unsigned long long)qc);
+        else atomicAdd(acc + (size_t)T * 16 + 15, (unsigned long long)qc);
       }
     }
-    lsum += -wn * lq;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < (1 + M) * 16; i += blockDim.x) {
@@ -327,31 +325,55 @@ __global__ void grad_kernel(int M, const uint8_t *order, const float *lt, const 
     const uint32_t T = row == 0 ? full : full ^ (1u << (row - 1));
     atomicAdd(acc + (size_t)T * 16 + col, v);
   }
-  for (int r = threadIdx.x; r < 1 + M; r += blockDim.x)
-    if (sw[r]) atomicAdd(accw + (r == 0 ? full : full ^ (1u << (r - 1))), sw[r]);
-  red[threadIdx.x] = lsum;
+  for (int r = threadIdx.x; r < 1 + M; r += blockDim.x) {
+    const uint32_t T = r == 0 ? full : full ^ (1u << (r - 1));
+    if (sw[r]) atomicAdd(accw + T, sw[r]);
+    if (sb[r]) atomicAdd(bpost + T, sb[r]);
+  }
+}
+
+// dL/do (fp32) through the tanh bounds: the choice logits take
+// P(j|T) W_T - C_{T,j}; the exponent -(B_T + Deg_theta(T) L_T), B = bpost
+// and L = acc[.. 15] (d/d ln Deg of -B ln Deg - Deg L).
+__global__ void dout_kernel(int M, const unsigned long long *acc, const unsigned long long *accw,
+                            const unsigned long long *bpost, const double *lp, const double *ld, const float *O,
+                            float *dO) {
+  size_t S = (size_t)1 << M;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < S * 16; i += (size_t)gridDim.x * blockDim.x) {
+    int j = (int)(i & 15);
+    double gq;
+    if (j == 15) gq = -(double)bpost[i >> 4] / GSCALE - ld[i >> 4] * ((double)(long long)acc[i] / GSCALE);
+    else gq = lp[i] * ((double)accw[i >> 4] / GSCALE) - (double)acc[i] / GSCALE;
+    double o = O[i];
+    double th = j == 15 ? tanh(o / KAP) : tanh(o / LAM);
+    dO[i] = (float)(gq * (1.0 - th * th));
+  }
+}
+
+// Per-CTA partials of the loss from the same sums:
+// -[ln 2 sum C_{T,j} log2 P(j|T) + ln 2 sum B_T log2 Deg_theta(T) + sum Deg_theta(T) L_T].
+__global__ void loss_kernel(int M, const unsigned long long *acc, const unsigned long long *bpost,
+                            const double *lp2, const double *ld, const double *ld2, double *lossp) {
+  __shared__ double red[256];
+  const size_t S = (size_t)1 << M;
+  double s = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < S * 16; i += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i & 15);
+    const size_t T = i >> 4;
+    if (j < 15) {
+      if (acc[i]) s += ((double)acc[i] / GSCALE) * lp2[i] * 0.6931471805599453;
+    } else {
+      if (bpost[T]) s += ((double)bpost[T] / GSCALE) * ld2[T] * 0.6931471805599453;
+      if (acc[i]) s += ld[T] * ((double)(long long)acc[i] / GSCALE);
+    }
+  }
+  red[threadIdx.x] = -s;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
   if (threadIdx.x == 0) lossp[blockIdx.x] = red[0];
-}
-
-// Fixed point -> dL/do (fp32) through the tanh bounds: the choice logits
-// take P(j|T) W_T - C_{T,j}, the exponent its accumulated gradient.
-__global__ void dout_kernel(int M, const unsigned long long *acc, const unsigned long long *accw, const double *lp,
-                            const float *O, float *dO) {
-  size_t S = (size_t)1 << M;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < S * 16; i += (size_t)gridDim.x * blockDim.x) {
-    int j = (int)(i & 15);
-    double gq;
-    if (j == 15) gq = (double)(long long)acc[i] / GSCALE;
-    else gq = lp[i] * ((double)accw[i >> 4] / GSCALE) - (double)acc[i] / GSCALE;
-    double o = O[i];
-    double th = j == 15 ? tanh(o / KAP) : tanh(o / LAM);
-    dO[i] = (float)(gq * (1.0 - th * th));
-  }
 }
 
 // Backward over a 64-state tile: dH = dZ W (tensor cores), ReLU masks, and
@@ -498,7 +520,7 @@ struct Net {
   __nv_bfloat16 *Wbf, *H1, *H2, *H3;
   float *P, *master, *m, *v, *grad, *O, *dO, *part;
   double *lp, *lp2, *lpc, *ld, *ld2, *ldi, *deg, *wplain, *wsum_part, *loss_part;
-  unsigned long long *acc, *accw;
+  unsigned long long *acc, *accw, *bpost;
   int M;
   int ntiles;
 };
@@ -508,7 +530,7 @@ size_t net_bytes(int M) {
   size_t nt = (S + 63) / 64;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   return al(NPARAM * 2) + 3 * al(S * HID * 2) + al(NPARAM * 4) * 5 + al(S * OUT * 4) * 2 + al(nt * NPARAM * 4) +
-         al(S * 16 * 8) * 3 + al(S * 8) * 5 + al(1024 * 8) * 2 + al(S * 16 * 8) + al(S * 8);
+         al(S * 16 * 8) * 3 + al(S * 8) * 5 + al(1024 * 8) * 2 + al(S * 16 * 8) + al(S * 8) * 2;
 }
 
 void carve(Net &n, void *mem, int M) {
@@ -542,6 +564,7 @@ void carve(Net &n, void *mem, int M) {
   n.loss_part = (double *)take(1024 * 8);
   n.acc = (unsigned long long *)take(S * 16 * 8);
   n.accw = (unsigned long long *)take(S * 8);
+  n.bpost = (unsigned long long *)take(S * 8);
 }
 
 // forward + tables for the current weights
@@ -553,27 +576,39 @@ cudaError_t net_forward(Net &n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// loss and gradient over n samples (device arrays); returns host loss
-cudaError_t net_loss_grad(Net &n, const uint8_t *order, const float *lt, const double *w, uint64_t ns,
-                          double inv_wsum, cudaStream_t st, double *loss) {
+// The training samples' sums (device arrays; see stats_kernel).
+cudaError_t net_stats(Net &n, const uint8_t *order, const float *lt, const double *w, uint64_t ns, double inv_wsum,
+                      cudaStream_t st) {
   size_t S = (size_t)1 << n.M;
   cudaMemsetAsync(n.acc, 0, S * 16 * 8, st);
   cudaMemsetAsync(n.accw, 0, S * 8, st);
-  const int gb = 1024;
-  grad_kernel<<<gb, 256, 0, st>>>(n.M, order, lt, w, ns, inv_wsum, n.lp2, n.ld, n.ld2, n.acc, n.accw, n.loss_part);
-  dout_kernel<<<(unsigned)((S * 16 + 255) / 256), 256, 0, st>>>(n.M, n.acc, n.accw, n.lp, n.O, n.dO);
+  cudaMemsetAsync(n.bpost, 0, S * 8, st);
+  stats_kernel<<<1024, 256, 0, st>>>(n.M, order, lt, w, ns, inv_wsum, n.acc, n.accw, n.bpost);
+  return cudaGetLastError();
+}
+
+// Parameter gradient of the current weights from the sums (after net_forward).
+cudaError_t net_grad(Net &n, cudaStream_t st) {
+  size_t S = (size_t)1 << n.M;
+  dout_kernel<<<(unsigned)((S * 16 + 255) / 256), 256, 0, st>>>(n.M, n.acc, n.accw, n.bpost, n.lp, n.ld, n.O, n.dO);
   mlp_bwd_kernel<<<n.ntiles, 128, 0, st>>>(n.M, n.Wbf, n.H1, n.H2, n.H3, n.dO, n.part);
   grad_reduce_kernel<<<(NPARAM + 255) / 256, 256, 0, st>>>(n.part, n.ntiles, n.grad);
+  return cudaGetLastError();
+}
+
+// Loss of the current weights from the sums (after net_forward); host value.
+cudaError_t net_loss(Net &n, cudaStream_t st, double *loss) {
+  size_t S = (size_t)1 << n.M;
+  const int gb = (int)std::min<size_t>(1024, (S * 16 + 255) / 256);
+  loss_kernel<<<gb, 256, 0, st>>>(n.M, n.acc, n.bpost, n.lp2, n.ld, n.ld2, n.loss_part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (loss) {
-    std::vector<double> lp(gb);
-    e = cudaMemcpyAsync(lp.data(), n.loss_part, gb * 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    double s = 0;
-    for (double x : lp) s += x;
-    *loss = s;
-  }
+  std::vector<double> lp(gb);
+  e = cudaMemcpyAsync(lp.data(), n.loss_part, gb * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  double s = 0;
+  for (double x : lp) s += x;
+  *loss = s;
   return e;
 }
 
@@ -683,18 +718,24 @@ static int train_impl(ae_ctx *c, int gid, uint64_t n_train, uint64_t seed, int s
   double wsum = 0;
   for (double x : wp) wsum += x;
   double inv = wsum > 0 ? 1.0 / wsum : 0.0;
+  // the samples enter the loss only through per-state sums: gather them
+  // once, release the samples, and take every step on the sums alone
+  e = net_stats(n, d_order, d_lt, d_w, n_train, inv, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_order); cudaFree(d_lt); cudaFree(d_w);
   double loss0 = 0, loss = 0;
-  for (int s = 0; s <= steps; ++s) {
+  for (int s = 0; e == cudaSuccess && s <= steps; ++s) {
     e = net_forward(n, st);
-    if (e == cudaSuccess) e = net_loss_grad(n, d_order, d_lt, d_w, n_train, inv, st, &loss);
+    if (e == cudaSuccess && (s == 0 || s == steps)) e = net_loss(n, st, &loss);
     if (e != cudaSuccess) break;
     if (s == 0) loss0 = loss;
     if (s == steps) break;
+    e = net_grad(n, st);
+    if (e != cudaSuccess) break;
     float b1t = (float)std::pow(0.9, s + 1), b2t = (float)std::pow(0.999, s + 1);
     adam_kernel<<<(NPARAM + 255) / 256, 256, 0, st>>>(n.master, n.m, n.v, n.grad, n.Wbf, n.P, (float)lr, b1t, b2t);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(d_order); cudaFree(d_lt); cudaFree(d_w);
   if (e != cudaSuccess) return ae_fail(c, AE_ERR_CUDA, std::string("training: ") + cudaGetErrorString(e));
   lg.learned.master.resize(NPARAM);
   cudaMemcpy(lg.learned.master.data(), n.master, NPARAM * 4, cudaMemcpyDeviceToHost);
@@ -820,7 +861,10 @@ extern "C" int ae_proposal_eval(ae_ctx *c, int M, const float *params, const dou
   double wsum = 0;
   for (uint64_t i = 0; i < n; ++i) wsum += w[i];
   cudaError_t e = net_forward(net, st);
-  if (e == cudaSuccess) e = net_loss_grad(net, d_order, d_lt, d_w, n, wsum > 0 ? 1.0 / wsum : 0.0, st, loss);
+  if (e == cudaSuccess) e = net_stats(net, d_order, d_lt, d_w, n, wsum > 0 ? 1.0 / wsum : 0.0, st);
+  if (e == cudaSuccess) e = net_grad(net, st);
+  if (e == cudaSuccess) e = net_loss(net, st, loss);   // ends with a stream synchronisation
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaMemcpy(grad, net.grad, NPARAM * 4, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && lp2_out) e = cudaMemcpy(lp2_out, net.lp2, S * 16 * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && ld_out) e = cudaMemcpy(ld_out, net.ld, S * 8, cudaMemcpyDeviceToHost);
