@@ -619,3 +619,24 @@ def test_fine_uniforms_layout():
                 m = (w[2 * h] << 20) | (w[2 * h + 1] >> 12)
                 assert u[row, 2 * b + h] == (2 * m + 1) * 2.0 ** -53
     assert np.all((u > 0) & (u < 1))
+
+
+def test_oracle_pool_values_cover_exact():
+    """The scale-test helper (tests/oracle_pool.py): its batched values lie
+    within its stated uncertainty of the exact ones at its own least certain
+    samples and at random ones, its points are the sampler's, and the exact
+    referee returns Integrand.evaluate."""
+    from oracle.estimate import GraphOracle
+    from tests.oracle_pool import exact_values, graph_values
+    g = enumerate_graphs(2)[1]
+    r = graph_values((2, 1, 100, 2048, 3, 8))
+    assert r["first"] == 100 and len(r["I"]) == 2048
+    o = GraphOracle(g, 1)
+    p = o.points(100, 2048, 3)
+    assert np.array_equal(p["z"], r["z"]) and np.array_equal(p["log2g"], r["log2g"])
+    k = r["exact_idx"]
+    assert np.all(np.abs(r["I"][k] - r["exact_I"]) <= r["scale"][k])
+    pick = np.random.default_rng(4).choice(2048, 24, replace=False)
+    ex = exact_values((2, 1, r["z"][pick]))
+    assert np.array_equal(ex, np.array([float(o.integrand.evaluate(z)[0]) for z in r["z"][pick]]))
+    assert np.all(np.abs(r["I"][pick] - ex) <= r["scale"][pick])
