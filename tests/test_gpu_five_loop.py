@@ -1,5 +1,7 @@
 """Five-loop graphs (a seeded subset of the 3213): the oracle's coefficient
-tables take hours per graph at this order, so the path is pinned in parts:
+tables take hours per graph at this order (one graph is compared with the
+oracle itself, from stored tables, in test_gpu_five_loop_oracle.py), so the
+path is pinned here in parts:
 sample points and densities bit for bit against the oracle's sampler; the
 GPU integrand bit for bit against the host replay of the same compiled tape
 (both evaluate the same IEEE operations in the same order); and the
